@@ -1,0 +1,447 @@
+"""Pins of the CPU oracle to things other than itself (CPU only).
+
+Each test checks one oracle function against what the paper or mathematics
+fixes: brute force on tiny inputs, closed forms, a dense eigendecomposition,
+quadrature, finite differences, statistical expectations. A plausible slip in
+the oracle (dropped term, wrong sign or index, transposed operand) fails at
+least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from helpers import cheb_eval, cliques_edges, dense_laplacian, dense_w, random_graph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def to_dense(g):
+    W = np.zeros((g.n, g.n))
+    for i in range(g.n):
+        for e in range(g.rowptr[i], g.rowptr[i + 1]):
+            W[i, g.colidx[e]] = g.val[e]
+    return W
+
+
+# --------------------------------------------------------------------------
+# §2 / §2.1: W, strengths, L = S - W
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_csr_matches_bruteforce(oracle_mod, seed):
+    n, m = 23, 120
+    src, dst, w = random_graph(n, m, seed, connected=False)
+    # plant explicit duplicates with different weights and self-loops
+    src = np.concatenate([src, [3, 5, 7, 7]]).astype(np.int32)
+    dst = np.concatenate([dst, [4, 3, 7, 7]]).astype(np.int32)
+    w = np.concatenate([w, [9.0, 0.01, 1.0, 2.0]])
+    g = oracle_mod.csr_build(n, src, dst, w)
+    W = dense_w(n, src, dst, w)
+    np.testing.assert_array_equal(to_dense(g), W)
+    # columns strictly increasing within rows, no diagonal
+    for i in range(n):
+        cols = g.colidx[g.rowptr[i]:g.rowptr[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+        assert i not in cols
+    assert g.nnz == int((W > 0).sum())  # all planted weights are positive
+
+
+def test_csr_empty_and_isolated(oracle_mod):
+    g = oracle_mod.csr_build(5, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    assert g.nnz == 0 and list(g.rowptr) == [0] * 6
+    g = oracle_mod.csr_build(6, [0, 0], [0, 5], [1.0, 2.0])
+    assert list(g.rowptr) == [0, 1, 1, 1, 1, 1, 2]
+    assert list(g.colidx) == [5, 0]
+
+
+def test_csr_rejects_bad_input(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.csr_build(3, [0], [3], [1.0])
+    with pytest.raises(ValueError):
+        oracle_mod.csr_build(3, [0], [1], [-1.0])
+    with pytest.raises(ValueError):
+        oracle_mod.csr_build(3, [0], [1], [float("nan")])
+
+
+def test_strength_and_laplacian_null_vector(oracle_mod):
+    src, dst, w = random_graph(40, 200, 7)
+    g = oracle_mod.csr_build(40, src, dst, w)
+    s = oracle_mod.strength(g)
+    W = dense_w(40, src, dst, w)
+    np.testing.assert_allclose(s, W.sum(axis=1), rtol=1e-14)
+    assert math.isclose(s.sum(), g.val.sum(), rel_tol=1e-13)
+    L = dense_laplacian(W)
+    np.testing.assert_allclose(L @ np.ones(40), 0.0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# §4.1 step 1: lambda_N
+# --------------------------------------------------------------------------
+
+def _named_graph(kind, n):
+    if kind == "path":
+        return np.arange(n - 1), np.arange(1, n)
+    if kind == "cycle":
+        return np.arange(n), (np.arange(n) + 1) % n
+    if kind == "complete":
+        i, j = np.triu_indices(n, 1)
+        return i, j
+    if kind == "star":
+        return np.zeros(n - 1, int), np.arange(1, n)
+    raise ValueError(kind)
+
+
+def test_lanczos_closed_form_spectra(oracle_mod):
+    rows = []
+    with open(os.path.join(GOLDEN, "closed_form_spectra.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                kind, n, lam = line.split()
+                rows.append((kind, int(n), float(lam)))
+    assert len(rows) >= 8
+    rng = np.random.default_rng(3)
+    for kind, n, lam in rows:
+        src, dst = _named_graph(kind, n)
+        g = oracle_mod.csr_build(n, src, dst)
+        th = oracle_mod.lanczos_max(g, n, rng.standard_normal(n))
+        assert abs(th - lam) <= 1e-10 * lam, (kind, n, th, lam)
+
+
+def test_lanczos_random_graph_vs_dense(oracle_mod):
+    n = 150
+    src, dst, w = random_graph(n, 900, 11)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    ev = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, dst, w)))
+    th = oracle_mod.lanczos_max(g, 80, np.random.default_rng(0).standard_normal(n))
+    assert abs(th - ev[-1]) <= 1e-9 * ev[-1]
+    # Ritz values never exceed the spectrum; lambda_hat brackets lambda_N
+    th5 = oracle_mod.lanczos_max(g, 5, np.random.default_rng(0).standard_normal(n))
+    assert th5 <= ev[-1] * (1 + 1e-12)
+    lh = oracle_mod.lambda_hat(th, oracle_mod.strength(g))
+    assert ev[-1] <= lh <= 2 * oracle_mod.strength(g).max() + 1e-12
+
+
+def test_tridiag_max_eig_vs_dense():
+    import oracle as O
+    rng = np.random.default_rng(5)
+    for k in (1, 2, 7, 30):
+        a = rng.standard_normal(k)
+        b = rng.standard_normal(max(k - 1, 0))
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        assert abs(O.tridiag_max_eig(a, b) - np.linalg.eigvalsh(T)[-1]) < 1e-12 * (1 + abs(a).max())
+
+
+# --------------------------------------------------------------------------
+# Coefficients of the ideal low-pass (2) in the Chebyshev basis
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("frac", [0.013, 0.2, 0.5, 0.77])
+def test_coeffs_match_projection_quadrature(oracle_mod, frac):
+    lam_max, p = 7.3, 25
+    lc = frac * lam_max
+    a = oracle_mod.cheb_coeffs(lam_max, lc, p, jackson=False)[0]
+    xc = 2 * lc / lam_max - 1
+    for j in range(p + 1):
+        # (2/pi) int_{-1}^{xc} T_j(x) (1-x)^(-1/2) (1+x)^(-1/2) dx; quad's
+        # algebraic weight handles the (1+x)^(-1/2) end point singularity
+        tj = np.polynomial.chebyshev.Chebyshev.basis(j)
+        val, _ = integrate.quad(lambda x: tj(x) / math.sqrt(1.0 - x), -1.0, xc, weight="alg",
+                                wvar=(-0.5, 0.0), limit=400, epsabs=1e-13, epsrel=1e-12)
+        ref = (2 / np.pi) * val * (0.5 if j == 0 else 1.0)
+        assert abs(a[j] - ref) < 1e-10, (j, a[j], ref)
+
+
+def test_coeffs_special_cases(oracle_mod):
+    p = 12
+    a = oracle_mod.cheb_coeffs(3.0, 3.0, p, jackson=True)[0]
+    np.testing.assert_allclose(a, np.eye(p + 1)[0], atol=1e-15)
+    a = oracle_mod.cheb_coeffs(3.0, 0.0, p, jackson=False)[0]
+    np.testing.assert_allclose(a, 0.0, atol=1e-15)
+    # cutoff at the middle: the step is odd about x = 0 plus 1/2, so even
+    # coefficients beyond a_0 vanish and a_0 = 1/2
+    a = oracle_mod.cheb_coeffs(3.0, 1.5, p, jackson=False)[0]
+    assert abs(a[0] - 0.5) < 1e-15
+    np.testing.assert_allclose(a[2::2], 0.0, atol=1e-15)
+    # h_lc(lambda) = 1 for lambda <= lc: at lambda = 0 (x = -1) the undamped
+    # series converges to 1 away from the cutoff
+    a = oracle_mod.cheb_coeffs(1.0, 0.6, 4000, jackson=False)[0]
+    assert abs(cheb_eval(a, -1.0) - 1.0) < 2e-3
+    assert abs(cheb_eval(a, 1.0)) < 2e-3
+
+
+def test_jackson_factors(oracle_mod):
+    for p in (1, 5, 50, 200):
+        g = oracle_mod.jackson(p)
+        assert abs(g[0] - 1.0) < 1e-14
+        assert abs(g[1] - math.cos(math.pi / (p + 2))) < 1e-14
+        assert np.all(np.diff(g) < 0) and g[-1] > 0
+
+
+@pytest.mark.parametrize("p", [10, 50, 200])
+def test_jackson_damped_step_stays_in_unit_interval(oracle_mod, p):
+    """The Jackson kernel is non-negative, so a damped [0, 1]-valued step
+    stays in [0, 1]; the undamped series overshoots (Gibbs)."""
+    x = np.linspace(-1, 1, 4001)
+    for lc in (0.05, 0.3, 0.61):
+        yd = cheb_eval(oracle_mod.cheb_coeffs(1.0, lc, p, True)[0], x)
+        assert yd.min() > -1e-12 and yd.max() < 1 + 1e-12
+        yu = cheb_eval(oracle_mod.cheb_coeffs(1.0, lc, p, False)[0], x)
+        assert yu.max() > 1.02
+
+
+# --------------------------------------------------------------------------
+# Fast filtering (3)/(6)/(11) against the exact spectral definition
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("jackson", [True, False])
+def test_filter_equals_dense_spectral_polynomial(oracle_mod, jackson):
+    n, n_sig, p = 70, 5, 33
+    src, dst, w = random_graph(n, 300, 21)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    L = dense_laplacian(dense_w(n, src, dst, w))
+    lam, chi = np.linalg.eigh(L)
+    lam_max = 1.01 * lam[-1]
+    R = np.random.default_rng(1).standard_normal((n, n_sig))
+    cut = [0.1 * lam_max, 0.45 * lam_max]
+    a = oracle_mod.cheb_coeffs(lam_max, cut, p, jackson)
+    Y = oracle_mod.cheb_filter(g, lam_max, a, R)
+    lt = 2 * lam / lam_max - 1
+    for q in range(2):
+        ref = chi @ (cheb_eval(a[q], lt)[:, None] * (chi.T @ R))
+        err = np.linalg.norm(Y[q] - ref) / np.linalg.norm(ref)
+        assert err < 1e-11, err
+
+
+def test_filter_p1_and_p2_closed_form(oracle_mod):
+    n = 30
+    src, dst, w = random_graph(n, 80, 4)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    L = dense_laplacian(dense_w(n, src, dst, w))
+    lam_max = 2.0 * np.abs(L).sum(axis=1).max()
+    Lt = 2 * L / lam_max - np.eye(n)
+    R = np.random.default_rng(2).standard_normal((n, 3))
+    a = np.array([[0.3, -0.7, 0.25]])
+    Y = oracle_mod.cheb_filter(g, lam_max, a, R)[0]
+    ref = 0.3 * R - 0.7 * Lt @ R + 0.25 * (2 * Lt @ Lt @ R - R)
+    np.testing.assert_allclose(Y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_projector_identity_and_truncation_error_shrinks(oracle_mod):
+    """(5): H_lk = U U^T; the polynomial filter approaches it as p grows
+    (measured outside a band around the cutoff, where the step is smooth)."""
+    k, m = 4, 30
+    n = k * m
+    rng = np.random.default_rng(8)
+    src, dst = [], []
+    for c in range(k):
+        for i in range(m):
+            for j in range(i + 1, m):
+                if rng.random() < 0.3:
+                    src.append(c * m + i); dst.append(c * m + j)
+    for _ in range(12):
+        a_, b_ = rng.integers(0, n, 2)
+        src.append(a_); dst.append(b_)
+    src, dst = np.array(src, np.int32), np.array(dst, np.int32)
+    W = dense_w(n, src, dst)
+    lam, chi = np.linalg.eigh(dense_laplacian(W))
+    U = chi[:, :k]
+    lc = 0.5 * (lam[k - 1] + lam[k])
+    H = chi @ np.diag((lam <= lc).astype(float)) @ chi.T
+    np.testing.assert_allclose(H, U @ U.T, atol=1e-10)
+    g = oracle_mod.csr_build(n, src, dst)
+    lam_max = 1.01 * lam[-1]
+    R = rng.standard_normal((n, 6))
+    band = 0.03 * lam_max
+    far = np.abs(lam - lc) > band
+    errs = []
+    for p in (10, 20, 40, 80, 160):
+        Y = oracle_mod.cheb_filter(g, lam_max, oracle_mod.cheb_coeffs(lam_max, lc, p, True), R)[0]
+        E = chi.T @ (Y - H @ R)
+        errs.append(np.linalg.norm(E[far]) / np.linalg.norm((chi.T @ (H @ R))[far] + 1e-300))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 0.05, errs
+
+
+def test_disconnected_components_give_constant_features(oracle_mod):
+    """§2.1: lambda_1 = 0 has one eigenvector per component (the indicator);
+    with lc below every component's lambda_2 the ideal filter is block-constant,
+    so normalised features are equal within each component."""
+    rng = np.random.default_rng(12)
+    sizes = [15, 22, 30]
+    src, dst, base = [], [], 0
+    for s in sizes:
+        for i in range(s):
+            for j in range(i + 1, s):
+                if rng.random() < 0.6:
+                    src.append(base + i); dst.append(base + j)
+        base += s
+    n = base
+    src, dst = np.array(src, np.int32), np.array(dst, np.int32)
+    W = dense_w(n, src, dst)
+    lam = np.linalg.eigvalsh(dense_laplacian(W))
+    assert np.sum(lam < 1e-9) == len(sizes)
+    lam2 = lam[len(sizes)]
+    lam_max = 1.01 * lam[-1]
+    g = oracle_mod.csr_build(n, src, dst)
+    a = oracle_mod.cheb_coeffs(lam_max, 0.5 * lam2, 300, True)
+    R = np.random.default_rng(3).standard_normal((n, 8)) / np.sqrt(8)
+    F = oracle_mod.features(oracle_mod.cheb_filter(g, lam_max, a, R)[0], True)
+    base = 0
+    for s in sizes:
+        blk = F[base:base + s]
+        assert np.abs(blk - blk.mean(axis=0)).max() < 2e-3
+        base += s
+
+
+# --------------------------------------------------------------------------
+# §3.2 eigenvalue count and dichotomy
+# --------------------------------------------------------------------------
+
+def test_eigencount_matches_expectation(oracle_mod):
+    n, eta, p = 120, 64, 60
+    src, dst, w = random_graph(n, 500, 31)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, dst, w)))
+    lam_max = 1.01 * lam[-1]
+    R = np.random.default_rng(4).standard_normal((n, eta)) / np.sqrt(eta)
+    cut = np.array([0.05, 0.2, 0.5]) * lam_max
+    a = oracle_mod.cheb_coeffs(lam_max, cut, p, True)
+    cnt = oracle_mod.eigencount(g, lam_max, a, R)
+    lt = 2 * lam / lam_max - 1
+    for q in range(3):
+        P = cheb_eval(a[q], lt)
+        mean = np.sum(P ** 2)
+        sd = math.sqrt(2 * np.sum(P ** 4) / eta)
+        assert abs(cnt[q] - mean) < 4 * sd, (q, cnt[q], mean, sd)
+        # and the count tracks the number of eigenvalues below the cutoff
+        assert abs(mean - np.sum(lam <= cut[q])) < 0.15 * n
+
+
+def test_moments_vs_dense_and_direct_count(oracle_mod):
+    n, eta, p = 60, 7, 20
+    src, dst, w = random_graph(n, 240, 41)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    lam, chi = np.linalg.eigh(dense_laplacian(dense_w(n, src, dst, w)))
+    lam_max = 1.01 * lam[-1]
+    R = np.random.default_rng(5).standard_normal((n, eta))
+    mu = oracle_mod.moments(g, lam_max, R, 2 * p)
+    lt = 2 * lam / lam_max - 1
+    Rh2 = np.sum((chi.T @ R) ** 2, axis=1)
+    for m in range(2 * p + 1):
+        ref = np.sum(Rh2 * np.cos(m * np.arccos(np.clip(lt, -1, 1))))
+        assert abs(mu[m] - ref) < 1e-10 * np.sum(Rh2)
+    a = oracle_mod.cheb_coeffs(lam_max, [0.1 * lam_max, 0.3 * lam_max], p, True)
+    direct = oracle_mod.eigencount(g, lam_max, a, R)
+    via = oracle_mod.count_from_moments(mu, a)
+    np.testing.assert_allclose(via, direct, rtol=1e-10)
+
+
+def test_dichotomy_on_disjoint_cliques(oracle_mod):
+    """k disjoint K_m: eigenvalues 0 (k times) and m. The dichotomy finds a
+    cutoff inside [0, m) whose count reaches k, and just below it the count
+    is below k."""
+    k, m, eta, p = 5, 8, 200, 80
+    src, dst = cliques_edges(k, m)
+    n = k * m
+    g = oracle_mod.csr_build(n, src, dst)
+    lam_max = 1.01 * m
+    R = np.random.default_rng(6).standard_normal((n, eta)) / np.sqrt(eta)
+    lk = oracle_mod.dichotomy(g, lam_max, p, R, k - 0.5, True, 40, 1e-9)
+    assert 0.0 < lk < m
+    a_hi = oracle_mod.cheb_coeffs(lam_max, lk, p, True)
+    a_lo = oracle_mod.cheb_coeffs(lam_max, lk - 2e-9 * lam_max, p, True)
+    assert oracle_mod.eigencount(g, lam_max, a_hi, R)[0] >= k - 0.5
+    assert oracle_mod.eigencount(g, lam_max, a_lo, R)[0] < k - 0.5
+
+
+# --------------------------------------------------------------------------
+# Features (6)/(11)
+# --------------------------------------------------------------------------
+
+def test_features(oracle_mod):
+    rng = np.random.default_rng(9)
+    Y = rng.standard_normal((50, 9))
+    Y[7] = 0.0
+    F = oracle_mod.features(Y, True)
+    nr = np.linalg.norm(F, axis=1)
+    np.testing.assert_allclose(np.delete(nr, 7), 1.0, rtol=1e-14)
+    assert np.all(F[7] == 0.0)
+    np.testing.assert_allclose(F * np.linalg.norm(Y, axis=1, keepdims=True), Y, rtol=1e-14, atol=1e-15)
+    np.testing.assert_array_equal(oracle_mod.features(Y, False), Y)
+
+
+def test_jl_proposition_distances(oracle_mod):
+    """Proposition of §3.1: with eta >= eta_0, all pairwise feature distances
+    are preserved within (1 +- eps) with probability >= 1 - N^-beta
+    (exact filter H_lk = U U^T on a small graph, fixed seed)."""
+    n, k = 40, 4
+    src, dst = cliques_edges(k, n // k)
+    rng = np.random.default_rng(14)
+    src = np.concatenate([src, rng.integers(0, n, 6)]).astype(np.int32)
+    dst = np.concatenate([dst, rng.integers(0, n, 6)]).astype(np.int32)
+    lam, chi = np.linalg.eigh(dense_laplacian(dense_w(n, src, dst)))
+    U = chi[:, :k]
+    eps, beta = 0.5, 1.0
+    eta0 = (4 + 2 * beta) / (eps ** 2 / 2 - eps ** 3 / 3) * math.log(n)
+    eta = int(math.ceil(eta0))
+    R = rng.standard_normal((n, eta)) / math.sqrt(eta)
+    Ft = (U @ U.T) @ R
+    f = U
+    i, j = np.triu_indices(n, 1)
+    d = np.sum((f[i] - f[j]) ** 2, axis=1)
+    dt = np.sum((Ft[i] - Ft[j]) ** 2, axis=1)
+    mask = d > 1e-12
+    ratio = dt[mask] / d[mask]
+    assert ratio.min() >= 1 - eps and ratio.max() <= 1 + eps
+
+
+# --------------------------------------------------------------------------
+# Reverse mode (adjoint) against central finite differences
+# --------------------------------------------------------------------------
+
+def test_backward_matches_finite_differences(oracle_mod):
+    n, n_sig, p = 14, 3, 7
+    src, dst, w = random_graph(n, 30, 51)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    s = oracle_mod.strength(g)
+    lam_max = 2.0 * s.max()
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal((n, n_sig))
+    G = rng.standard_normal((n, n_sig))
+    a = oracle_mod.cheb_coeffs(lam_max, 0.3 * lam_max, p, True)[0]
+    gv, ga, gR = oracle_mod.cheb_filter_backward(g, lam_max, a, R, G, want_grad_R=True)
+
+    def loss(val=None, a_=None, R_=None):
+        gg = oracle_mod.CSR(g.n, g.rowptr, g.colidx, g.val if val is None else val)
+        return float(np.sum(G * oracle_mod.cheb_filter(gg, lam_max, a if a_ is None else a_,
+                                                        R if R_ is None else R_)[0]))
+
+    h = 1e-6
+    # each undirected edge: perturb both stored directions together
+    checked = 0
+    for u in range(n):
+        for e in range(g.rowptr[u], g.rowptr[u + 1]):
+            v = g.colidx[e]
+            if v < u:
+                continue
+            f = [ff for ff in range(g.rowptr[v], g.rowptr[v + 1]) if g.colidx[ff] == u][0]
+            vp, vm = g.val.copy(), g.val.copy()
+            vp[e] += h; vp[f] += h; vm[e] -= h; vm[f] -= h
+            fd = (loss(val=vp) - loss(val=vm)) / (2 * h)
+            assert abs(fd - gv[e]) <= 1e-6 * max(1.0, abs(fd)), (u, v, fd, gv[e])
+            assert abs(gv[e] - gv[f]) <= 1e-13 * max(1.0, abs(gv[e]))
+            checked += 1
+    assert checked > 10
+    for j in range(p + 1):
+        ap, am = a.copy(), a.copy()
+        ap[j] += h; am[j] -= h
+        fd = (loss(a_=ap) - loss(a_=am)) / (2 * h)
+        assert abs(fd - ga[j]) <= 1e-6 * max(1.0, abs(fd))
+    for (i, r) in [(0, 0), (5, 2), (13, 1)]:
+        Rp, Rm = R.copy(), R.copy()
+        Rp[i, r] += h; Rm[i, r] -= h
+        fd = (loss(R_=Rp) - loss(R_=Rm)) / (2 * h)
+        assert abs(fd - gR[i, r]) <= 1e-6 * max(1.0, abs(fd))
