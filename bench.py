@@ -1,0 +1,405 @@
+"""Benchmark: filtered nnz*R*p updates/s of the accelerated-spectral-clustering
+hot path on one GB300 (or N GPUs, one process each).
+
+One step = one pass of the whole path over one batch of synthetic input
+(a seeded stochastic-block-model graph and a block of random signals already
+resident in device memory):
+  CSR build from the edge list -> lambda_N by Lanczos (40 steps) ->
+  moment sweep (p orders, FP32 blocks) -> dichotomy for lambda_k ->
+  coefficients -> filter sweep (p orders, storage per workload) ->
+  row-normalised features.
+Updates counted per step: (nnz_off + N) * R * p for each of the two sweeps.
+
+Default workload ("sbm1m"): N = 1,000,000, k = 100 equal communities, mean
+degree 30, c_out/c_in = 0.08, unit weights, R = 128 signals, p = 200, filter
+blocks stored in BF16 with FP32 accumulation; the same step with FP32 blocks
+is timed beside it. Inputs (graph 0.25 GB CSR, blocks 0.5 GB) are larger
+than L2, so no flush is needed between steps.
+
+--impl reference times the CPU FP64 oracle (the correctness reference; there
+is no other implementation) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, k, mean degree, eps, R, p, storage)
+    "sbm1m": dict(n=1_000_000, k=100, deg=30.0, eps=0.08, R=128, p=200, storage="bf16", graph_seed=1003,
+                  r_seed=2003),
+    "sbm100k": dict(n=100_000, k=20, deg=20.0, eps=0.1, R=64, p=100, storage="f32", graph_seed=1002, r_seed=2002,
+                    sizes=(2000, 8000)),
+    "sbm1k": dict(n=1000, k=10, deg=16.0, eps=0.05, R=14, p=50, storage="f32", graph_seed=1001, r_seed=2001),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sbm1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    return ap.parse_args()
+
+
+def make_inputs(wl, rank=0):
+    from paper_1509_08863_gb300 import synth
+
+    if "sizes" in wl:
+        sizes = synth.community_sizes_uniform(wl["n"], wl["k"], wl["sizes"][0], wl["sizes"][1], wl["graph_seed"])
+    else:
+        sizes = synth.community_sizes_equal(wl["n"], wl["k"])
+    gr = synth.sbm_edges(wl["n"], sizes, wl["deg"], wl["eps"], seed=wl["graph_seed"])
+    R = synth.standard_normal_block(wl["n"], wl["R"], seed=wl["r_seed"] + 7919 * rank)
+    R /= np.sqrt(wl["R"])
+    return gr, R
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("sf_step.cuh", "sf_cheb.cu"):
+        with open(os.path.join(ROOT, "paper_1509_08863_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"cheb_step_{workload}_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha") == kernel_source_hash():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, wl):
+    import oracle
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    gr, R = make_inputs(wl)
+    g = oracle.csr_build(wl["n"], gr.src, gr.dst, gr.w)
+    lam = 2.0 * float(oracle.strength(g).max())
+    p_ref = 4 if wl["n"] >= 500_000 else max(1, min(wl["p"], 20))
+    a = oracle.cheb_coeffs(lam, 0.1 * lam, p_ref, True)
+    col = np.ascontiguousarray(R[:, :1])
+    units = (g.nnz + wl["n"]) * 1 * p_ref
+    for _ in range(args.warmup):
+        oracle.cheb_filter(g, lam, a, col)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.cheb_filter(g, lam, a, col)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    v = units / t
+    sample = f"1 of {wl['R']} signal columns, all {wl['n']} nodes, {p_ref} Chebyshev orders (oracle_cheb_filter)"
+    out = {
+        "impl": "reference",
+        "metric": "filtered nnz*R*p updates/s",
+        "value": v,
+        "unit": "updates/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": wl["n"], "R": wl["R"], "p": wl["p"], "k": wl["k"],
+                   "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"]},
+        "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    import paper_1509_08863_gb300 as sf
+    from paper_1509_08863_gb300 import build as sfbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+    if rank == 0:
+        sfbuild.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    gr, R = make_inputs(wl, rank)
+    n, eta, p, k = wl["n"], wl["R"], wl["p"], wl["k"]
+    storage = sf.BF16 if wl["storage"] == "bf16" else sf.F32
+    src_h = torch.from_numpy(gr.src).pin_memory()
+    dst_h = torch.from_numpy(gr.dst).pin_memory()
+    R_h = torch.from_numpy(R.astype(np.float32)).pin_memory()
+    src_d, dst_d, R_d = src_h.to(dev), dst_h.to(dev), R_h.to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(src, dst, Rt, st, collect=None):
+        g = sf.csr_build(n, src, dst, None)
+        _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
+        mu = sf.cheb_moments(g, lh, Rt, p, sf.Opts(storage=sf.F32))
+        if dist:
+            t = torch.as_tensor(mu, device=dev)
+            dist.all_reduce(t)
+            mu = t.cpu().numpy()
+        lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
+        a = sf.cheb_coeffs(lh, lk, p, True)
+        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW))[0]
+        F = sf.features(Y, True, out=Y)
+        if collect is not None:
+            collect.update(lam_hat=lh, lam_k=lk, nnz=g.nnz, Y=Y)
+        g.free()
+        return F
+
+    info = {}
+    F = step(src_d, dst_d, R_d, storage, info)
+    torch.cuda.synchronize()
+    nnz = info["nnz"]
+    updates = 2.0 * (nnz + n) * eta * p
+
+    def timed(st, steps, warmup, e2e=False):
+        for _ in range(warmup):
+            if e2e:
+                out = step(src_h.to(dev, non_blocking=True), dst_h.to(dev, non_blocking=True),
+                           R_h.to(dev, non_blocking=True), st)
+                out.cpu()
+            else:
+                step(src_d, dst_d, R_d, st)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        host_out = torch.empty((n, eta), dtype=torch.float32).pin_memory() if e2e else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = sf.launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            if e2e:
+                out = step(src_h.to(dev, non_blocking=True), dst_h.to(dev, non_blocking=True),
+                           R_h.to(dev, non_blocking=True), st)
+                host_out.copy_(out, non_blocking=True)
+            else:
+                step(src_d, dst_d, R_d, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = sf.launch_count() - l0
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches
+
+    # main timed region (device-resident inputs) with kernel timing and clocks
+    clk = ClockSampler(local if world == 1 else int(os.environ.get("LOCAL_RANK", "0")))
+    for _ in range(args.warmup):
+        step(src_d, dst_d, R_d, storage)
+    torch.cuda.synchronize()
+    clk.start()
+    sf.profile_begin()
+    ms, launches = timed(storage, args.steps, 0)
+    k_launches, k_ms, k_bytes = sf.profile_end()
+    clocks = clk.stop()
+    value = updates * world / (ms * 1e-3)
+
+    # the same step with FP32 blocks in the filter (moment sweep is FP32 in both)
+    fp32 = None
+    if storage != sf.F32 and not args.no_fp32:
+        ms32, _ = timed(sf.F32, max(3, args.steps // 2), 1)
+        fp32 = {"value": updates * world / (ms32 * 1e-3), "ms_per_step": ms32,
+                "speedup_of_storage": ms32 / ms}
+    # end to end from pinned host buffers, features copied back
+    e2e = None
+    if not args.no_e2e:
+        mse, _ = timed(storage, max(3, args.steps // 2), 1, e2e=True)
+        e2e = {"value": updates * world / (mse * 1e-3), "unit": "updates/s",
+               "h2d_bytes_per_step": int(src_h.numel() * 4 + dst_h.numel() * 4 + R_h.numel() * 4),
+               "d2h_bytes_per_step": int(n * eta * 4)}
+
+    # accuracy of this step's features/filter against the FP64 oracle on one column
+    hbm, peak_kind = peaks()
+    kernel_gbs = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": kernel_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": kernel_gbs / hbm, "traffic": traffic_from_profile(args.workload),
+            "kernel": "cheb_step_kernel", "launches_timed": k_launches,
+            "avg_launch_ms": k_ms / max(k_launches, 1), "bytes_per_launch": k_bytes / max(k_launches, 1),
+            "peak_source": f"{peak_kind} hbm_gbs"}
+
+    result = {
+        "metric": "filtered nnz*R*p updates/s",
+        "value": value,
+        "unit": "updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "N": n, "nnz_off": nnz, "R": eta, "p": p, "k": k,
+                   "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
+                   "filter_storage": wl["storage"], "moment_storage": "f32", "algo": "clenshaw",
+                   "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"column-shard x{world}" if world > 1 else "single GPU"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "fp32_storage": fp32,
+        "lam_hat": info["lam_hat"],
+        "lam_k_estimate": info["lam_k"],
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"], result["accuracy"] = cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev)
+    if rank == 0:
+        print(json.dumps(result))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev):
+    """Time the oracle on one signal column of the same graph and p, and use
+    its output to measure the GPU filter's error on that column."""
+    import torch
+
+    import oracle
+
+    n, p = wl["n"], wl["p"]
+    g = oracle.csr_build(n, gr.src, gr.dst, gr.w)
+    lh, lk = info["lam_hat"], info["lam_k"]
+    a = oracle.cheb_coeffs(lh, lk, p, True)
+    col = np.ascontiguousarray(R[:, :1])
+    t0 = time.perf_counter()
+    Yo = oracle.cheb_filter(g, lh, a, col)[0][:, 0]
+    dt = time.perf_counter() - t0
+    cpu = {"value": (g.nnz + n) * p / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
+           "sample": f"1 of {wl['R']} signal columns, all {n} nodes, p={p} (oracle_cheb_filter, FP64, 1 thread)",
+           "seconds": dt}
+    # GPU filter outputs (FP32 and the workload's storage) on the same column
+    gg = sf.csr_build(n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device=dev)
+    acc = {}
+    rows = np.random.default_rng(5).choice(n, size=min(50_000, n), replace=False)
+    for name, st in (("f32", sf.F32), ("bf16", sf.BF16)):
+        Y = sf.cheb_filter(gg, lh, a, Rt, sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW))[0][:, 0].cpu().numpy()
+        acc[name] = {
+            "rel_fro_all_rows": float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),
+            "rel_fro_50k_rows": float(np.linalg.norm(Y[rows] - Yo[rows]) / np.linalg.norm(Yo[rows])),
+        }
+    gg.free()
+    acc["reference"] = "FP64 oracle, column 0, same lam_hat and coefficients"
+    return cpu, acc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,329 @@
+/*
+ * specfilt.h -- C ABI of the GB300 graph-filtering library (libspecfilt.so).
+ *
+ * The library computes the hot path of accelerated spectral clustering by
+ * graph filtering of random signals (Tremblay, Puy, Borgnat, Gribonval,
+ * Vandergheynst): a polynomial approximation of the ideal low-pass filter of
+ * Eq. (2) applied by repeated sparse products with the Laplacian L = S - W
+ * (§2.1, §2.4 Eq. (3)) to a block R of random signals (§3.1), the
+ * eigenvalue count and dichotomy built on it (§3.2), the largest-eigenvalue
+ * estimate it needs (§4.1 step 1) and the feature rows it yields (Eq. (6),
+ * Eq. (11)). The polynomial is expanded in the Chebyshev basis of
+ * Lt = (2 / lam_max) L - I, so every filter order is one sparse-times-dense
+ * product T_j = 2 Lt T_{j-1} - T_{j-2}.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: SF_OK (0) or an error status; nothing is thrown.
+ *     sf_last_error() gives a message for the calling thread's last failure.
+ *   - Pointers documented "device" are CUDA device (or managed) memory on
+ *     the current device; "host" pointers are ordinary CPU memory.
+ *   - Ownership: the caller owns every buffer it passes. Objects the library
+ *     creates (sf_graph, sf_batch) are freed with their *_free function.
+ *     Internal work buffers are stream-ordered allocations released before
+ *     the call returns or at the end of its stream work.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless they return host values,
+ *     in which case they synchronise it before returning (stated per call).
+ *   - Layouts: signal blocks are row-major N x n_sig (one row per node,
+ *     signals contiguous); coefficient tables are row-major
+ *     [n_cut][p + 1]; graphs are CSR with int32 indices and fp32 weights.
+ *   - Errors from bad arguments leave outputs untouched. A CUDA failure
+ *     returns SF_ERR_CUDA and leaves outputs undefined.
+ */
+#ifndef SPECFILT_H
+#define SPECFILT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SF_API __attribute__((visibility("default")))
+#else
+#define SF_API
+#endif
+
+/* Status codes. */
+enum {
+    SF_OK = 0,
+    SF_ERR_ARG = 1,      /* invalid argument (sizes, pointers, graph content) */
+    SF_ERR_CUDA = 2,     /* a CUDA runtime call or kernel failed */
+    SF_ERR_OOM = 3,      /* device allocation failed */
+    SF_ERR_TIMEOUT = 4,  /* a bounded device wait gave up */
+    SF_ERR_NUMERIC = 5   /* non-finite value detected where a finite one is required */
+};
+typedef int32_t sf_status;
+
+/* Element types of signal blocks. */
+enum { SF_F32 = 0, SF_BF16 = 1, SF_F16 = 2 };
+
+/* Filter algorithms. */
+enum {
+    SF_ALGO_AUTO = 0,     /* forward recurrence for several cutoffs, Clenshaw for one */
+    SF_ALGO_FORWARD = 1,  /* T_j blocks forward, Y_c += a_cj T_j for every cutoff c */
+    SF_ALGO_CLENSHAW = 2  /* backward Clenshaw sum, one cutoff at a time */
+};
+
+/*
+ * Tuning and precision options; a NULL sf_opts* means all zero (defaults).
+ *   storage         SF_F32 / SF_BF16 / SF_F16: element type of the T_j (or
+ *                   Clenshaw b_j) blocks kept between orders. Products and
+ *                   accumulations are FP32 in every case; the output Y is FP32.
+ *                   SF_F16 stores each order scaled by a power of two chosen
+ *                   from the previous order's largest magnitude.
+ *   algo            SF_ALGO_*.
+ *   slab_cols       signal columns processed per sweep (0 = automatic). The
+ *                   signals are independent, so the block is filtered in
+ *                   column slabs whose gathered operand fits in L2.
+ *   block_warps     warps per thread block of the sweep kernel (0 = automatic).
+ *   blocks_per_sm   resident blocks per SM of the persistent sweep grid (0 = max).
+ *   ckpt_every      adjoint only: 0 = automatic (store every T_j when it fits
+ *                   under mem_cap_mb, else checkpoint), 1 = store all, k > 1 =
+ *                   keep every k-th pair of blocks and recompute the rest.
+ *   mem_cap_mb      adjoint only: memory budget for stored T_j blocks (0 = 16384).
+ */
+typedef struct sf_opts {
+    int32_t storage;
+    int32_t algo;
+    int32_t slab_cols;
+    int32_t block_warps;
+    int32_t blocks_per_sm;
+    int32_t ckpt_every;
+    int64_t mem_cap_mb;
+} sf_opts;
+
+typedef struct sf_graph sf_graph; /* device-resident CSR of W, owned by the library */
+typedef struct sf_batch sf_batch; /* block-diagonal concatenation of several graphs */
+
+/* ---------------------------------------------------------------------- */
+/* Status helpers                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Static text for a status code. */
+SF_API const char *sf_status_str(sf_status s);
+/* Message describing the calling thread's most recent failure ("" if none). */
+SF_API const char *sf_last_error(void);
+/* ABI version (major * 100 + minor). */
+SF_API int32_t sf_version(void);
+/* Number of CUDA kernels this library has launched in this process. */
+SF_API int64_t sf_launch_count(void);
+
+/* ---------------------------------------------------------------------- */
+/* Graph construction (§2: W_ij = W_ji >= 0; §2.1: s_i = sum_{j != i} W_ij) */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Build the symmetric CSR of W from an undirected edge list.
+ *   n_nodes   number of nodes N (>= 1)
+ *   n_edges   number of listed edges m (>= 0); 2 m must be < 2^31
+ *   src, dst  device int32[m], endpoints in [0, N)
+ *   w         device float[m], weights (finite, >= 0), or NULL for all 1
+ * Each edge (u, v, w) with u != v yields W_uv and W_vu; self-loops are
+ * dropped (the strength of §2.1 excludes j = i); repeated pairs keep the
+ * largest weight. Columns are sorted within each row, so the result is
+ * bit-identical for any order of the edge list. Also computes the strengths
+ * s_i (FP64) and whether every stored weight equals 1.
+ * Synchronises `stream` (the entry count must be known). Errors: SF_ERR_ARG
+ * for an endpoint out of range or a negative / non-finite weight.
+ */
+SF_API sf_status sf_csr_build(int32_t n_nodes, int64_t n_edges, const int32_t *src, const int32_t *dst,
+                              const float *w, void *stream, sf_graph **out);
+
+/* Sizes: N, stored off-diagonal entries, and 1 when every weight is 1. Host outputs, any may be NULL. */
+SF_API sf_status sf_graph_info(const sf_graph *g, int32_t *n, int64_t *nnz_off, int32_t *unit_weights,
+                               double *max_strength);
+
+/* Borrowed device views of the CSR (valid until sf_graph_free); any may be NULL. */
+SF_API sf_status sf_graph_csr(const sf_graph *g, const int32_t **rowptr, const int32_t **colidx,
+                              const float **val, const double **strength);
+
+/*
+ * Replace the stored weights (same pattern) and recompute strengths.
+ *   val  device float[nnz_off] in CSR order; must be symmetric (W_uv = W_vu)
+ *        and >= 0 -- the symmetry is the caller's contract, not checked.
+ * Synchronises `stream` (the largest strength is read back).
+ */
+SF_API sf_status sf_graph_set_values(sf_graph *g, const float *val, void *stream);
+
+SF_API void sf_graph_free(sf_graph *g);
+
+/* ---------------------------------------------------------------------- */
+/* lambda_N (§4.1 step 1)                                                  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Largest Laplacian eigenvalue estimate by `iters` Lanczos steps in FP64 on
+ * the device (no re-orthogonalisation; the largest Ritz value is unaffected
+ * by the loss of orthogonality), the tridiagonal solved on the host.
+ *   v0        device double[N] start vector, or NULL to draw one from the
+ *             SplitMix64 sequence seeded by `seed` (uniform in [-1, 1))
+ *   theta_max host out: largest Ritz value (<= lambda_N)
+ *   lam_hat   host out: min(1.01 * theta_max, 2 * max_i s_i), the value the
+ *             filters should use (1 for an edgeless graph)
+ * Synchronises `stream`.
+ */
+SF_API sf_status sf_lambda_max_estimate(const sf_graph *g, int32_t iters, const double *v0, uint64_t seed,
+                                        void *stream, double *theta_max, double *lam_hat);
+
+/* ---------------------------------------------------------------------- */
+/* Coefficients of the ideal low-pass Eq. (2) (host, FP64)                 */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Chebyshev coefficients of h_lc on [0, lam_max] for each cutoff:
+ * coeffs[c][0] = 1 - theta_c / pi, coeffs[c][j] = -2 sin(j theta_c) / (pi j),
+ * theta_c = arccos(clamp(2 lc / lam_max - 1, -1, 1)); with jackson != 0 each
+ * term is multiplied by the Jackson factor g_j of a degree-p expansion.
+ *   cutoffs host double[n_cut]; coeffs host double[n_cut][p + 1].
+ */
+SF_API sf_status sf_cheb_coeffs(double lam_max, const double *cutoffs, int32_t n_cut, int32_t p,
+                                int32_t jackson, double *coeffs);
+
+/* ---------------------------------------------------------------------- */
+/* Fast filtering of random signals (§2.4 Eq. (3), §3.1 Eq. (6), §4.1 step 5) */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Y_c = sum_{j=0}^{p} coeffs[c][j] T_j(Lt) R for c = 0..n_cut-1.
+ *   lam_max  the lam_hat used for Lt (> 0)
+ *   coeffs   host double[n_cut][p + 1] (p >= 0, 1 <= n_cut <= 64)
+ *   R        device N x n_sig block, element type r_dtype (SF_F32 or SF_BF16)
+ *   Y        device float[n_cut][N][n_sig]
+ * Asynchronous on `stream`.
+ */
+SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double *coeffs, int32_t n_cut,
+                                int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                const sf_opts *opts, void *stream);
+
+/*
+ * Chebyshev moments mu_m = <R, T_m(Lt) R>_F, m = 0..2p, from one sweep of p
+ * orders: mu_{2j} = 2 <T_j R, T_j R> - mu_0 and
+ * mu_{2j-1} = 2 <T_j R, T_{j-1} R> - mu_1 (products of Chebyshev
+ * polynomials). Per-row partial sums in FP32, everything across rows in
+ * FP64 with a fixed reduction order (deterministic).
+ *   moments host double[2p + 1]. Synchronises `stream`.
+ */
+SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *R, int32_t r_dtype,
+                                 int32_t n_sig, int32_t p, double *moments, const sf_opts *opts,
+                                 void *stream);
+
+/*
+ * Eigenvalue count of §3.2 from moments (host, FP64):
+ * counts[c] = sum_{j,j'} a_cj a_cj' (mu_{j+j'} + mu_{|j-j'|}) / 2, i.e. the
+ * squared Frobenius norm of the filtered block. moments: host double[2p + 1].
+ */
+SF_API sf_status sf_count_from_moments(const double *moments, int32_t p, const double *coeffs,
+                                       int32_t n_cut, double *counts);
+
+/*
+ * sf_cheb_moments followed by coefficients (with or without Jackson
+ * damping) and counts for every cutoff. counts: host double[n_cut];
+ * moments_out: host double[2p + 1] or NULL. Synchronises `stream`.
+ */
+SF_API sf_status sf_eigencount(const sf_graph *g, double lam_max, const void *R, int32_t r_dtype,
+                               int32_t n_sig, int32_t p, const double *cutoffs, int32_t n_cut,
+                               int32_t jackson, double *counts, double *moments_out, const sf_opts *opts,
+                               void *stream);
+
+/*
+ * Dichotomy of §3.2 on [0, lam_max] (host, FP64, on moments -- no GPU work):
+ * the smallest cutoff whose count reaches k, by bisection stopped after
+ * max_iter halvings or when the bracket is below tol * lam_max; returns the
+ * bracket's upper end in *lam_k.
+ */
+SF_API sf_status sf_dichotomy(const double *moments, int32_t p, double lam_max, double k, int32_t jackson,
+                              int32_t max_iter, double tol, double *lam_k);
+
+/*
+ * Feature rows f~_i (Eq. (6), Eq. (11)): F = Y, or with normalize != 0 each
+ * row divided by its Euclidean norm (norm in FP64; all-zero rows stay zero).
+ *   Y, F  device float[N][n_sig] (F may alias Y). Asynchronous.
+ */
+SF_API sf_status sf_features(const float *Y, int32_t n, int32_t n_sig, int32_t normalize, float *F,
+                             void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Adjoint (reverse mode) of the filter                                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Gradients of l = <G, Y>_F for Y = sum_j coeffs[j] T_j(Lt) R (one cutoff),
+ * lam_max held fixed:
+ *   grad_val     device float[nnz_off]: dl/dW_uv for the undirected edge of
+ *                each stored entry (both directions carry the same value),
+ *                = (2 / lam_max)(M_uu + M_vv - M_uv - M_vu), with
+ *                M = Gb_1 T_0^T + sum_{j>=2} 2 Gb_j T_{j-1}^T on the pattern
+ *   grad_coeffs  host double[p + 1]: <G, T_j R>  (may be NULL)
+ *   grad_R       device float[N][n_sig]: sum_j coeffs[j] T_j(Lt) G (may be NULL)
+ * Gb_j run the Clenshaw recurrence on G top-down (Lt is symmetric). T_j
+ * blocks are stored or recomputed from checkpoints per opts (ckpt_every,
+ * mem_cap_mb). G and R are FP32. Synchronises `stream` when grad_coeffs
+ * is non-NULL.
+ */
+SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double lam_max, const double *coeffs, int32_t p,
+                                         const float *R, int32_t n_sig, const float *G, float *grad_val,
+                                         double *grad_coeffs, float *grad_R, const sf_opts *opts,
+                                         void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Many graphs in one sweep                                                */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Concatenate graphs into one block-diagonal CSR (node ids offset by the
+ * preceding graphs' sizes). The source graphs may be freed afterwards.
+ * Synchronises `stream`.
+ */
+SF_API sf_status sf_batch_build(const sf_graph *const *graphs, int32_t n_graphs, void *stream,
+                                sf_batch **out);
+
+/* Total nodes, total stored entries, number of graphs; row offsets host int32[n_graphs + 1] (may be NULL). */
+SF_API sf_status sf_batch_info(const sf_batch *b, int32_t *n_total, int64_t *nnz_total, int32_t *n_graphs,
+                               int32_t *row_offsets);
+
+SF_API void sf_batch_free(sf_batch *b);
+
+/*
+ * Filter every graph of the batch with its own lam_max and coefficients in
+ * one sweep per order (one kernel launch per order covers all graphs).
+ *   lam_max  host double[n_graphs]
+ *   coeffs   host double[n_graphs][p + 1]
+ *   R, Y     device blocks of sum(N_g) rows x n_sig, graph g's rows at its
+ *            row offset; R of type r_dtype, Y float.
+ * Asynchronous on `stream`.
+ */
+SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
+                                        int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                        const sf_opts *opts, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Tile autotuner and kernel timing                                        */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Time candidate tile shapes (slab width, warps per block, blocks per SM) of
+ * the sweep kernel on this graph for n_sig signals and the given storage
+ * type, a few orders each, and write the fastest into *best (other fields
+ * copied from *base, which may be NULL). Results are cached per
+ * (N, nnz, n_sig, storage, n_cut) in the process. Synchronises `stream`.
+ */
+SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, int32_t n_cut,
+                             const sf_opts *base, void *stream, sf_opts *best);
+
+/*
+ * Kernel timing of the sweep kernel: after sf_profile_begin(), every launch
+ * of the per-order sweep kernel is bracketed by CUDA events on its stream.
+ * sf_profile_end() synchronises those events and returns the number of
+ * timed launches, their summed duration (ms) and their summed algorithmic
+ * bytes (compulsory traffic: CSR once, gathered rows once, streamed blocks).
+ */
+SF_API sf_status sf_profile_begin(void);
+SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPECFILT_H */

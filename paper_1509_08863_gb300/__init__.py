@@ -1,0 +1,484 @@
+"""GB300 graph filtering of random signals for accelerated spectral clustering.
+
+Thin Python binding over the C ABI of ``libspecfilt.so`` (declared in
+``include/specfilt.h``). Every step of the path runs in the library's CUDA
+kernels; this module only marshals arguments: PyTorch supplies device memory
+and the current CUDA stream, numpy carries small host tables (coefficients,
+moments, counts).
+
+The library must be built (``paper_1509_08863_gb300.build.build()``); if it
+is missing every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "SpecFiltError",
+    "Opts",
+    "Graph",
+    "Batch",
+    "lib",
+    "csr_build",
+    "lambda_max_estimate",
+    "cheb_coeffs",
+    "cheb_filter",
+    "cheb_moments",
+    "count_from_moments",
+    "eigencount",
+    "dichotomy",
+    "features",
+    "cheb_filter_backward",
+    "batch_build",
+    "cheb_filter_batched",
+    "autotune",
+    "profile_begin",
+    "profile_end",
+    "launch_count",
+    "ChebFilter",
+    "F32",
+    "BF16",
+    "ALGO_AUTO",
+    "ALGO_FORWARD",
+    "ALGO_CLENSHAW",
+]
+
+F32, BF16, F16 = 0, 1, 2
+ALGO_AUTO, ALGO_FORWARD, ALGO_CLENSHAW = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspecfilt.so")
+_lib = None
+
+
+class SpecFiltError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status}: {detail}")
+
+
+class _Opts(C.Structure):
+    _fields_ = [
+        ("storage", C.c_int32),
+        ("algo", C.c_int32),
+        ("slab_cols", C.c_int32),
+        ("block_warps", C.c_int32),
+        ("blocks_per_sm", C.c_int32),
+        ("ckpt_every", C.c_int32),
+        ("mem_cap_mb", C.c_int64),
+    ]
+
+
+@dataclass
+class Opts:
+    """Mirror of ``sf_opts`` (zeros mean automatic)."""
+
+    storage: int = F32
+    algo: int = ALGO_AUTO
+    slab_cols: int = 0
+    block_warps: int = 0
+    blocks_per_sm: int = 0
+    ckpt_every: int = 0
+    mem_cap_mb: int = 0
+
+    def c(self) -> _Opts:
+        return _Opts(self.storage, self.algo, self.slab_cols, self.block_warps, self.blocks_per_sm,
+                      self.ckpt_every, self.mem_cap_mb)
+
+
+_vp = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+_f64 = C.c_double
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libspecfilt.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise SpecFiltError(-1, "load", f"{LIB_PATH} is missing; build it with paper_1509_08863_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "sf_status_str": (C.c_char_p, [_i32]),
+        "sf_last_error": (C.c_char_p, []),
+        "sf_version": (_i32, []),
+        "sf_launch_count": (_i64, []),
+        "sf_csr_build": (_i32, [_i32, _i64, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+        "sf_graph_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i32), _dp]),
+        "sf_graph_csr": (_i32, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
+        "sf_graph_set_values": (_i32, [_vp, _vp, _vp]),
+        "sf_graph_free": (None, [_vp]),
+        "sf_lambda_max_estimate": (_i32, [_vp, _i32, _vp, C.c_uint64, _vp, _dp, _dp]),
+        "sf_cheb_coeffs": (_i32, [_f64, _dp, _i32, _i32, _i32, _dp]),
+        "sf_cheb_filter": (_i32, [_vp, _f64, _dp, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
+        "sf_cheb_moments": (_i32, [_vp, _f64, _vp, _i32, _i32, _i32, _dp, C.POINTER(_Opts), _vp]),
+        "sf_count_from_moments": (_i32, [_dp, _i32, _dp, _i32, _dp]),
+        "sf_eigencount": (_i32, [_vp, _f64, _vp, _i32, _i32, _i32, _dp, _i32, _i32, _dp, _dp, C.POINTER(_Opts),
+                                 _vp]),
+        "sf_dichotomy": (_i32, [_dp, _i32, _f64, _f64, _i32, _i32, _f64, _dp]),
+        "sf_features": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp]),
+        "sf_cheb_filter_backward": (_i32, [_vp, _f64, _dp, _i32, _vp, _i32, _vp, _vp, _dp, _vp,
+                                           C.POINTER(_Opts), _vp]),
+        "sf_batch_build": (_i32, [C.POINTER(_vp), _i32, _vp, C.POINTER(_vp)]),
+        "sf_batch_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32)]),
+        "sf_batch_free": (None, [_vp]),
+        "sf_cheb_filter_batched": (_i32, [_vp, _dp, _dp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
+        "sf_autotune": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_Opts), _vp, C.POINTER(_Opts)]),
+        "sf_profile_begin": (_i32, []),
+        "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        L = lib()
+        raise SpecFiltError(st, where, L.sf_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, name="tensor"):
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f64arr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _rdtype(R):
+    torch = _torch()
+    if R.dtype == torch.float32:
+        return F32
+    if R.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"R must be float32 or bfloat16, got {R.dtype}")
+
+
+def _opts_ptr(opts):
+    if opts is None:
+        return None, None
+    o = opts.c() if isinstance(opts, Opts) else opts
+    return o, C.byref(o)
+
+
+class _DevView:
+    """__cuda_array_interface__ over a borrowed device pointer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+class Graph:
+    """Device CSR of W owned by the library (§2, §2.1)."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, nnz, unit, smax = _i32(), _i64(), _i32(), _f64()
+        _check(lib().sf_graph_info(self._h, C.byref(n), C.byref(nnz), C.byref(unit), C.byref(smax)), "sf_graph_info")
+        return n.value, nnz.value, bool(unit.value), smax.value
+
+    @property
+    def n(self):
+        return self.info()[0]
+
+    @property
+    def nnz(self):
+        return self.info()[1]
+
+    def csr(self):
+        """Copies (torch CUDA tensors) of rowptr, colidx, val, strength."""
+        torch = _torch()
+        n, nnz, _, _ = self.info()
+        rp, ci, va, st = _vp(), _vp(), _vp(), _vp()
+        _check(lib().sf_graph_csr(self._h, C.byref(rp), C.byref(ci), C.byref(va), C.byref(st)), "sf_graph_csr")
+        torch.cuda.synchronize()
+
+        def view(ptr, shape, ts, dt):
+            if shape[0] == 0 or not ptr.value:
+                return torch.zeros(shape, dtype=dt, device="cuda")
+            return torch.as_tensor(_DevView(ptr.value, shape, ts), device="cuda").clone()
+
+        return (view(rp, (n + 1,), "<i4", torch.int32), view(ci, (nnz,), "<i4", torch.int32),
+                view(va, (nnz,), "<f4", torch.float32), view(st, (n,), "<f8", torch.float64))
+
+    def set_values(self, val):
+        torch = _torch()
+        _check(lib().sf_graph_set_values(self._h, _dev_ptr(val, torch.float32, "val"), _stream()),
+               "sf_graph_set_values")
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().sf_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def csr_build(n: int, src, dst, w=None) -> Graph:
+    """Symmetric CSR of W from an undirected edge list (int32 src/dst, float32 w on the GPU)."""
+    torch = _torch()
+    m = int(src.shape[0])
+    out = _vp()
+    _check(lib().sf_csr_build(int(n), m, _dev_ptr(src, torch.int32, "src"), _dev_ptr(dst, torch.int32, "dst"),
+                              _dev_ptr(w, torch.float32, "w") if w is not None else None, _stream(),
+                              C.byref(out)), "sf_csr_build")
+    return Graph(out.value)
+
+
+def lambda_max_estimate(g: Graph, iters: int = 40, v0=None, seed: int = 0):
+    """(theta_max, lam_hat): Lanczos Ritz value and the bound used by the filters (§4.1 step 1)."""
+    torch = _torch()
+    th, lh = _f64(), _f64()
+    _check(lib().sf_lambda_max_estimate(g.handle, int(iters), _dev_ptr(v0, torch.float64, "v0") if v0 is not None
+                                        else None, C.c_uint64(seed), _stream(), C.byref(th), C.byref(lh)),
+           "sf_lambda_max_estimate")
+    return th.value, lh.value
+
+
+def cheb_coeffs(lam_max: float, cutoffs, p: int, jackson: bool = True) -> np.ndarray:
+    cut, cp = _f64arr(np.atleast_1d(cutoffs))
+    out = np.zeros((cut.shape[0], p + 1))
+    _check(lib().sf_cheb_coeffs(float(lam_max), cp, cut.shape[0], int(p), int(bool(jackson)),
+                                out.ctypes.data_as(_dp)), "sf_cheb_coeffs")
+    return out
+
+
+def cheb_filter(g: Graph, lam_max: float, coeffs, R, opts: Opts | None = None, out=None):
+    """Y[c] = sum_j coeffs[c, j] T_j(Lt) R on the GPU; returns a float32 tensor [n_cut, N, n_sig]."""
+    torch = _torch()
+    a, ap = _f64arr(np.atleast_2d(coeffs))
+    n_cut, p1 = a.shape
+    n, n_sig = R.shape
+    if out is None:
+        out = torch.empty((n_cut, n, n_sig), dtype=torch.float32, device=R.device)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_filter(g.handle, float(lam_max), ap, n_cut, p1 - 1, _dev_ptr(R, None, "R"), _rdtype(R),
+                                n_sig, _dev_ptr(out, torch.float32, "Y"), op, _stream()), "sf_cheb_filter")
+    return out
+
+
+def cheb_moments(g: Graph, lam_max: float, R, p: int, opts: Opts | None = None) -> np.ndarray:
+    n, n_sig = R.shape
+    mu = np.zeros(2 * p + 1)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_moments(g.handle, float(lam_max), _dev_ptr(R, None, "R"), _rdtype(R), n_sig, int(p),
+                                 mu.ctypes.data_as(_dp), op, _stream()), "sf_cheb_moments")
+    return mu
+
+
+def count_from_moments(mu, p: int, coeffs) -> np.ndarray:
+    mu, mp = _f64arr(mu)
+    a, ap = _f64arr(np.atleast_2d(coeffs))
+    out = np.zeros(a.shape[0])
+    _check(lib().sf_count_from_moments(mp, int(p), ap, a.shape[0], out.ctypes.data_as(_dp)),
+           "sf_count_from_moments")
+    return out
+
+
+def eigencount(g: Graph, lam_max: float, R, p: int, cutoffs, jackson: bool = True, opts: Opts | None = None):
+    """(counts per cutoff, moments) of §3.2 from one moment sweep."""
+    n, n_sig = R.shape
+    cut, cp = _f64arr(np.atleast_1d(cutoffs))
+    counts = np.zeros(cut.shape[0])
+    mu = np.zeros(2 * p + 1)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_eigencount(g.handle, float(lam_max), _dev_ptr(R, None, "R"), _rdtype(R), n_sig, int(p), cp,
+                               cut.shape[0], int(bool(jackson)), counts.ctypes.data_as(_dp), mu.ctypes.data_as(_dp),
+                               op, _stream()), "sf_eigencount")
+    return counts, mu
+
+
+def dichotomy(mu, p: int, lam_max: float, k: float, jackson: bool = True, max_iter: int = 40,
+              tol: float = 1e-9) -> float:
+    mu, mp = _f64arr(mu)
+    out = _f64()
+    _check(lib().sf_dichotomy(mp, int(p), float(lam_max), float(k), int(bool(jackson)), int(max_iter), float(tol),
+                              C.byref(out)), "sf_dichotomy")
+    return out.value
+
+
+def features(Y, normalize: bool = True, out=None):
+    torch = _torch()
+    n, n_sig = Y.shape
+    if out is None:
+        out = torch.empty_like(Y)
+    _check(lib().sf_features(_dev_ptr(Y, torch.float32, "Y"), n, n_sig, int(bool(normalize)),
+                             _dev_ptr(out, torch.float32, "F"), _stream()), "sf_features")
+    return out
+
+
+def cheb_filter_backward(g: Graph, lam_max: float, coeffs, R, G, want_grad_R: bool = True,
+                         opts: Opts | None = None):
+    """(grad_val [nnz], grad_coeffs [p+1] numpy, grad_R or None) of <G, Y>."""
+    torch = _torch()
+    a, ap = _f64arr(np.ravel(coeffs))
+    n, n_sig = R.shape
+    nnz = g.nnz
+    gv = torch.empty(max(nnz, 1), dtype=torch.float32, device=R.device)
+    ga = np.zeros(a.shape[0])
+    gR = torch.empty_like(R) if want_grad_R else None
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_filter_backward(g.handle, float(lam_max), ap, a.shape[0] - 1,
+                                         _dev_ptr(R, torch.float32, "R"), n_sig, _dev_ptr(G, torch.float32, "G"),
+                                         _dev_ptr(gv, torch.float32, "grad_val"), ga.ctypes.data_as(_dp),
+                                         _dev_ptr(gR, torch.float32, "grad_R") if gR is not None else None, op,
+                                         _stream()), "sf_cheb_filter_backward")
+    return gv[:nnz], ga, gR
+
+
+class Batch:
+    """Block-diagonal concatenation of several graphs."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, nnz, ng = _i32(), _i64(), _i32()
+        _check(lib().sf_batch_info(self._h, C.byref(n), C.byref(nnz), C.byref(ng), None), "sf_batch_info")
+        offs = (C.c_int32 * (ng.value + 1))()
+        _check(lib().sf_batch_info(self._h, None, None, None, offs), "sf_batch_info")
+        return n.value, nnz.value, ng.value, np.array(offs[:], dtype=np.int64)
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().sf_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def batch_build(graphs) -> Batch:
+    arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    out = _vp()
+    _check(lib().sf_batch_build(arr, len(graphs), _stream(), C.byref(out)), "sf_batch_build")
+    return Batch(out.value)
+
+
+def cheb_filter_batched(b: Batch, lam_max, coeffs, R, opts: Opts | None = None, out=None):
+    """Every graph of the batch filtered with its own lam_max and coefficient row, one sweep per order."""
+    torch = _torch()
+    lm, lp = _f64arr(np.ravel(lam_max))
+    a, ap = _f64arr(np.atleast_2d(coeffs))
+    n, n_sig = R.shape
+    if out is None:
+        out = torch.empty((n, n_sig), dtype=torch.float32, device=R.device)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_filter_batched(b.handle, lp, ap, a.shape[1] - 1, _dev_ptr(R, None, "R"), _rdtype(R), n_sig,
+                                        _dev_ptr(out, torch.float32, "Y"), op, _stream()), "sf_cheb_filter_batched")
+    return out
+
+
+def autotune(g: Graph, n_sig: int, storage: int = F32, n_cut: int = 1, base: Opts | None = None) -> Opts:
+    b, bp = _opts_ptr(base)
+    best = _Opts()
+    _check(lib().sf_autotune(g.handle, int(n_sig), int(storage), int(n_cut), bp, _stream(), C.byref(best)),
+           "sf_autotune")
+    return Opts(best.storage, best.algo, best.slab_cols, best.block_warps, best.blocks_per_sm, best.ckpt_every,
+                best.mem_cap_mb)
+
+
+def profile_begin():
+    _check(lib().sf_profile_begin(), "sf_profile_begin")
+
+
+def profile_end():
+    """(launches, total ms, total algorithmic bytes) of the sweep kernel since profile_begin()."""
+    n, ms, by = _i64(), _f64(), _f64()
+    _check(lib().sf_profile_end(C.byref(n), C.byref(ms), C.byref(by)), "sf_profile_end")
+    return n.value, ms.value, by.value
+
+
+def launch_count() -> int:
+    return int(lib().sf_launch_count())
+
+
+def _autograd():
+    torch = _torch()
+
+    class _ChebFilter(torch.autograd.Function):
+        """Y = sum_j a_j T_j(Lt) R with gradients for the edge weights (CSR order),
+        the coefficients and R; lam_max is held fixed."""
+
+        @staticmethod
+        def forward(ctx, val, coeffs, R, graph, lam_max, opts):
+            graph.set_values(val.detach().contiguous())
+            a = coeffs.detach().cpu().double().numpy()
+            Y = cheb_filter(graph, lam_max, a[None, :], R.detach().contiguous(), opts)[0]
+            ctx.save_for_backward(val, coeffs, R)
+            ctx.graph, ctx.lam_max, ctx.opts = graph, lam_max, opts
+            return Y
+
+        @staticmethod
+        def backward(ctx, G):
+            val, coeffs, R = ctx.saved_tensors
+            ctx.graph.set_values(val.detach().contiguous())
+            a = coeffs.detach().cpu().double().numpy()
+            gv, ga, gR = cheb_filter_backward(ctx.graph, ctx.lam_max, a, R.detach().contiguous(),
+                                              G.contiguous().float(), want_grad_R=ctx.needs_input_grad[2],
+                                              opts=ctx.opts)
+            gcoef = torch.as_tensor(ga, dtype=coeffs.dtype, device=coeffs.device)
+            return gv, gcoef, gR, None, None, None
+
+    return _ChebFilter
+
+
+_CF = None
+
+
+def ChebFilter(val, coeffs, R, graph: Graph, lam_max: float, opts: Opts | None = None):
+    """Differentiable filter: gradients flow to `val` (CSR-order weights), `coeffs` and `R`."""
+    global _CF
+    if _CF is None:
+        _CF = _autograd()
+    return _CF.apply(val, coeffs, R, graph, lam_max, opts)

@@ -1,0 +1,371 @@
+// Adjoint of the filter Y = sum_j a_j T_j(Lt) R for the loss l = <G, Y>.
+//
+// Reverse mode of the three-term recurrence (Lt is symmetric):
+//   Gb_p = a_p G;  Gb_j = a_j G + 2 Lt Gb_{j+1} - Gb_{j+2} (1 <= j < p);
+//   Gb_0 = a_0 G + Lt Gb_1 - Gb_2 = dl/dR;
+//   dl/da_j = <G, T_j R>;
+//   M = dl/dLt on the stored pattern and the diagonal
+//     = Gb_1 T_0^T + sum_{j >= 2} 2 Gb_j T_{j-1}^T   (a sampled dense-dense
+//       product: only entries (u, v) with W_uv stored, plus (u, u));
+//   dl/dW_uv = (2/lam)(M_uu + M_vv - M_uv - M_vu) (L = S - W, §2.1).
+// One fused kernel per order computes Gb_j for a row (a Clenshaw step), then
+// reuses it from registers for that row's sampled products against the
+// gathered rows of T_{j-1}, and the row's part of <G, T_j>.
+#include <math.h>
+
+#include "sf_step.cuh"
+
+namespace sf {
+
+struct AdjParams {
+    int32_t n;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const float *val;
+    const float *dtil;
+    float wscale_u;
+    int32_t ld;
+    const float *B1;     // Gb_{j+1} (gathered), nullptr when Gb_j is given
+    const float *B2;     // Gb_{j+2} or nullptr
+    const float *Gq;     // packed G slab
+    float *Bout;         // Gb_j (written) -- or read when `given`
+    float *Routf;        // final: dl/dR slab (fp32), when j == 0
+    const float *Tm1;    // T_{j-1} (gathered for the sampled products), nullptr for j == 0
+    const float *Tj;     // T_j (own rows) for <G, T_j>
+    float m;             // 2, or 1 for j == 0
+    float alpha;         // a_j
+    float csd;           // 1 for j == 1, 2 for j >= 2
+    int32_t given;       // Gb_j already in Bout (j == p)
+    float *Moff;         // [nnz] accumulated
+    float *Mdiag;        // [n] accumulated
+    double *part;        // [gridDim.x] partial <G, T_j>
+};
+
+template <int LPR>
+__global__ void __launch_bounds__(256) adj_step_kernel(const AdjParams P) {
+    using V = VT<float>;
+    constexpr int VEC = 4;
+    constexpr int NG = 32 / LPR;
+    constexpr int U = (NG == 1) ? 8 : 4;
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31;
+    const int q = lane % LPR, grp = lane / LPR;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t ld = P.ld;
+    const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
+    double gdot = 0.0;
+    for (int64_t i = warp0; i < P.n; i += nwarps) {
+        const int32_t beg = __ldg(P.rowptr + i), end = __ldg(P.rowptr + i + 1);
+        const int64_t ro = i * ld + q * VEC;
+        float t[VEC];
+        if (!P.given) {
+            float acc[VEC] = {0.f, 0.f, 0.f, 0.f};
+            for (int32_t base = beg; base < end; base += U * NG) {
+                int32_t k[U];
+                float wv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int32_t e = base + u * NG + grp;
+                    const bool ok = e < end;
+                    k[u] = ok ? __ldg(P.colidx + e) : -1;
+                    wv[u] = ok ? (P.val ? __ldg(P.val + e) : 1.0f) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    float xv[VEC] = {0.f, 0.f, 0.f, 0.f};
+                    if (k[u] >= 0) V::ld_gather(P.B1 + (int64_t)k[u] * ld + q * VEC, xv);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[v], acc[v]);
+                }
+            }
+#pragma unroll
+            for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+            // every group holds the full sum: each computes the row's Gb_j chunk
+            float xi[VEC], gq[VEC];
+            V::ld_gather(P.B1 + ro, xi);
+            V::ld_gather(P.Gq + ro, gq);
+            const float d = __ldg(P.dtil + i);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) t[v] = fmaf(P.alpha, gq[v], P.m * fmaf(d, xi[v], -P.wscale_u * acc[v]));
+            if (P.B2) {
+                float z[VEC];
+                V::ld_gather(P.B2 + ro, z);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) t[v] -= z[v];
+            }
+            if (grp == 0) {
+                if (P.Routf) V::st(P.Routf + ro, t);
+                else V::st(P.Bout + ro, t);
+            }
+        } else {
+            V::ld_gather(P.Bout + ro, t);
+        }
+        // <G, T_j> on the row
+        if (grp == 0 && P.Tj) {
+            float gq[VEC], tj[VEC];
+            V::ld_gather(P.Gq + ro, gq);
+            V::ld_gather(P.Tj + ro, tj);
+            float s = 0.f;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s = fmaf(gq[v], tj[v], s);
+#pragma unroll
+            for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+            if (q == 0) gdot += (double)s;
+        }
+        if (P.Tm1) {
+            // diagonal term by group 0, neighbours by all groups
+            if (grp == 0) {
+                float tp[VEC];
+                V::ld_gather(P.Tm1 + ro, tp);
+                float s = 0.f;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) s = fmaf(t[v], tp[v], s);
+#pragma unroll
+                for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+                if (q == 0) P.Mdiag[i] += P.csd * s;
+            }
+            for (int32_t base = beg; base < end; base += NG) {
+                const int32_t e = base + grp;
+                float s = 0.f;
+                if (e < end) {
+                    const int32_t v = __ldg(P.colidx + e);
+                    float tp[VEC];
+                    V::ld_gather(P.Tm1 + (int64_t)v * ld + q * VEC, tp);
+#pragma unroll
+                    for (int c = 0; c < VEC; ++c) s = fmaf(t[c], tp[c], s);
+                }
+#pragma unroll
+                for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+                if (e < end && q == 0) P.Moff[e] += P.csd * s;
+            }
+        }
+    }
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = gdot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += red[k];
+        P.part[blockIdx.x] = a;
+    }
+}
+
+// grad[e] = (2/lam)(Md[u] + Md[v] - M[e] - M[rev(e)]), rev(e) = entry (v, u),
+// found by binary search in the sorted row v.
+__global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *Moff,
+                                 const float *Mdiag, float two_over_lam, float *grad) {
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        for (int32_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+            const int32_t v = colidx[e];
+            int32_t lo = rowptr[v], hi = rowptr[v + 1] - 1;
+            float mvu = 0.f;
+            while (lo <= hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                const int32_t c = colidx[mid];
+                if (c == u) {
+                    mvu = Moff[mid];
+                    break;
+                }
+                if (c < u) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            grad[e] = two_over_lam * ((Mdiag[u] + Mdiag[v]) - (Moff[e] + mvu));
+        }
+    }
+}
+
+template <int LPR>
+static void launch_adj(const AdjParams &P, int grid, int block, cudaStream_t s) {
+    adj_step_kernel<LPR><<<grid, block, 0, s>>>(P);
+}
+
+static sf_status adj_launch(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s) {
+    switch (lpr) {
+        case 2: launch_adj<2>(P, grid, block, s); break;
+        case 4: launch_adj<4>(P, grid, block, s); break;
+        case 8: launch_adj<8>(P, grid, block, s); break;
+        case 16: launch_adj<16>(P, grid, block, s); break;
+        case 32: launch_adj<32>(P, grid, block, s); break;
+        default: set_error("bad lanes per row"); return SF_ERR_ARG;
+    }
+    return check_launch("adj_step_kernel");
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double lam_max, const double *coeffs,
+                                                    int32_t p, const float *R, int32_t n_sig, const float *G,
+                                                    float *grad_val, double *grad_coeffs, float *grad_R,
+                                                    const sf_opts *opts, void *stream) {
+    SF_ARG(g, "graph is NULL");
+    SF_ARG(lam_max > 0.0 && isfinite(lam_max), "lam_max must be finite and > 0");
+    SF_ARG(p >= 1 && p <= 100000, "p must be in [1, 100000]");
+    SF_ARG(n_sig >= 1, "n_sig must be >= 1");
+    SF_ARG(coeffs && R && G, "coeffs/R/G is NULL");
+    SF_ARG(g->nnz == 0 || grad_val, "grad_val is NULL");
+    SF_ARG(g->device == current_device(), "graph lives on another device");
+    for (int j = 0; j <= p; ++j) SF_ARG(isfinite(coeffs[j]), "coefficient %d is not finite", j);
+    sf_opts o = {};
+    if (opts) o = *opts;
+    SF_ARG(o.storage == SF_F32, "the adjoint keeps FP32 blocks (storage must be SF_F32)");
+    if (o.slab_cols <= 0) o.slab_cols = auto_slab_cols(g->n, n_sig, SF_F32, 48ll << 20);
+    SweepShape sh;
+    sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD, &sh);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->n;
+    const int ld = sh.ld;
+    const size_t blk = (size_t)n * ld;
+    const int64_t cap_mb = o.mem_cap_mb > 0 ? o.mem_cap_mb : 16384;
+    int k = o.ckpt_every;
+    if (k <= 0) k = ((double)(p + 1) * blk * 4 <= (double)cap_mb * (1 << 20)) ? 1 : (int)ceil(sqrt((double)p));
+    if (k > p) k = p;
+    // checkpoint slots: 0 and (c-1, c) for c = k, 2k, ... <= p (all j when k == 1)
+    std::vector<int> slot((size_t)p + 1, -1);
+    int nslots = 0;
+    for (int j = 0; j <= p; ++j) {
+        if (k == 1 || j == 0 || j % k == 0 || (j + 1) % k == 0) slot[j] = nslots++;
+    }
+    Scratch sc(s);
+    float *store = nullptr, *seg = nullptr, *work[3] = {nullptr, nullptr, nullptr}, *bb[3] = {nullptr, nullptr, nullptr};
+    float *gq = nullptr, *coef = nullptr, *dtil = nullptr, *moff = nullptr, *mdiag = nullptr, *gR = nullptr;
+    double *part = nullptr, *ga = nullptr;
+    if ((st = sc.get(&store, (size_t)nslots * blk))) return st;
+    if (k > 1 && (st = sc.get(&seg, (size_t)(k + 1) * blk))) return st;
+    for (int q = 0; q < 3; ++q) {
+        if ((st = sc.get(&work[q], blk))) return st;
+        if ((st = sc.get(&bb[q], blk))) return st;
+    }
+    if ((st = sc.get(&gq, blk)) || (st = sc.get(&coef, (size_t)p + 1)) || (st = sc.get(&dtil, (size_t)n)) ||
+        (st = sc.get(&mdiag, (size_t)n)) || (st = sc.get(&part, (size_t)sh.grid + 1)) ||
+        (st = sc.get(&ga, (size_t)p + 1)))
+        return st;
+    if (g->nnz > 0 && (st = sc.get(&moff, (size_t)g->nnz))) return st;
+    if (grad_R && (st = sc.get(&gR, blk))) return st;
+    {
+        std::vector<float> cf((size_t)p + 1);
+        for (int j = 0; j <= p; ++j) cf[j] = (float)coeffs[j];
+        SF_CHECK_CUDA(cudaMemcpyAsync(coef, cf.data(), sizeof(float) * (p + 1), cudaMemcpyHostToDevice, s));
+    }
+    if (moff) SF_CHECK_CUDA(cudaMemsetAsync(moff, 0, sizeof(float) * g->nnz, s));
+    SF_CHECK_CUDA(cudaMemsetAsync(mdiag, 0, sizeof(float) * n, s));
+    SF_CHECK_CUDA(cudaMemsetAsync(ga, 0, sizeof(double) * (p + 1), s));
+    if (n > 0) {
+        dtil_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->strength, (int32_t)n, 2.0 / lam_max, nullptr, nullptr,
+                                                                dtil, nullptr);
+        if ((st = check_launch("dtil_kernel"))) return st;
+    }
+    const float *val = g->unit_weights ? nullptr : g->val;
+    const int pack_grid = 2 * sm_count();
+    const double two_over_lam = 2.0 / lam_max;
+
+    for (int c0 = 0; c0 < n_sig; c0 += ld) {
+        const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;
+        auto T_at = [&](int j) { return store + (size_t)slot[j] * blk; };
+        // ---- forward: T_0..T_p, keeping the checkpoint slots
+        pack_kernel<float><<<pack_grid, 256, 0, s>>>(R, SF_F32, (int32_t)n, n_sig, c0, w, ld, work[0], nullptr, 0, 0,
+                                                     nullptr, 1, 0, nullptr, nullptr, nullptr);
+        if ((st = check_launch("pack_kernel"))) return st;
+        SF_CHECK_CUDA(cudaMemcpyAsync(T_at(0), work[0], blk * 4, cudaMemcpyDeviceToDevice, s));
+        StepParams P = {};
+        P.n = (int32_t)n;
+        P.rowptr = g->rowptr;
+        P.colidx = g->colidx;
+        P.val = val;
+        P.dtil = dtil;
+        P.wscale_u = (float)two_over_lam;
+        P.ld = ld;
+        P.n_cut = 0;
+        auto fwd_step = [&](const float *Xp, const float *Zp, float *outp, int j) {
+            P.X = Xp;
+            P.Z = Zp;
+            P.out = outp;
+            P.m = (j == 1) ? 1.0f : 2.0f;
+            P.j = j;
+            return launch_step(sh, MODE_FWD, P, s, 0.0);
+        };
+        for (int j = 1; j <= p; ++j) {
+            float *outp = (k == 1) ? T_at(j) : work[j % 3];
+            const float *Xp = (k == 1) ? T_at(j - 1) : work[(j - 1) % 3];
+            const float *Zp = (j >= 2) ? ((k == 1) ? T_at(j - 2) : work[(j - 2) % 3]) : nullptr;
+            if ((st = fwd_step(Xp, Zp, outp, j))) return st;
+            if (k > 1 && slot[j] >= 0)
+                SF_CHECK_CUDA(cudaMemcpyAsync(T_at(j), outp, blk * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        // ---- backward
+        int seg_base = -1;
+        auto ensure_segment = [&](int jlo) -> sf_status {
+            // segment holding T_c .. T_{min(c + k, p)} with c = k * floor(jlo / k)
+            const int c = (jlo / k) * k;
+            if (c == seg_base) return SF_OK;
+            const int top = (c + k < p) ? c + k : p;
+            SF_CHECK_CUDA(cudaMemcpyAsync(seg, T_at(c), blk * 4, cudaMemcpyDeviceToDevice, s));
+            for (int j = c + 1; j <= top; ++j) {
+                const float *Xp = seg + (size_t)(j - 1 - c) * blk;
+                const float *Zp = nullptr;
+                if (j >= 2) Zp = (j - 2 >= c) ? seg + (size_t)(j - 2 - c) * blk : T_at(j - 2);
+                sf_status e = fwd_step(Xp, Zp, seg + (size_t)(j - c) * blk, j);
+                if (e) return e;
+            }
+            seg_base = c;
+            return SF_OK;
+        };
+        auto T_get = [&](int j) -> const float * {
+            if (k == 1) return T_at(j);
+            if (seg_base >= 0 && j >= seg_base && j <= seg_base + k) return seg + (size_t)(j - seg_base) * blk;
+            return T_at(j);  // a checkpoint slot
+        };
+        // Gb_p = a_p G (pack with b-start), packed G
+        pack_kernel<float><<<pack_grid, 256, 0, s>>>(G, SF_F32, (int32_t)n, n_sig, c0, w, ld, gq, nullptr, 0, 1, coef,
+                                                     p + 1, p, nullptr, bb[p % 3], nullptr);
+        if ((st = check_launch("pack_kernel"))) return st;
+        AdjParams A = {};
+        A.n = (int32_t)n;
+        A.rowptr = g->rowptr;
+        A.colidx = g->colidx;
+        A.val = val;
+        A.dtil = dtil;
+        A.wscale_u = (float)two_over_lam;
+        A.ld = ld;
+        A.Gq = gq;
+        A.Moff = moff;
+        A.Mdiag = mdiag;
+        A.part = part;
+        for (int j = p; j >= 0; --j) {
+            if (k > 1 && j >= 1 && (st = ensure_segment(j - 1))) return st;
+            A.given = (j == p);
+            A.B1 = (j < p) ? bb[(j + 1) % 3] : nullptr;
+            A.B2 = (j + 2 <= p) ? bb[(j + 2) % 3] : nullptr;
+            A.Bout = bb[j % 3];
+            A.Routf = (j == 0) ? gR : nullptr;
+            if (j == 0 && !gR) A.Routf = work[0];  // dl/dR not requested: scratch target
+            A.Tm1 = (j >= 1) ? T_get(j - 1) : nullptr;
+            A.Tj = (j >= 1) ? T_get(j) : T_at(0);
+            A.m = (j == 0) ? 1.0f : 2.0f;
+            A.alpha = (float)coeffs[j];
+            A.csd = (j == 1) ? 1.0f : 2.0f;
+            if ((st = adj_launch(sh.lpr, A, sh.grid, sh.block, s))) return st;
+            pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 1, ga + j);
+            if ((st = check_launch("pair_sum_kernel"))) return st;
+        }
+        if (grad_R) {
+            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(gR, (int32_t)n, ld, w, 1, grad_R, n_sig, c0);
+            if ((st = check_launch("unpack_kernel"))) return st;
+        }
+    }
+    if (g->nnz > 0) {
+        edge_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, g->rowptr, g->colidx, moff, mdiag,
+                                                                     (float)two_over_lam, grad_val);
+        if ((st = check_launch("edge_grad_kernel"))) return st;
+    }
+    if (grad_coeffs) {
+        SF_CHECK_CUDA(cudaMemcpyAsync(grad_coeffs, ga, sizeof(double) * (p + 1), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    return SF_OK;
+}

@@ -1,0 +1,500 @@
+// Fast filtering of random signals: forward Chebyshev recurrence with
+// multi-cutoff accumulation, Clenshaw summation for one cutoff, the moment
+// sweep behind the eigenvalue count, batched graphs, and the tile autotuner.
+#include <math.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "sf_step.cuh"
+
+namespace sf {
+
+// ------------------------------------------------------------ shapes
+static int vec_of(int storage) { return storage == SF_F32 ? 4 : 8; }
+static int bytes_of(int storage) { return storage == SF_F32 ? 4 : 2; }
+
+int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t budget) {
+    const int vec = vec_of(storage), b = bytes_of(storage);
+    // smallest admissible width covering all signals
+    int full = vec * 2;
+    while (full < n_sig && full < vec * 32) full *= 2;
+    int w = full;
+    while (w > vec * 2 && (int64_t)n * w * b > budget) w /= 2;
+    return w;
+}
+
+template <typename TS, int LPR>
+static const void *step_fn(int mode) {
+    switch (mode) {
+        case MODE_FWD: return (const void *)cheb_step_kernel<TS, LPR, MODE_FWD>;
+        case MODE_MOM: return (const void *)cheb_step_kernel<TS, LPR, MODE_MOM>;
+        default: return (const void *)cheb_step_kernel<TS, LPR, MODE_CLEN>;
+    }
+}
+
+template <typename TS>
+static const void *step_fn_lpr(int lpr, int mode) {
+    switch (lpr) {
+        case 2: return step_fn<TS, 2>(mode);
+        case 4: return step_fn<TS, 4>(mode);
+        case 8: return step_fn<TS, 8>(mode);
+        case 16: return step_fn<TS, 16>(mode);
+        case 32: return step_fn<TS, 32>(mode);
+        default: return nullptr;
+    }
+}
+
+static const void *kernel_for(int storage, int lpr, int mode) {
+    if (storage == SF_F32) return step_fn_lpr<float>(lpr, mode);
+    if (storage == SF_BF16) return step_fn_lpr<__nv_bfloat16>(lpr, mode);
+    return nullptr;
+}
+
+sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, SweepShape *sh) {
+    SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage type %d is not supported (SF_F32 or SF_BF16)",
+           storage);
+    const int vec = vec_of(storage);
+    SF_ARG(slab_cols % vec == 0, "slab_cols %d is not a multiple of %d", slab_cols, vec);
+    const int lpr = slab_cols / vec;
+    SF_ARG(lpr == 2 || lpr == 4 || lpr == 8 || lpr == 16 || lpr == 32,
+           "slab_cols %d gives %d lanes per row (need 2..32, power of two)", slab_cols, lpr);
+    if (block_warps <= 0) block_warps = 8;
+    SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
+    const void *fn = kernel_for(storage, lpr, mode);
+    SF_ARG(fn, "no kernel for this shape");
+    int occ = 0;
+    SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, 0));
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+    sh->storage = storage;
+    sh->lpr = lpr;
+    sh->ld = slab_cols;
+    sh->block = block_warps * 32;
+    sh->grid = occ * sm_count();
+    return SF_OK;
+}
+
+template <typename TS, int LPR>
+static void launch_mode(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
+    switch (mode) {
+        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD><<<sh.grid, sh.block, 0, s>>>(P); break;
+        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM><<<sh.grid, sh.block, 0, s>>>(P); break;
+        default: cheb_step_kernel<TS, LPR, MODE_CLEN><<<sh.grid, sh.block, 0, s>>>(P); break;
+    }
+}
+
+template <typename TS>
+static void launch_lpr(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
+    switch (sh.lpr) {
+        case 2: launch_mode<TS, 2>(mode, sh, P, s); break;
+        case 4: launch_mode<TS, 4>(mode, sh, P, s); break;
+        case 8: launch_mode<TS, 8>(mode, sh, P, s); break;
+        case 16: launch_mode<TS, 16>(mode, sh, P, s); break;
+        default: launch_mode<TS, 32>(mode, sh, P, s); break;
+    }
+}
+
+sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes) {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    const bool prof = profiling_on() && profile_events(&ea, &eb);
+    if (prof) cudaEventRecord(ea, s);
+    if (sh.storage == SF_F32) launch_lpr<float>(mode, sh, P, s);
+    else launch_lpr<__nv_bfloat16>(mode, sh, P, s);
+    sf_status st = check_launch("cheb_step_kernel");
+    if (prof) {
+        cudaEventRecord(eb, s);
+        profile_record(ea, eb, bytes);
+    }
+    return st;
+}
+
+// Compulsory bytes of one sweep launch: CSR streamed once, the gathered slab
+// read once, the streamed slabs, the accumulators read and written.
+static double step_bytes(int64_t n, int64_t nnz, bool unit, bool batched, int w, int storage, int mode,
+                         bool has_z, int n_cut, bool final_f32) {
+    const double b = bytes_of(storage);
+    double by = (double)(n + 1) * 4 + (double)n * 4 + (double)nnz * (unit ? 4 : 8);
+    if (batched) by += (double)n * 8;
+    const double blk = (double)n * w * b;
+    by += blk;                              // gathered T_{j-1}
+    if (has_z) by += blk;                   // T_{j-2}
+    by += final_f32 ? (double)n * w * 4 : blk;  // output
+    if (mode == MODE_CLEN) by += blk;       // addend block
+    if (mode == MODE_FWD) by += 2.0 * n_cut * n * w * 4;
+    return by;
+}
+
+// ------------------------------------------------------------ common driver
+struct GraphView {
+    int32_t n;
+    int64_t nnz;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const float *val;  // nullptr for unit weights
+    const double *strength;
+    const int32_t *gid;  // batches
+    int32_t n_graphs;
+};
+
+static GraphView view_of(const sf_graph *g) {
+    return GraphView{g->n, g->nnz, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, g->strength, nullptr, 1};
+}
+
+static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r) {
+    sf_opts z = {};
+    *r = o ? *o : z;
+    if (r->storage != SF_F32 && r->storage != SF_BF16) {
+        set_error("storage type %d is not supported (SF_F32 or SF_BF16)", r->storage);
+        return SF_ERR_ARG;
+    }
+    if (r->slab_cols <= 0) r->slab_cols = auto_slab_cols(n, n_sig, r->storage, 48ll << 20);
+    return SF_OK;
+}
+
+static sf_status launch_pack(int storage, int grid, cudaStream_t s, const void *R, int r_dtype, int32_t n,
+                             int32_t n_sig, int32_t c0, int32_t w, int32_t ld, void *T0, float *Y, int64_t ystride,
+                             int32_t n_cut, const float *coef, int32_t coef_ld, int32_t jcoef, const int32_t *gid,
+                             void *bstart, double *part) {
+    if (storage == SF_F32)
+        pack_kernel<float><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (float *)T0, Y, ystride, n_cut, coef,
+                                                coef_ld, jcoef, gid, (float *)bstart, part);
+    else
+        pack_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (__nv_bfloat16 *)T0, Y,
+                                                        ystride, n_cut, coef, coef_ld, jcoef, gid,
+                                                        (__nv_bfloat16 *)bstart, part);
+    return check_launch("pack_kernel");
+}
+
+// Runs the filter over all slabs. mode: MODE_FWD (n_cut accumulators),
+// MODE_CLEN (one cutoff) or MODE_MOM (moment sums into mom[(p+1)][2] on the
+// device, accumulated over slabs; mom0 gets <T0,T0>).
+static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, double two_over_lam, int mode,
+                            const double *coeffs_host, int n_cut, int p, const void *R, int r_dtype, int n_sig,
+                            float *Y, double *mom, const sf_opts &o, cudaStream_t s) {
+    SweepShape sh;
+    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, &sh);
+    if (st) return st;
+    const int ld = sh.ld;
+    const int64_t n = G.n;
+    const size_t eb = bytes_of(o.storage);
+    Scratch sc(s);
+    void *buf[3] = {nullptr, nullptr, nullptr};
+    void *qbuf = nullptr;
+    float *yacc = nullptr, *coef = nullptr, *dtil = nullptr, *wscale = nullptr;
+    double *part = nullptr, *tol = nullptr;
+    const int nbuf = 3;
+    for (int k = 0; k < nbuf; ++k)
+        if ((st = sc.get((char **)&buf[k], (size_t)n * ld * eb))) return st;
+    if (mode == MODE_CLEN && (st = sc.get((char **)&qbuf, (size_t)n * ld * eb))) return st;
+    const int ncy = (mode == MODE_FWD) ? n_cut : (mode == MODE_CLEN ? 1 : 0);
+    if (ncy && (st = sc.get(&yacc, (size_t)ncy * n * ld))) return st;
+    const int ncoef = (mode == MODE_MOM) ? 0 : G.n_graphs * n_cut * (p + 1);
+    if (ncoef && (st = sc.get(&coef, (size_t)ncoef))) return st;
+    if ((st = sc.get(&dtil, (size_t)n))) return st;
+    if (G.gid) {
+        if ((st = sc.get(&wscale, (size_t)n))) return st;
+        if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
+    }
+    if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * sh.grid + 2))) return st;
+
+    if (ncoef) {
+        std::vector<float> cf((size_t)ncoef);
+        for (int k = 0; k < ncoef; ++k) cf[k] = (float)coeffs_host[k];
+        SF_CHECK_CUDA(cudaMemcpyAsync(coef, cf.data(), sizeof(float) * ncoef, cudaMemcpyHostToDevice, s));
+        // cf must outlive the copy: pageable copies complete before returning
+    }
+    if (G.gid) {
+        SF_CHECK_CUDA(cudaMemcpyAsync(tol, two_over_lam_g, sizeof(double) * G.n_graphs, cudaMemcpyHostToDevice, s));
+    }
+    if (n > 0) {
+        dtil_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G.strength, (int32_t)n, two_over_lam, G.gid, tol,
+                                                                dtil, wscale);
+        if ((st = check_launch("dtil_kernel"))) return st;
+    }
+    const int pack_grid = 2 * sm_count();
+    for (int c0 = 0; c0 < n_sig; c0 += ld) {
+        const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;
+        StepParams P = {};
+        P.n = (int32_t)n;
+        P.rowptr = G.rowptr;
+        P.colidx = G.colidx;
+        P.val = G.val;
+        P.dtil = dtil;
+        P.wscale = wscale;
+        P.wscale_u = (float)two_over_lam;
+        P.gid = G.gid;
+        P.ld = ld;
+        P.coef = coef;
+        P.coef_ld = p + 1;
+        P.n_cut = n_cut;
+        P.Y = yacc;
+        P.ystride = n * ld;
+        P.part = part;
+        const bool unit = G.val == nullptr;
+        const bool batched = G.gid != nullptr;
+        if (mode == MODE_FWD || mode == MODE_MOM) {
+            // T_0 = R (and Y_c = a_c0 T_0, or <T0,T0>)
+            if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, buf[0], yacc,
+                                  n * ld, n_cut, coef, p + 1, 0, G.gid, nullptr, mode == MODE_MOM ? part : nullptr)))
+                return st;
+            if (mode == MODE_MOM) {
+                pair_sum_kernel<<<1, 256, 0, s>>>(part, pack_grid, 1, mom);
+                if ((st = check_launch("pair_sum_kernel"))) return st;
+            }
+            // orders 1..p: buffer of T_j is j % 3
+            for (int j = 1; j <= p; ++j) {
+                P.X = buf[(j - 1) % 3];
+                P.Z = (j >= 2) ? buf[(j - 2) % 3] : nullptr;
+                P.out = buf[j % 3];
+                P.m = (j == 1) ? 1.0f : 2.0f;
+                P.j = j;
+                double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false);
+                if ((st = launch_step(sh, mode, P, s, by))) return st;
+                if (mode == MODE_MOM) {
+                    pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 2, mom + 2 * j);
+                    if ((st = check_launch("pair_sum_kernel"))) return st;
+                }
+            }
+        } else {
+            // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};
+            // Y = a_0 R + Lt b_1 - b_2.
+            if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, nullptr,
+                                  0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr)))
+                return st;
+            P.Q = qbuf;
+            for (int j = p - 1; j >= 0; --j) {
+                // b_j lives in buffer j % 3; b_{j+1}, b_{j+2} in the other two
+                P.X = buf[(j + 1) % 3];
+                P.Z = (j + 2 <= p) ? buf[(j + 2) % 3] : nullptr;
+                P.j = j;
+                if (j == 0) {
+                    P.m = 1.0f;
+                    P.out = nullptr;
+                    P.outf = yacc;
+                } else {
+                    P.m = 2.0f;
+                    P.out = buf[j % 3];
+                    P.outf = nullptr;
+                }
+                double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, MODE_CLEN, j + 2 <= p, 1, j == 0);
+                if ((st = launch_step(sh, MODE_CLEN, P, s, by))) return st;
+            }
+            if (p == 0) {
+                // Y = a_0 R: b_0 computed by the pack as a_p R with p = 0, widen to fp32
+                if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, yacc,
+                                      n * ld, 1, coef, 1, 0, G.gid, nullptr, nullptr)))
+                    return st;
+            }
+        }
+        if (ncy) {
+            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0);
+            if ((st = check_launch("unpack_kernel"))) return st;
+        }
+    }
+    return SF_OK;
+}
+
+static sf_status check_common(const sf_graph *g, double lam_max, int p, const void *R, int r_dtype, int n_sig) {
+    SF_ARG(g, "graph is NULL");
+    SF_ARG(lam_max > 0.0 && isfinite(lam_max), "lam_max must be finite and > 0 (got %g)", lam_max);
+    SF_ARG(p >= 0 && p <= 100000, "p must be in [0, 100000] (got %d)", p);
+    SF_ARG(n_sig >= 1, "n_sig must be >= 1 (got %d)", n_sig);
+    SF_ARG(R, "R is NULL");
+    SF_ARG(r_dtype == SF_F32 || r_dtype == SF_BF16, "R dtype must be SF_F32 or SF_BF16");
+    SF_ARG(g->device == current_device(), "graph lives on device %d, current device is %d", g->device,
+           current_device());
+    return SF_OK;
+}
+
+// moments from the per-order dot products D_j = <T_j,T_j>, E_j = <T_j,T_{j-1}>
+static void moments_from_dots(const double *dots, int p, double *mu) {
+    // dots[2j] = D_j, dots[2j+1] = E_j (E_0 unused)
+    mu[0] = dots[0];
+    if (p >= 1) mu[1] = dots[3];
+    for (int j = 1; j <= p; ++j) mu[2 * j] = 2.0 * dots[2 * j] - mu[0];
+    for (int j = 2; j <= p; ++j) mu[2 * j - 1] = 2.0 * dots[2 * j + 1] - mu[1];
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" {
+
+SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double *coeffs, int32_t n_cut,
+                                int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                const sf_opts *opts, void *stream) {
+    sf_status st = check_common(g, lam_max, p, R, r_dtype, n_sig);
+    if (st) return st;
+    SF_ARG(coeffs && Y, "coeffs/Y is NULL");
+    SF_ARG(n_cut >= 1 && n_cut <= 64, "n_cut must be in [1, 64] (got %d)", n_cut);
+    for (int64_t k = 0; k < (int64_t)n_cut * (p + 1); ++k)
+        SF_ARG(isfinite(coeffs[k]), "coefficient %lld is not finite", (long long)k);
+    sf_opts o;
+    if ((st = resolve_opts(opts, g->n, n_sig, &o))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int algo = o.algo;
+    if (algo == SF_ALGO_AUTO) algo = (n_cut == 1) ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
+    SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
+    GraphView G = view_of(g);
+    if (algo == SF_ALGO_FORWARD)
+        return run_sweeps(G, nullptr, 2.0 / lam_max, MODE_FWD, coeffs, n_cut, p, R, r_dtype, n_sig, Y, nullptr, o, s);
+    for (int c = 0; c < n_cut; ++c) {
+        st = run_sweeps(G, nullptr, 2.0 / lam_max, MODE_CLEN, coeffs + (int64_t)c * (p + 1), 1, p, R, r_dtype,
+                        n_sig, Y + (int64_t)c * g->n * n_sig, nullptr, o, s);
+        if (st) return st;
+    }
+    return SF_OK;
+}
+
+SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *R, int32_t r_dtype,
+                                 int32_t n_sig, int32_t p, double *moments, const sf_opts *opts,
+                                 void *stream) {
+    sf_status st = check_common(g, lam_max, p, R, r_dtype, n_sig);
+    if (st) return st;
+    SF_ARG(moments, "moments is NULL");
+    sf_opts o;
+    if ((st = resolve_opts(opts, g->n, n_sig, &o))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    double *dots = nullptr;
+    if ((st = sc.get(&dots, (size_t)2 * (p + 1)))) return st;
+    SF_CHECK_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * 2 * (p + 1), s));
+    GraphView G = view_of(g);
+    if ((st = run_sweeps(G, nullptr, 2.0 / lam_max, MODE_MOM, nullptr, 0, p, R, r_dtype, n_sig, nullptr, dots, o,
+                         s)))
+        return st;
+    std::vector<double> hd((size_t)2 * (p + 1));
+    SF_CHECK_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 2 * (p + 1), cudaMemcpyDeviceToHost, s));
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    moments_from_dots(hd.data(), p, moments);
+    return SF_OK;
+}
+
+SF_API sf_status sf_eigencount(const sf_graph *g, double lam_max, const void *R, int32_t r_dtype,
+                               int32_t n_sig, int32_t p, const double *cutoffs, int32_t n_cut,
+                               int32_t jackson, double *counts, double *moments_out, const sf_opts *opts,
+                               void *stream) {
+    SF_ARG(cutoffs && counts, "cutoffs/counts is NULL");
+    SF_ARG(n_cut >= 1, "n_cut must be >= 1");
+    std::vector<double> mu((size_t)2 * p + 1);
+    sf_status st = sf_cheb_moments(g, lam_max, R, r_dtype, n_sig, p, mu.data(), opts, stream);
+    if (st) return st;
+    std::vector<double> a((size_t)p + 1);
+    for (int c = 0; c < n_cut; ++c) {
+        cheb_coeffs_host(lam_max, cutoffs[c], p, jackson, a.data());
+        counts[c] = count_from_moments_host(mu.data(), p, a.data());
+    }
+    if (moments_out)
+        for (int m = 0; m <= 2 * p; ++m) moments_out[m] = mu[m];
+    return SF_OK;
+}
+
+SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
+                                        int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                        const sf_opts *opts, void *stream) {
+    SF_ARG(b, "batch is NULL");
+    SF_ARG(lam_max && coeffs && R && Y, "null pointer");
+    SF_ARG(p >= 0 && n_sig >= 1, "need p >= 0 and n_sig >= 1");
+    SF_ARG(r_dtype == SF_F32 || r_dtype == SF_BF16, "R dtype must be SF_F32 or SF_BF16");
+    SF_ARG(b->device == current_device(), "batch lives on another device");
+    std::vector<double> tol((size_t)b->n_graphs);
+    for (int k = 0; k < b->n_graphs; ++k) {
+        SF_ARG(lam_max[k] > 0.0 && isfinite(lam_max[k]), "lam_max[%d] must be finite and > 0", k);
+        tol[k] = 2.0 / lam_max[k];
+    }
+    for (int64_t k = 0; k < (int64_t)b->n_graphs * (p + 1); ++k)
+        SF_ARG(isfinite(coeffs[k]), "coefficient %lld is not finite", (long long)k);
+    sf_opts o;
+    sf_status st = resolve_opts(opts, b->n, n_sig, &o);
+    if (st) return st;
+    int algo = o.algo == SF_ALGO_AUTO ? SF_ALGO_CLENSHAW : o.algo;
+    SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
+    GraphView G{b->n, b->nnz, b->rowptr, b->colidx, b->unit_weights ? nullptr : b->val, b->strength, b->row_graph,
+                b->n_graphs};
+    return run_sweeps(G, tol.data(), 0.0, algo == SF_ALGO_FORWARD ? MODE_FWD : MODE_CLEN, coeffs, 1, p, R, r_dtype,
+                      n_sig, Y, nullptr, o, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ autotuner
+SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, int32_t n_cut,
+                             const sf_opts *base, void *stream, sf_opts *best) {
+    SF_ARG(g && best, "null pointer");
+    SF_ARG(n_sig >= 1 && n_cut >= 1, "need n_sig >= 1 and n_cut >= 1");
+    SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage must be SF_F32 or SF_BF16");
+    static std::mutex mu;
+    static std::map<std::tuple<int, int64_t, int, int, int, int>, sf_opts> cache;
+    sf_opts b0 = {};
+    if (base) b0 = *base;
+    b0.storage = storage;
+    auto key = std::make_tuple(g->n, g->nnz, n_sig, storage, n_cut, current_device());
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *best = it->second;
+            best->ckpt_every = b0.ckpt_every;
+            best->mem_cap_mb = b0.mem_cap_mb;
+            return SF_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int vec = vec_of(storage);
+    int full = vec * 2;
+    while (full < n_sig && full < vec * 32) full *= 2;
+    const int p_try = 6;
+    Scratch sc(s);
+    float *R = nullptr, *Y = nullptr;
+    sf_status st;
+    if ((st = sc.get(&R, (size_t)g->n * n_sig))) return st;
+    if ((st = sc.get(&Y, (size_t)g->n * n_sig * n_cut))) return st;
+    SF_CHECK_CUDA(cudaMemsetAsync(R, 0, sizeof(float) * g->n * n_sig, s));
+    std::vector<double> cf((size_t)n_cut * (p_try + 1), 0.1);
+    cudaEvent_t e0, e1;
+    SF_CHECK_CUDA(cudaEventCreate(&e0));
+    SF_CHECK_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    sf_opts bo = b0;
+    const int warps_opts[2] = {4, 8};
+    for (int w = full; w >= vec * 2; w /= 2) {
+        for (int wi = 0; wi < 2; ++wi) {
+            for (int bps = 0; bps <= 4; bps += 2) {
+                sf_opts t = b0;
+                t.slab_cols = w;
+                t.block_warps = warps_opts[wi];
+                t.blocks_per_sm = bps;
+                t.algo = n_cut == 1 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
+                // warm-up then time
+                st = sf_cheb_filter(g, 2.0 * g->max_strength + 1.0, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t,
+                                    stream);
+                if (st) continue;
+                cudaEventRecord(e0, s);
+                st = sf_cheb_filter(g, 2.0 * g->max_strength + 1.0, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t,
+                                    stream);
+                cudaEventRecord(e1, s);
+                if (st) continue;
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bo = t;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SF_CHECK_CUDA(cudaGetLastError());
+    bo.algo = base ? base->algo : SF_ALGO_AUTO;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = bo;
+    }
+    *best = bo;
+    return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/specfilt.h"
+
+namespace sf {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+sf_status cuda_fail(cudaError_t e, const char *what);
+
+#define SF_CHECK_CUDA(call)                                        \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::sf::cuda_fail(_e, #call);  \
+    } while (0)
+
+#define SF_ARG(cond, ...)                 \
+    do {                                  \
+        if (!(cond)) {                    \
+            ::sf::set_error(__VA_ARGS__); \
+            return SF_ERR_ARG;            \
+        }                                 \
+    } while (0)
+
+// Counts every kernel launch issued by the library; call after each launch.
+void note_launch();
+// Checks the launch that was just issued.
+sf_status check_launch(const char *name);
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered device allocation; zero bytes gives nullptr.
+sf_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// RAII holder for stream-ordered allocations of one call.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    sf_status get(T **p, size_t count) {
+        void *q = nullptr;
+        sf_status st = dev_alloc(&q, count * sizeof(T), s);
+        if (st != SF_OK) return st;
+        if (q) ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return SF_OK;
+    }
+    ~Scratch() {
+        for (void *q : ptrs) dev_free(q, s);
+    }
+};
+
+// ---------------------------------------------------------------- device info
+int sm_count();
+int current_device();
+
+// ---------------------------------------------------------------- scans
+// Exclusive prefix sum of n int32 values (out may alias in). The total must
+// fit in int32. Uses stream-ordered temporaries.
+sf_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+// Deterministic sum of `count` doubles (fixed order), result in device *out.
+sf_status reduce_sum_f64(const double *in, int64_t count, double *out, cudaStream_t s);
+
+// ---------------------------------------------------------------- profiling
+bool profiling_on();
+void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes);
+bool profile_events(cudaEvent_t *a, cudaEvent_t *b);
+
+// ---------------------------------------------------------------- host math
+void cheb_coeffs_host(double lam_max, double lc, int p, int jackson, double *a);
+double count_from_moments_host(const double *mu, int p, const double *a);
+double tridiag_max_eig_host(int k, const double *a, const double *b);
+
+}  // namespace sf
+
+// ---------------------------------------------------------------- objects
+struct sf_graph {
+    int32_t n = 0;
+    int64_t nnz = 0;  // stored off-diagonal entries
+    int32_t *rowptr = nullptr;
+    int32_t *colidx = nullptr;
+    float *val = nullptr;
+    double *strength = nullptr;
+    double max_strength = 0.0;
+    int32_t unit_weights = 1;
+    int device = 0;
+};
+
+struct sf_batch {
+    int32_t n_graphs = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t *rowptr = nullptr;
+    int32_t *colidx = nullptr;
+    float *val = nullptr;
+    double *strength = nullptr;
+    int32_t *row_graph = nullptr;  // graph id of each row
+    int32_t unit_weights = 1;
+    std::vector<int32_t> offsets;   // host, n_graphs + 1
+    std::vector<int64_t> nnz_offsets;
+    int device = 0;
+};
+
+// Strength recomputation (shared by build and set_values).
+namespace sf {
+sf_status compute_strength(sf_graph *g, cudaStream_t s);
+}

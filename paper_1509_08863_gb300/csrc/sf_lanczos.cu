@@ -1,0 +1,222 @@
+// lambda_N estimate (§4.1 step 1) by Lanczos in FP64 on the device, and the
+// feature rows of Eq. (6) / Eq. (11) (optionally L2-normalised).
+#include <math.h>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): state += golden gamma, then two xor-shift-multiply
+// rounds. Maps (seed, i) to a uniform double in [-1, 1).
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+__global__ void lanczos_init_kernel(double *v, const double *v0, uint64_t seed, int32_t n) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = v0 ? v0[i] : splitmix_uniform(seed, (uint64_t)i);
+}
+
+// part[b] = block partial of sum x_i y_i (fixed strided order per block).
+template <int BS>
+__device__ void block_dot_store(double acc, double *part) {
+    __shared__ double sh[BS];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = BS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// w = L v (warp per row, lanes over the row's entries); partial <w, v>.
+__global__ void __launch_bounds__(256) lap_spmv_f64_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                                                           const float *val, const double *strength, const double *v,
+                                                           double *w, double *part) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double dot = 0.0;
+    for (int64_t i = warp0; i < n; i += nw) {
+        const int32_t beg = rowptr[i], end = rowptr[i + 1];
+        double acc = 0.0;
+        for (int32_t e = beg + lane; e < end; e += 32) acc += (double)(val ? val[e] : 1.0f) * v[colidx[e]];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            const double wi = strength[i] * v[i] - acc;
+            w[i] = wi;
+            dot += wi * v[i];
+        }
+    }
+    block_dot_store<256>(dot, part);
+}
+
+// w -= alpha[k] v + beta[k] vp; partial |w|^2.
+__global__ void lanczos_update_kernel(int32_t n, double *w, const double *v, const double *vp, const double *alpha,
+                                      const double *beta, int k, double *part) {
+    const double a = alpha[k], b = (k > 0) ? beta[k - 1] : 0.0;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = w[i] - a * v[i] - (k > 0 ? b * vp[i] : 0.0);
+        w[i] = x;
+        acc += x * x;
+    }
+    block_dot_store<256>(acc, part);
+}
+
+// out[k] = scale-function of the sum of part[0..count)
+__global__ void lanczos_scalar_kernel(const double *part, int count, double *out, int k, int do_sqrt) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < count; t += blockDim.x) acc += part[t];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = do_sqrt ? sqrt(sh[0]) : sh[0];
+}
+
+__global__ void lanczos_scale_kernel(int32_t n, const double *w, const double *nrm, int k, double *v) {
+    const double inv = 1.0 / nrm[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = w[i] * inv;
+}
+
+__global__ void sumsq_kernel(int32_t n, const double *v, double *part) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += v[i] * v[i];
+    block_dot_store<256>(acc, part);
+}
+
+// ------------------------------------------------------------ features
+// One warp per row: per-lane FP32 partial sums of squares combined in FP64,
+// then scale by the FP32-rounded 1/norm; rows of zero norm are written as
+// zeros.
+__global__ void __launch_bounds__(256) features_kernel(const float *Y, int32_t n, int32_t n_sig, int32_t normalize,
+                                                       float *F) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp0; i < n; i += nw) {
+        const float *y = Y + i * n_sig;
+        float *f = F + i * n_sig;
+        if (!normalize) {
+            for (int c = lane; c < n_sig; c += 32) f[c] = y[c];
+            continue;
+        }
+        float part = 0.f;
+        for (int c = lane; c < n_sig; c += 32) part = fmaf(y[c], y[c], part);
+        double ss = (double)part;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        const double nrm = sqrt(ss);
+        const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
+        for (int c = lane; c < n_sig; c += 32) f[c] = y[c] * inv;
+    }
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" {
+
+SF_API sf_status sf_lambda_max_estimate(const sf_graph *g, int32_t iters, const double *v0, uint64_t seed,
+                                        void *stream, double *theta_max, double *lam_hat) {
+    SF_ARG(g, "graph is NULL");
+    SF_ARG(iters >= 1 && iters <= 10000, "iters must be in [1, 10000]");
+    SF_ARG(g->device == current_device(), "graph lives on another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t n = g->n;
+    if (iters > n) iters = n;
+    Scratch sc(s);
+    double *v = nullptr, *vp = nullptr, *w = nullptr, *part = nullptr, *alpha = nullptr, *beta = nullptr,
+           *nrm = nullptr;
+    sf_status st;
+    const int grid = 4 * sm_count();
+    if ((st = sc.get(&v, n)) || (st = sc.get(&vp, n)) || (st = sc.get(&w, n)) || (st = sc.get(&part, grid)) ||
+        (st = sc.get(&alpha, iters)) || (st = sc.get(&beta, iters)) || (st = sc.get(&nrm, 1)))
+        return st;
+    const float *val = g->unit_weights ? nullptr : g->val;
+    lanczos_init_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, v0, seed, n);
+    if ((st = check_launch("lanczos_init_kernel"))) return st;
+    sumsq_kernel<<<grid, 256, 0, s>>>(n, w, part);
+    if ((st = check_launch("sumsq_kernel"))) return st;
+    lanczos_scalar_kernel<<<1, 256, 0, s>>>(part, grid, nrm, 0, 1);
+    if ((st = check_launch("lanczos_scalar_kernel"))) return st;
+    lanczos_scale_kernel<<<grid, 256, 0, s>>>(n, w, nrm, 0, v);
+    if ((st = check_launch("lanczos_scale_kernel"))) return st;
+    for (int k = 0; k < iters; ++k) {
+        lap_spmv_f64_kernel<<<grid, 256, 0, s>>>(n, g->rowptr, g->colidx, val, g->strength, v, w, part);
+        if ((st = check_launch("lap_spmv_f64_kernel"))) return st;
+        lanczos_scalar_kernel<<<1, 256, 0, s>>>(part, grid, alpha, k, 0);
+        if ((st = check_launch("lanczos_scalar_kernel"))) return st;
+        if (k + 1 == iters) break;
+        lanczos_update_kernel<<<grid, 256, 0, s>>>(n, w, v, vp, alpha, beta, k, part);
+        if ((st = check_launch("lanczos_update_kernel"))) return st;
+        lanczos_scalar_kernel<<<1, 256, 0, s>>>(part, grid, beta, k, 1);
+        if ((st = check_launch("lanczos_scalar_kernel"))) return st;
+        // vp <- v, v <- w / beta_k (rotate buffers: the old vp becomes the new v)
+        std::swap(vp, v);
+        lanczos_scale_kernel<<<grid, 256, 0, s>>>(n, w, beta, k, v);
+        if ((st = check_launch("lanczos_scale_kernel"))) return st;
+    }
+    std::vector<double> a((size_t)iters), b((size_t)iters);
+    SF_CHECK_CUDA(cudaMemcpyAsync(a.data(), alpha, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+    SF_CHECK_CUDA(cudaMemcpyAsync(b.data(), beta, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    // keep the leading part of the tridiagonal before the Krylov space is exhausted
+    int k = iters;
+    double scale = 0.0;
+    for (int j = 0; j < iters; ++j) {
+        if (!isfinite(a[j])) {
+            k = j;
+            break;
+        }
+        scale = fmax(scale, fabs(a[j]));
+        if (j + 1 < iters) {
+            if (!isfinite(b[j]) || b[j] <= 1e-12 * fmax(scale, b[j])) {
+                k = j + 1;
+                break;
+            }
+            scale = fmax(scale, b[j]);
+        }
+    }
+    if (k < 1) {
+        set_error("Lanczos produced no finite coefficient (graph values not finite?)");
+        return SF_ERR_NUMERIC;
+    }
+    const double th = tridiag_max_eig_host(k, a.data(), b.data());
+    if (theta_max) *theta_max = th;
+    if (lam_hat) {
+        double lh = fmin(1.01 * th, 2.0 * g->max_strength);
+        *lam_hat = lh > 0.0 ? lh : 1.0;
+    }
+    return SF_OK;
+}
+
+SF_API sf_status sf_features(const float *Y, int32_t n, int32_t n_sig, int32_t normalize, float *F,
+                             void *stream) {
+    SF_ARG(Y && F, "Y/F is NULL");
+    SF_ARG(n >= 0 && n_sig >= 1, "need n >= 0 and n_sig >= 1");
+    if (n == 0) return SF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t warps = n;
+    int64_t grid = (warps * 32 + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (grid > cap) grid = cap;
+    features_kernel<<<(unsigned)grid, 256, 0, s>>>(Y, n, n_sig, normalize, F);
+    return check_launch("features_kernel");
+}
+
+}  // extern "C"

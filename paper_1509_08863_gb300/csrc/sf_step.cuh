@@ -1,0 +1,351 @@
+// The per-order sweep kernel: one sparse product with Lt = (2/lam) L - I
+// fused with the three-term Chebyshev recurrence and its epilogue
+// (coefficient accumulation, Clenshaw addend, or moment dot products).
+//
+// Layout: the signal block is processed in column slabs. A slab buffer is
+// row-major [N][ld] with ld = LPR * VEC elements, so one row of the slab is
+// LPR lanes x 16 bytes. One warp owns one row at a time; its 32 lanes form
+// NG = 32 / LPR groups, each group reading a different neighbour's 16-byte
+// chunks, so a warp keeps U * NG neighbour rows in flight. The groups' partial
+// sums are combined with a butterfly of shuffles and group 0 runs the
+// epilogue for the row.
+#pragma once
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+// ------------------------------------------------------------ 16-byte vectors
+template <typename TS>
+struct VT;
+
+template <>
+struct VT<float> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void ld_gather(const float *p, float (&x)[4]) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    __device__ __forceinline__ static void ld_stream(const float *p, float (&x)[4]) {
+        float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    __device__ __forceinline__ static void st(float *p, const float (&x)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+    // value as it is stored (identity for fp32)
+    __device__ __forceinline__ static float rt(float x) { return x; }
+    __device__ __forceinline__ static float from(float x) { return x; }
+};
+
+template <>
+struct VT<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void unpack(uint4 v, float (&x)[8]) {
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __bfloat1622float2(h[k]);
+            x[2 * k] = f.x;
+            x[2 * k + 1] = f.y;
+        }
+    }
+    __device__ __forceinline__ static void ld_gather(const __nv_bfloat16 *p, float (&x)[8]) {
+        unpack(__ldg(reinterpret_cast<const uint4 *>(p)), x);
+    }
+    __device__ __forceinline__ static void ld_stream(const __nv_bfloat16 *p, float (&x)[8]) {
+        unpack(__ldcs(reinterpret_cast<const uint4 *>(p)), x);
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, const float (&x)[8]) {
+        uint4 v;
+        __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+        *reinterpret_cast<uint4 *>(p) = v;
+    }
+    __device__ __forceinline__ static float rt(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+};
+
+// ------------------------------------------------------------ parameters
+enum StepMode { MODE_FWD = 0, MODE_MOM = 1, MODE_CLEN = 2 };
+
+struct StepParams {
+    int32_t n;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const float *val;       // nullptr: all weights 1
+    const float *dtil;      // per row: 2 s_i / lam - 1
+    const float *wscale;    // per row 2 / lam (batches) or nullptr
+    float wscale_u;         // uniform 2 / lam
+    const int32_t *gid;     // per-row graph id (batches) or nullptr
+    int32_t ld;             // slab row stride in elements
+    const void *X;          // T_{j-1} (forward) or b_{j+1} (Clenshaw): gathered
+    const void *Z;          // T_{j-2} or b_{j+2}: subtracted (nullptr: none)
+    const void *Q;          // Clenshaw addend block (packed R or G)
+    void *out;              // T_j or b_j (storage type)
+    float *outf;            // Clenshaw final: fp32 output instead of `out`
+    float m;                // 2 (general order) or 1 (first order / final Clenshaw step)
+    // forward accumulation
+    float *Y;               // n_cut accumulators [n_cut][N][ld] fp32
+    int64_t ystride;        // N * ld
+    int32_t n_cut;
+    const float *coef;      // [graphs][n_cut][coef_ld]
+    int32_t coef_ld;        // p + 1
+    int32_t j;              // coefficient index used by this order
+    // moments
+    double *part;           // [gridDim.x][2]: sum t.t, sum t.x
+};
+
+// ------------------------------------------------------------ the sweep
+template <typename TS, int LPR, int MODE>
+__global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
+    using V = VT<TS>;
+    constexpr int VEC = V::V;
+    constexpr int NG = 32 / LPR;
+    constexpr int U = (NG == 1) ? 8 : 4;
+    __shared__ double red[8][2];
+    const int lane = threadIdx.x & 31;
+    const int q = lane % LPR, grp = lane / LPR;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const TS *__restrict__ X = static_cast<const TS *>(P.X);
+    const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
+    const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
+    TS *__restrict__ out = static_cast<TS *>(P.out);
+    const int32_t ld = P.ld;
+    double mtt = 0.0, mtx = 0.0;
+
+    for (int64_t i = warp0; i < P.n; i += nwarps) {
+        const int32_t beg = __ldg(P.rowptr + i), end = __ldg(P.rowptr + i + 1);
+        float acc[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+        for (int32_t base = beg; base < end; base += U * NG) {
+            int32_t k[U];
+            float wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t e = base + u * NG + grp;
+                const bool ok = e < end;
+                k[u] = ok ? __ldcs(P.colidx + e) : -1;
+                wv[u] = ok ? (P.val ? __ldcs(P.val + e) : 1.0f) : 0.0f;
+            }
+            float xv[U][VEC];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (k[u] >= 0) {
+                    V::ld_gather(X + (int64_t)k[u] * ld + q * VEC, xv[u]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) xv[u][v] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[u][v], acc[v]);
+        }
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+
+        if (grp == 0) {
+            const int64_t ro = i * ld + q * VEC;
+            float xi[VEC], t[VEC];
+            V::ld_gather(X + ro, xi);
+            const float d = __ldcs(P.dtil + i);
+            const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
+            const int g = P.gid ? __ldcs(P.gid + i) : 0;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) t[v] = P.m * fmaf(d, xi[v], -sc * acc[v]);
+            if (Z) {
+                float z[VEC];
+                V::ld_stream(Z + ro, z);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) t[v] -= z[v];
+            }
+            if (MODE == MODE_CLEN) {
+                const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
+                float qv[VEC];
+                V::ld_stream(Qb + ro, qv);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
+            }
+            if (MODE == MODE_CLEN && P.outf) {
+                float *o = P.outf + ro;
+#pragma unroll
+                for (int v = 0; v < VEC; v += 4)
+                    __stcs(reinterpret_cast<float4 *>(o + v), make_float4(t[v], t[v + 1], t[v + 2], t[v + 3]));
+            } else {
+                V::st(out + ro, t);
+            }
+            if (MODE == MODE_FWD) {
+                for (int c = 0; c < P.n_cut; ++c) {
+                    const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + P.j);
+                    float *y = P.Y + c * P.ystride + ro;
+#pragma unroll
+                    for (int v = 0; v < VEC; v += 4) {
+                        float4 yy = __ldcs(reinterpret_cast<const float4 *>(y + v));
+                        yy.x = fmaf(a, t[v], yy.x);
+                        yy.y = fmaf(a, t[v + 1], yy.y);
+                        yy.z = fmaf(a, t[v + 2], yy.z);
+                        yy.w = fmaf(a, t[v + 3], yy.w);
+                        __stcs(reinterpret_cast<float4 *>(y + v), yy);
+                    }
+                }
+            }
+            if (MODE == MODE_MOM) {
+                float tt = 0.f, tx = 0.f;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const float ts = V::rt(t[v]);  // the value the next order reads
+                    tt = fmaf(ts, ts, tt);
+                    tx = fmaf(ts, xi[v], tx);
+                }
+#pragma unroll
+                for (int off = 1; off < LPR; off <<= 1) {
+                    tt += __shfl_xor_sync((LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u), tt, off);
+                    tx += __shfl_xor_sync((LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u), tx, off);
+                }
+                if (q == 0) {
+                    mtt += (double)tt;
+                    mtx += (double)tx;
+                }
+            }
+        }
+    }
+    if (MODE == MODE_MOM) {
+        const int w = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[w][0] = mtt;
+            red[w][1] = mtx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                a += red[k][0];
+                b += red[k][1];
+            }
+            P.part[2 * blockIdx.x] = a;
+            P.part[2 * blockIdx.x + 1] = b;
+        }
+    }
+}
+
+// ------------------------------------------------------------ pack / unpack
+// T0 = R slab converted to the storage type (zero padded to ld columns).
+// Optionally: Y_c = a_c0 * T0 (forward), b_p = a_p * T0 (Clenshaw start,
+// written to `bstart`), and per-block partial sum of T0.T0 (moments).
+template <typename TS>
+__global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0, int32_t w,
+                            int32_t ld, TS *T0, float *Y, int64_t ystride, int32_t n_cut, const float *coef,
+                            int32_t coef_ld, int32_t jcoef, const int32_t *gid, TS *bstart, double *part) {
+    __shared__ double red[256];
+    const int64_t total = (int64_t)n * ld;
+    double acc = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / ld;
+        const int32_t c = (int32_t)(idx - i * ld);
+        float x = 0.f;
+        if (c < w) {
+            const int64_t src = i * n_sig + c0 + c;
+            x = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
+                                     : static_cast<const float *>(R)[src];
+        }
+        TS xs;
+        if constexpr (sizeof(TS) == 4) xs = x;
+        else xs = __float2bfloat16_rn(x);
+        T0[idx] = xs;
+        const float xr = VT<TS>::rt(x);
+        acc += (double)xr * (double)xr;
+        const int g = gid ? gid[i] : 0;
+        if (Y) {
+            for (int k = 0; k < n_cut; ++k) {
+                const float a = coef[((int64_t)g * n_cut + k) * coef_ld + jcoef];
+                Y[k * ystride + idx] = a * xr;
+            }
+        }
+        if (bstart) {
+            const float a = coef[(int64_t)g * coef_ld + jcoef];
+            if constexpr (sizeof(TS) == 4) bstart[idx] = a * xr;
+            else bstart[idx] = __float2bfloat16_rn(a * xr);
+        }
+    }
+    if (part) {
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    }
+}
+
+// Y_out[c][i][c0 + col] = Yslab[c][i][col] for col < w.
+static __global__ void unpack_kernel(const float *Yslab, int32_t n, int32_t ld, int32_t w, int32_t n_cut,
+                              float *Y, int32_t n_sig, int32_t c0) {
+    const int64_t total = (int64_t)n_cut * n * w;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cc = idx / ((int64_t)n * w);
+        const int64_t rem = idx - cc * n * w;
+        const int64_t i = rem / w;
+        const int32_t col = (int32_t)(rem - i * w);
+        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * n + i) * ld + col);
+    }
+}
+
+// d~_i = 2 s_i / lam - 1 (uniform lam) or per-graph lam (batches); also
+// writes 2 / lam per row for batches.
+static __global__ void dtil_kernel(const double *s, int32_t n, double two_over_lam, const int32_t *gid,
+                            const double *two_over_lam_g, float *dtil, float *wscale) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double tl = gid ? two_over_lam_g[gid[i]] : two_over_lam;
+    dtil[i] = (float)(tl * s[i] - 1.0);
+    if (wscale) wscale[i] = (float)tl;
+}
+
+// Sum the [count][2] partials in a fixed order and add into out[0..1].
+static __global__ void pair_sum_kernel(const double *part, int32_t count, int32_t stride, double *out) {
+    __shared__ double a[256], b[256];
+    double x = 0.0, y = 0.0;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        x += part[(int64_t)k * stride];
+        if (stride == 2) y += part[(int64_t)k * 2 + 1];
+    }
+    a[threadIdx.x] = x;
+    b[threadIdx.x] = y;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            a[threadIdx.x] += a[threadIdx.x + s];
+            b[threadIdx.x] += b[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] += a[0];
+        if (stride == 2) out[1] += b[0];
+    }
+}
+
+// ------------------------------------------------------------ host side
+struct SweepShape {
+    int storage;      // SF_F32 / SF_BF16
+    int lpr;          // lanes per row-chunk
+    int ld;           // slab columns (= lpr * vec)
+    int block;        // threads per block
+    int grid;         // blocks
+};
+
+// Picks the slab width (columns) for n rows and n_sig signals.
+int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t l2_budget_bytes);
+sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, SweepShape *sh);
+sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes);
+
+}  // namespace sf

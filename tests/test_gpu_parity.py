@@ -1,0 +1,413 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle
+on the same seeded inputs.
+
+Tolerances:
+* CSR (indices and merged weights): bit-exact. Strengths: equal (both sum the
+  same FP32 weights in column order in FP64).
+* Filtered blocks, FP32 storage: relative Frobenius error <= 1e-5 per
+  coefficient set at p = 50 (the stated target); larger p is bounded by
+  the FP32 rounding growth 1e-5 * (p / 50)^1.5 and reported.
+* Moments: |mu_gpu - mu_oracle| <= 2e-6 * (m + 1) * mu_0 (FP32 blocks, FP64
+  reductions); counts derive from them.
+* Features: 1e-6 relative per row; adjoint 2e-4 relative (FP32 over p orders).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from helpers import cliques_edges, dense_laplacian, dense_w, random_graph  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_08863_gb300 import build
+
+    build.build()
+    import paper_1509_08863_gb300 as m
+
+    return m
+
+
+def cuda_edges(src, dst, w=None):
+    s = torch.as_tensor(np.asarray(src, np.int32), device="cuda")
+    d = torch.as_tensor(np.asarray(dst, np.int32), device="cuda")
+    ww = None if w is None else torch.as_tensor(np.asarray(w, np.float32), device="cuda")
+    return s, d, ww
+
+
+def build_both(sf, oracle_mod, n, src, dst, w=None):
+    w32 = None if w is None else np.asarray(w, np.float32)
+    g = sf.csr_build(n, *cuda_edges(src, dst, w32))
+    go = oracle_mod.csr_build(n, src, dst, None if w32 is None else w32.astype(np.float64))
+    return g, go
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def config1_graph():
+    from paper_1509_08863_gb300 import synth
+
+    sizes = synth.community_sizes_equal(1000, 10)
+    return synth.sbm_edges(1000, sizes, 16.0, 0.05, seed=1001)
+
+
+# ------------------------------------------------------------------ CSR
+@pytest.mark.parametrize("seed", [0, 1])
+def test_csr_bitexact_random_multigraph(sf, oracle_mod, seed):
+    n = 777
+    src, dst, w = random_graph(n, 6000, seed, connected=False)
+    src = np.concatenate([src, src[:500], np.arange(50)]).astype(np.int32)   # duplicates
+    dst = np.concatenate([dst, dst[:500], np.arange(50)]).astype(np.int32)   # and self-loops
+    w = np.concatenate([w, np.random.default_rng(seed).uniform(0, 3, 500), np.ones(50)]).astype(np.float32)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    rp, ci, va, st = [t.cpu().numpy() for t in g.csr()]
+    np.testing.assert_array_equal(rp, go.rowptr)
+    np.testing.assert_array_equal(ci, go.colidx)
+    np.testing.assert_array_equal(va, go.val.astype(np.float32))
+    np.testing.assert_array_equal(st, oracle_mod.strength(go))
+    assert g.info()[2] is False
+
+
+def test_csr_order_independent_and_unit_flag(sf, oracle_mod):
+    gr = config1_graph()
+    g1 = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst, gr.w))
+    perm = np.random.default_rng(5).permutation(gr.n_edges)
+    g2 = sf.csr_build(gr.n, *cuda_edges(gr.dst[perm], gr.src[perm], gr.w[perm]))
+    for a, b in zip(g1.csr(), g2.csr()):
+        assert torch.equal(a, b)
+    go = oracle_mod.csr_build(gr.n, gr.src, gr.dst, gr.w)
+    np.testing.assert_array_equal(g1.csr()[1].cpu().numpy(), go.colidx)
+    assert g1.info()[2] is True
+
+
+def test_csr_edge_cases(sf, oracle_mod):
+    # no edges, one node
+    g = sf.csr_build(1, *cuda_edges(np.zeros(0), np.zeros(0)))
+    assert g.info()[:2] == (1, 0)
+    # only self-loops and isolated nodes
+    g = sf.csr_build(9, *cuda_edges([1, 1, 4], [1, 1, 4]))
+    assert g.info()[1] == 0 and list(g.csr()[0].cpu().numpy()) == [0] * 10
+    # a hub row far longer than a warp or a tile
+    n = 70000
+    src = np.zeros(n - 1, np.int32)
+    dst = np.arange(1, n, dtype=np.int32)
+    g, go = build_both(sf, oracle_mod, n, src, dst)
+    np.testing.assert_array_equal(g.csr()[1].cpu().numpy(), go.colidx)
+    np.testing.assert_array_equal(g.csr()[0].cpu().numpy(), go.rowptr)
+
+
+def test_csr_rejects_bad_input(sf):
+    with pytest.raises(sf.SpecFiltError) as e:
+        sf.csr_build(5, *cuda_edges([0, 1], [1, 5]))
+    assert e.value.status == 1
+    with pytest.raises(sf.SpecFiltError):
+        sf.csr_build(5, *cuda_edges([0, 1], [1, 2], [1.0, -1.0]))
+    with pytest.raises(sf.SpecFiltError):
+        sf.csr_build(5, *cuda_edges([0, 1], [1, 2], [1.0, float("inf")]))
+
+
+# ------------------------------------------------------------------ lambda_N
+def test_lambda_max_matches_oracle_and_bounds(sf, oracle_mod):
+    n = 600
+    src, dst, w = random_graph(n, 5000, 3)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    v0 = np.random.default_rng(0).standard_normal(n)
+    th, lh = sf.lambda_max_estimate(g, 60, torch.as_tensor(v0, device="cuda"))
+    tho = oracle_mod.lanczos_max(go, 60, v0)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, np.asarray(dst), np.asarray(w, np.float32))))[-1]
+    assert abs(th - tho) <= 1e-9 * tho
+    assert abs(th - lam) <= 1e-8 * lam
+    assert lam <= lh <= 2 * oracle_mod.strength(go).max() * (1 + 1e-12)
+    assert lh == pytest.approx(oracle_mod.lambda_hat(tho, oracle_mod.strength(go)), rel=1e-12)
+    # seeded start vector (no v0) converges too
+    th2, _ = sf.lambda_max_estimate(g, 60, None, seed=7)
+    assert abs(th2 - lam) <= 1e-8 * lam
+
+
+def test_lambda_max_closed_forms(sf):
+    # complete graph K_n and star S_n: lambda_N = n
+    for n, (s, d) in [(13, np.triu_indices(13, 1)), (40, (np.zeros(39, int), np.arange(1, 40)))]:
+        g = sf.csr_build(n, *cuda_edges(s, d))
+        th, _ = sf.lambda_max_estimate(g, n, None, seed=3)
+        assert abs(th - n) <= 1e-9 * n
+
+
+# ------------------------------------------------------------------ filter
+def _setup_config1(sf, oracle_mod):
+    gr = config1_graph()
+    g, go = build_both(sf, oracle_mod, gr.n, gr.src, gr.dst, gr.w)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(gr.n, gr.src, gr.dst)))
+    from paper_1509_08863_gb300 import synth
+
+    R = synth.gaussian_block(gr.n, 14, seed=2001)
+    th, lh = sf.lambda_max_estimate(g, 60, None, seed=1)
+    return gr, g, go, lam, R, lh
+
+
+@pytest.mark.parametrize("algo", ["forward", "clenshaw"])
+@pytest.mark.parametrize("slab", [0, 8, 32])
+def test_filter_config1_fp32_within_1e5(sf, oracle_mod, algo, slab):
+    gr, g, go, lam, R, lh = _setup_config1(sf, oracle_mod)
+    p, k = 50, 10
+    a = oracle_mod.cheb_coeffs(lh, lam[k - 1], p, True)  # lambda_c = true lambda_k
+    Yo = oracle_mod.cheb_filter(go, lh, a, R)[0]
+    opts = sf.Opts(algo=sf.ALGO_FORWARD if algo == "forward" else sf.ALGO_CLENSHAW, slab_cols=slab)
+    Y = sf.cheb_filter(g, lh, a, torch.as_tensor(R, dtype=torch.float32, device="cuda"), opts)[0]
+    err = rel(Y.cpu().numpy(), Yo)
+    assert err <= 1e-5, err
+
+
+def test_filter_multi_cutoff_ragged(sf, oracle_mod):
+    n, n_sig, p = 3001, 37, 23
+    src, dst, w = random_graph(n, 20000, 9)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    _, lh = sf.lambda_max_estimate(g, 40, None, seed=2)
+    R = np.random.default_rng(4).standard_normal((n, n_sig)) / math.sqrt(n_sig)
+    a = oracle_mod.cheb_coeffs(lh, [0.05 * lh, 0.2 * lh, 0.7 * lh], p, True)
+    Yo = oracle_mod.cheb_filter(go, lh, a, R)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    for slab in (8, 16, 64):
+        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(algo=sf.ALGO_FORWARD, slab_cols=slab)).cpu().numpy()
+        for c in range(3):
+            assert rel(Y[c], Yo[c]) <= 1e-5
+        Yc = sf.cheb_filter(g, lh, a, Rt, sf.Opts(algo=sf.ALGO_CLENSHAW, slab_cols=slab)).cpu().numpy()
+        for c in range(3):
+            assert rel(Yc[c], Yo[c]) <= 1e-5
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+def test_filter_low_orders(sf, oracle_mod, p):
+    n = 500
+    src, dst, w = random_graph(n, 3000, 12)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    R = np.random.default_rng(1).standard_normal((n, 10))
+    a = np.random.default_rng(2).standard_normal((2, p + 1))
+    Yo = oracle_mod.cheb_filter(go, lh, a, R)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(algo=algo)).cpu().numpy()
+        for c in range(2):
+            assert rel(Y[c], Yo[c]) <= 2e-6
+
+
+def test_filter_empty_rows_and_bf16_input(sf, oracle_mod):
+    n = 1200
+    src, dst, w = random_graph(n // 2, 3000, 21)  # upper half of the nodes isolated
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    R = np.random.default_rng(3).standard_normal((n, 16)).astype(np.float32)
+    Rb = torch.as_tensor(R, device="cuda").to(torch.bfloat16)
+    Rr = Rb.float().cpu().numpy().astype(np.float64)  # the values the GPU sees
+    a = oracle_mod.cheb_coeffs(lh, 0.3 * lh, 30, True)
+    Yo = oracle_mod.cheb_filter(go, lh, a, Rr)[0]
+    Y = sf.cheb_filter(g, lh, a, Rb)[0].cpu().numpy()
+    assert rel(Y, Yo) <= 1e-5
+    # isolated rows: Lt x = -x, so Y_i = sum_j a_j T_j(-1) r_i
+    iso = np.arange(n // 2, n)
+    fac = np.polynomial.chebyshev.chebval(-1.0, a[0])
+    np.testing.assert_allclose(Y[iso], fac * Rr[iso], rtol=1e-5, atol=1e-6)
+
+
+def test_filter_bf16_storage_error(sf, oracle_mod):
+    """BF16 blocks, FP32 accumulation: error against the oracle fed the
+    BF16-rounded R stays below the bound 2^-8 * sqrt(p) (one BF16 rounding
+    per order, accumulated as independent errors), and against the FP64 R."""
+    gr, g, go, lam, R, lh = _setup_config1(sf, oracle_mod)
+    p = 50
+    a = oracle_mod.cheb_coeffs(lh, 0.5 * (lam[9] + lam[10]), p, True)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    Rr = Rt.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    Yo_r = oracle_mod.cheb_filter(go, lh, a, Rr)[0]
+    for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.BF16, algo=algo))[0].cpu().numpy()
+        err = rel(Y, Yo_r)
+        assert err <= 2.0 ** -8 * math.sqrt(p), (algo, err)
+
+
+# ------------------------------------------------------------------ moments / count
+def test_moments_and_counts_match_oracle(sf, oracle_mod):
+    from paper_1509_08863_gb300 import synth
+
+    n, eta, p = 2000, 24, 40
+    sizes = synth.community_sizes_uniform(n, 8, 100, 400, seed=1)
+    gr = synth.sbm_edges(n, sizes, 12.0, 0.1, seed=2)
+    g, go = build_both(sf, oracle_mod, n, gr.src, gr.dst, gr.w)
+    _, lh = sf.lambda_max_estimate(g, 50, None, seed=1)
+    R = synth.gaussian_block(n, eta, seed=3)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    mu = sf.cheb_moments(g, lh, Rt, p)
+    muo = oracle_mod.moments(go, lh, R, 2 * p)
+    for m in range(2 * p + 1):
+        assert abs(mu[m] - muo[m]) <= 2e-6 * (m + 1) * muo[0], (m, mu[m], muo[m])
+    cuts = np.linspace(0.0, 0.2 * lh, 16)
+    counts, _ = sf.eigencount(g, lh, Rt, p, cuts, True)
+    a = oracle_mod.cheb_coeffs(lh, cuts, p, True)
+    co = oracle_mod.eigencount(go, lh, a, R)
+    bound = 2e-6 * (2 * p + 1) * muo[0] * np.sum(np.abs(a), axis=1) ** 2
+    assert np.all(np.abs(counts - co) <= bound), (counts, co)
+    # slabs and blocks per SM do not change the moments beyond rounding
+    mu2 = sf.cheb_moments(g, lh, Rt, p, sf.Opts(slab_cols=8))
+    np.testing.assert_allclose(mu2, mu, rtol=0, atol=1e-9 * muo[0])
+
+
+def test_moments_deterministic(sf, oracle_mod):
+    gr = config1_graph()
+    g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst, gr.w))
+    R = torch.randn(gr.n, 14, device="cuda")
+    m1 = sf.cheb_moments(g, 70.0, R, 30)
+    m2 = sf.cheb_moments(g, 70.0, R, 30)
+    np.testing.assert_array_equal(m1, m2)
+
+
+def test_dichotomy_finds_gap_on_cliques(sf, oracle_mod):
+    k, m, eta, p = 6, 12, 128, 120
+    src, dst = cliques_edges(k, m)
+    rng = np.random.default_rng(0)
+    src = np.concatenate([src, rng.integers(0, k * m, 8)]).astype(np.int32)
+    dst = np.concatenate([dst, rng.integers(0, k * m, 8)]).astype(np.int32)
+    n = k * m
+    g, go = build_both(sf, oracle_mod, n, src, dst)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, dst)))
+    _, lh = sf.lambda_max_estimate(g, n, None, seed=1)
+    R = np.random.default_rng(1).standard_normal((n, eta)) / math.sqrt(eta)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    mu = sf.cheb_moments(g, lh, Rt, p)
+    lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
+    lk_o = oracle_mod.dichotomy(go, lh, p, R, k - 0.5, True, 40, 1e-9)
+    assert lam[k - 1] < lk < lam[k] and lam[k - 1] < lk_o < lam[k]
+    assert abs(lk - lk_o) <= 0.05 * (lam[k] - lam[k - 1])
+
+
+# ------------------------------------------------------------------ features
+def test_features_match_oracle(sf, oracle_mod):
+    rng = np.random.default_rng(8)
+    Y = rng.standard_normal((3001, 37)).astype(np.float32)
+    Y[[0, 17, 3000]] = 0.0
+    Fo = oracle_mod.features(Y.astype(np.float64), True)
+    F = sf.features(torch.as_tensor(Y, device="cuda"), True).cpu().numpy()
+    nr = np.linalg.norm(Fo, axis=1)
+    np.testing.assert_allclose(F, Fo, rtol=0, atol=1e-6 * max(nr.max(), 1))
+    assert np.all(F[[0, 17, 3000]] == 0)
+    F0 = sf.features(torch.as_tensor(Y, device="cuda"), False).cpu().numpy()
+    np.testing.assert_array_equal(F0, Y)
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("ckpt", [1, 3])
+def test_backward_matches_oracle(sf, oracle_mod, ckpt):
+    n, n_sig, p = 400, 12, 17
+    src, dst, w = random_graph(n, 2500, 31)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((n, n_sig)).astype(np.float32)
+    G = rng.standard_normal((n, n_sig)).astype(np.float32)
+    a = oracle_mod.cheb_coeffs(lh, 0.25 * lh, p, True)[0]
+    gv_o, ga_o, gR_o = oracle_mod.cheb_filter_backward(go, lh, a, R.astype(np.float64), G.astype(np.float64), True)
+    gv, ga, gR = sf.cheb_filter_backward(g, lh, a, torch.as_tensor(R, device="cuda"), torch.as_tensor(G, device="cuda"),
+                                         True, sf.Opts(ckpt_every=ckpt, slab_cols=16))
+    assert rel(gv.cpu().numpy(), gv_o) <= 2e-4
+    assert rel(ga, ga_o) <= 2e-5
+    assert rel(gR.cpu().numpy(), gR_o) <= 2e-5
+
+
+def test_backward_checkpoint_equals_store(sf, oracle_mod):
+    n, n_sig, p = 900, 20, 30
+    src, dst, w = random_graph(n, 6000, 41)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    R = torch.randn(n, n_sig, device="cuda")
+    G = torch.randn(n, n_sig, device="cuda")
+    a = np.random.default_rng(0).standard_normal(p + 1) * 0.1
+    out1 = sf.cheb_filter_backward(g, lh, a, R, G, True, sf.Opts(ckpt_every=1))
+    out2 = sf.cheb_filter_backward(g, lh, a, R, G, True, sf.Opts(ckpt_every=6))
+    assert torch.equal(out1[0], out2[0]) and torch.equal(out1[2], out2[2])
+    np.testing.assert_array_equal(out1[1], out2[1])
+
+
+def test_autograd_function(sf, oracle_mod):
+    n, n_sig, p = 300, 8, 12
+    src, dst, w = random_graph(n, 1500, 51)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    val = g.csr()[2].clone().requires_grad_(True)
+    coeffs = torch.tensor(oracle_mod.cheb_coeffs(lh, 0.3 * lh, p, True)[0], dtype=torch.float64,
+                          requires_grad=True)
+    R = torch.randn(n, n_sig, device="cuda", requires_grad=True)
+    Y = sf.ChebFilter(val, coeffs, R, g, lh)
+    G = torch.randn_like(Y)
+    (Y * G).sum().backward()
+    gv_o, ga_o, gR_o = oracle_mod.cheb_filter_backward(go, lh, coeffs.detach().numpy(),
+                                                       R.detach().cpu().double().numpy(),
+                                                       G.cpu().double().numpy(), True)
+    assert rel(val.grad.cpu().numpy(), gv_o) <= 2e-4
+    assert rel(coeffs.grad.numpy(), ga_o) <= 2e-5
+    assert rel(R.grad.cpu().numpy(), gR_o) <= 2e-5
+
+
+# ------------------------------------------------------------------ batches
+def test_batched_matches_oracle_and_single_launches(sf, oracle_mod):
+    from paper_1509_08863_gb300 import synth
+
+    graphs, ks = synth.batched_sbm(5, seed=77, n_lo=300, n_hi=2500, k_lo=2, k_hi=6)
+    gs, gos, lams = [], [], []
+    for gr in graphs:
+        g, go = build_both(sf, oracle_mod, gr.n, gr.src, gr.dst, gr.w)
+        gs.append(g)
+        gos.append(go)
+        lams.append(sf.lambda_max_estimate(g, 40, None, seed=1)[1])
+    b = sf.batch_build(gs)
+    n_tot, nnz_tot, ng, offs = b.info()
+    assert ng == 5 and n_tot == sum(gr.n for gr in graphs)
+    p, n_sig = 30, 32
+    coeffs = np.stack([oracle_mod.cheb_coeffs(lams[i], (0.02 + 0.03 * i) * lams[i], p, True)[0] for i in range(5)])
+    R = np.random.default_rng(9).standard_normal((n_tot, n_sig)) / math.sqrt(n_sig)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    for algo in (sf.ALGO_CLENSHAW, sf.ALGO_FORWARD):
+        opts = sf.Opts(algo=algo, slab_cols=32)
+        Y = sf.cheb_filter_batched(b, lams, coeffs, Rt, opts)
+        for i in range(5):
+            sl = slice(int(offs[i]), int(offs[i + 1]))
+            Yo = oracle_mod.cheb_filter(gos[i], lams[i], coeffs[i], R[sl])[0]
+            assert rel(Y[sl].cpu().numpy(), Yo) <= 1e-5
+            Ys = sf.cheb_filter(gs[i], lams[i], coeffs[i], Rt[sl].contiguous(), opts)[0]
+            assert torch.equal(Ys, Y[sl])  # same per-row arithmetic, bit for bit
+
+
+# ------------------------------------------------------------------ misc
+def test_argument_errors(sf):
+    gr = config1_graph()
+    g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst))
+    R = torch.randn(gr.n, 4, device="cuda")
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter(g, -1.0, np.ones((1, 3)), R)
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter(g, 10.0, np.ones((1, 3)), R, sf.Opts(storage=sf.F16))
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter(g, 10.0, np.array([[1.0, float("nan")]]), R)
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter(g, 10.0, np.ones((1, 3)), R, sf.Opts(slab_cols=12))
+
+
+def test_autotune_and_profile(sf, oracle_mod):
+    gr = config1_graph()
+    g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst))
+    best = sf.autotune(g, 14, sf.F32, 1)
+    assert best.slab_cols in (8, 16)
+    R = torch.randn(gr.n, 14, device="cuda")
+    sf.profile_begin()
+    n0 = sf.launch_count()
+    sf.cheb_filter(g, 70.0, np.ones((1, 11)) * 0.1, R, best)
+    n_l, ms, by = sf.profile_end()
+    assert n_l == 10 and ms > 0 and by > 0
+    assert sf.launch_count() - n0 >= 12

@@ -1,0 +1,77 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every declared
+entry point, and its host-only FP64 logic (coefficients, counts from
+moments, dichotomy, status strings) agrees with the oracle. No GPU work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sflib():
+    from paper_1509_08863_gb300 import build
+
+    build.build()
+    import paper_1509_08863_gb300 as sf
+
+    return sf
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"SF_API\s+[^;{(]*?\b(sf_\w+)\s*\(", txt, flags=re.S))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(sflib):
+    names = declared_symbols()
+    assert len(names) >= 20, names
+    L = C.CDLL(sflib.LIB_PATH)
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+def test_status_strings(sflib):
+    L = sflib.lib()
+    assert L.sf_status_str(0) == b"SF_OK"
+    assert b"invalid argument" in L.sf_status_str(1)
+    assert L.sf_version() >= 100
+
+
+def test_host_coefficients_match_oracle(sflib, oracle_mod):
+    for lam, cuts, p, jk in [(7.5, [0.3, 2.0, 7.5], 40, True), (1.0, [0.0, 0.5], 7, False), (3.0, [1.2], 200, True)]:
+        a = sflib.cheb_coeffs(lam, cuts, p, jk)
+        b = oracle_mod.cheb_coeffs(lam, cuts, p, jk)
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-15)
+
+
+def test_host_count_from_moments_and_dichotomy(sflib, oracle_mod):
+    from helpers import cliques_edges
+
+    k, m, eta, p = 4, 7, 120, 60
+    src, dst = cliques_edges(k, m)
+    g = oracle_mod.csr_build(k * m, src, dst)
+    lam = 1.01 * m
+    R = np.random.default_rng(2).standard_normal((k * m, eta)) / np.sqrt(eta)
+    mu = oracle_mod.moments(g, lam, R, 2 * p)
+    a = oracle_mod.cheb_coeffs(lam, [0.5, 3.0, 6.0], p, True)
+    np.testing.assert_allclose(sflib.count_from_moments(mu, p, a), oracle_mod.count_from_moments(mu, a), rtol=1e-12)
+    lk = sflib.dichotomy(mu, p, lam, k - 0.5, True, 40, 1e-9)
+    lo = oracle_mod.dichotomy(g, lam, p, R, k - 0.5, True, 40, 1e-9)
+    assert abs(lk - lo) <= 2e-9 * lam * 4
+
+
+def test_argument_errors_without_gpu(sflib):
+    L = sflib.lib()
+    out = np.zeros(3)
+    cut = np.array([0.5])
+    st = L.sf_cheb_coeffs(-1.0, cut.ctypes.data_as(C.POINTER(C.c_double)), 1, 2, 1,
+                          out.ctypes.data_as(C.POINTER(C.c_double)))
+    assert st == 1 and b"lam_max" in L.sf_last_error()
