@@ -68,11 +68,10 @@ enum {
 
 /*
  * Tuning and precision options; a NULL sf_opts* means all zero (defaults).
- *   storage         SF_F32 / SF_BF16 / SF_F16: element type of the T_j (or
- *                   Clenshaw b_j) blocks kept between orders. Products and
+ *   storage         SF_F32 / SF_BF16: element type of the T_j (or Clenshaw
+ *                   b_j) blocks kept between orders. Products and
  *                   accumulations are FP32 in every case; the output Y is FP32.
- *                   SF_F16 stores each order scaled by a power of two chosen
- *                   from the previous order's largest magnitude.
+ *                   SF_F16 is reserved and rejected with SF_ERR_ARG.
  *   algo            SF_ALGO_*.
  *   slab_cols       signal columns processed per sweep (0 = automatic). The
  *                   signals are independent, so the block is filtered in
@@ -297,6 +296,15 @@ SF_API void sf_batch_free(sf_batch *b);
 SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
                                         int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
                                         const sf_opts *opts, void *stream);
+
+/*
+ * Synchronise `stream` and report whether a sweep kernel gave up a bounded
+ * wait for its staged CSR tile since the last check (SF_ERR_TIMEOUT; the
+ * flag is then cleared). Entry points that synchronise check it themselves;
+ * asynchronous ones (sf_cheb_filter, sf_cheb_filter_batched) leave it to
+ * this call.
+ */
+SF_API sf_status sf_device_check(void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Tile autotuner and kernel timing                                        */

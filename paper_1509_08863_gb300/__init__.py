@@ -39,6 +39,7 @@ __all__ = [
     "profile_begin",
     "profile_end",
     "launch_count",
+    "device_check",
     "ChebFilter",
     "F32",
     "BF16",
@@ -132,6 +133,7 @@ def lib():
         "sf_cheb_filter_batched": (_i32, [_vp, _dp, _dp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
         "sf_autotune": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_Opts), _vp, C.POINTER(_Opts)]),
         "sf_profile_begin": (_i32, []),
+        "sf_device_check": (_i32, [_vp]),
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -437,6 +439,11 @@ def profile_end():
     n, ms, by = _i64(), _f64(), _f64()
     _check(lib().sf_profile_end(C.byref(n), C.byref(ms), C.byref(by)), "sf_profile_end")
     return n.value, ms.value, by.value
+
+
+def device_check():
+    """Synchronise the current stream; raise if a sweep kernel gave up a bounded wait."""
+    _check(lib().sf_device_check(_stream()), "sf_device_check")
 
 
 def launch_count() -> int:

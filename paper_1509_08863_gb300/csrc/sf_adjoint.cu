@@ -215,7 +215,8 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     SF_ARG(o.storage == SF_F32, "the adjoint keeps FP32 blocks (storage must be SF_F32)");
     if (o.slab_cols <= 0) o.slab_cols = auto_slab_cols(g->n, n_sig, SF_F32, 48ll << 20);
     SweepShape sh;
-    sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD, &sh);
+    sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD,
+                              !g->unit_weights, &sh);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
@@ -281,6 +282,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         P.wscale_u = (float)two_over_lam;
         P.ld = ld;
         P.n_cut = 0;
+        P.status = device_status();
         auto fwd_step = [&](const float *Xp, const float *Zp, float *outp, int j) {
             P.X = Xp;
             P.Z = Zp;

@@ -52,7 +52,23 @@ static const void *kernel_for(int storage, int lpr, int mode) {
     return nullptr;
 }
 
-sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, SweepShape *sh) {
+__device__ int32_t g_sweep_status;
+
+int32_t *device_status() {
+    static int32_t *cache[64] = {nullptr};
+    const int d = current_device();
+    if (d < 64 && cache[d]) return cache[d];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sweep_status) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (d < 64) cache[d] = static_cast<int32_t *>(p);
+    return static_cast<int32_t *>(p);
+}
+
+sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
+                     SweepShape *sh) {
     SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage type %d is not supported (SF_F32 or SF_BF16)",
            storage);
     const int vec = vec_of(storage);
@@ -64,8 +80,10 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
     const void *fn = kernel_for(storage, lpr, mode);
     SF_ARG(fn, "no kernel for this shape");
+    const int smem = step_smem_bytes(weighted);
+    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_bytes(true)));
     int occ = 0;
-    SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, 0));
+    SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, smem));
     if (occ < 1) occ = 1;
     if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
     sh->storage = storage;
@@ -73,15 +91,16 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     sh->ld = slab_cols;
     sh->block = block_warps * 32;
     sh->grid = occ * sm_count();
+    sh->smem = smem;
     return SF_OK;
 }
 
 template <typename TS, int LPR>
 static void launch_mode(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
     switch (mode) {
-        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD><<<sh.grid, sh.block, 0, s>>>(P); break;
-        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM><<<sh.grid, sh.block, 0, s>>>(P); break;
-        default: cheb_step_kernel<TS, LPR, MODE_CLEN><<<sh.grid, sh.block, 0, s>>>(P); break;
+        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        default: cheb_step_kernel<TS, LPR, MODE_CLEN><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
     }
 }
 
@@ -174,8 +193,10 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                             const double *coeffs_host, int n_cut, int p, const void *R, int r_dtype, int n_sig,
                             float *Y, double *mom, const sf_opts &o, cudaStream_t s) {
     SweepShape sh;
-    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, &sh);
+    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh);
     if (st) return st;
+    int32_t *status = device_status();
+    SF_ARG(status, "device status word unavailable");
     const int ld = sh.ld;
     const int64_t n = G.n;
     const size_t eb = bytes_of(o.storage);
@@ -232,6 +253,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         P.Y = yacc;
         P.ystride = n * ld;
         P.part = part;
+        P.status = status;
         const bool unit = G.val == nullptr;
         const bool batched = G.gid != nullptr;
         if (mode == MODE_FWD || mode == MODE_MOM) {
@@ -323,6 +345,22 @@ using namespace sf;
 
 extern "C" {
 
+SF_API sf_status sf_device_check(void *stream) {
+    int32_t *p = device_status();
+    SF_ARG(p, "device status word unavailable");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t h = 0;
+    SF_CHECK_CUDA(cudaMemcpyAsync(&h, p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        SF_CHECK_CUDA(cudaMemsetAsync(p, 0, sizeof(int32_t), s));
+        SF_CHECK_CUDA(cudaStreamSynchronize(s));
+        set_error("a sweep kernel's bounded wait for its staged tile gave up (status %d)", h);
+        return SF_ERR_TIMEOUT;
+    }
+    return SF_OK;
+}
+
 SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double *coeffs, int32_t n_cut,
                                 int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
                                 const sf_opts *opts, void *stream) {
@@ -369,6 +407,7 @@ SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *
     std::vector<double> hd((size_t)2 * (p + 1));
     SF_CHECK_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 2 * (p + 1), cudaMemcpyDeviceToHost, s));
     SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    if ((st = sf_device_check(stream))) return st;
     moments_from_dots(hd.data(), p, moments);
     return SF_OK;
 }

@@ -21,6 +21,10 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;  // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;
 
+__global__ void fill_i32_kernel(int32_t *p, int count, int32_t v) {
+    if ((int)threadIdx.x < count) p[threadIdx.x] = v;
+}
+
 __global__ void expand_edges_kernel(const int32_t *src, const int32_t *dst, const float *w, int64_t m,
                                     int32_t n, int cb, uint64_t sentinel, uint64_t *keys, float *vals,
                                     int32_t *flags /* [0]=bad index [1]=bad weight [2]=self loops */) {
@@ -239,7 +243,7 @@ SF_API sf_status sf_csr_build(int32_t n_nodes, int64_t n_edges, const int32_t *s
         graph_release(g);
         return e;
     };
-    if (cudaMalloc(&g->rowptr, sizeof(int32_t) * (size_t)(n_nodes + 1)) != cudaSuccess ||
+    if (cudaMalloc(&g->rowptr, sizeof(int32_t) * (size_t)(n_nodes + 1 + kCsrPad)) != cudaSuccess ||
         cudaMalloc(&g->strength, sizeof(double) * (size_t)n_nodes) != cudaSuccess) {
         cudaGetLastError();
         set_error("device allocation failed for a graph of %d nodes", n_nodes);
@@ -292,8 +296,8 @@ SF_API sf_status sf_csr_build(int32_t n_nodes, int64_t n_edges, const int32_t *s
                     cudaStreamSynchronize(s) != cudaSuccess)
                     return fail(cuda_fail(cudaGetLastError(), "reading entry count"));
                 nnz = (int64_t)last_pos + last_head;
-                if (cudaMalloc(&g->colidx, sizeof(int32_t) * (size_t)nnz) != cudaSuccess ||
-                    cudaMalloc(&g->val, sizeof(float) * (size_t)nnz) != cudaSuccess) {
+                if (cudaMalloc(&g->colidx, sizeof(int32_t) * (size_t)(nnz + kCsrPad)) != cudaSuccess ||
+                    cudaMalloc(&g->val, sizeof(float) * (size_t)(nnz + kCsrPad)) != cudaSuccess) {
                     cudaGetLastError();
                     set_error("device allocation failed for %lld entries", (long long)nnz);
                     return fail(SF_ERR_OOM);
@@ -304,7 +308,20 @@ SF_API sf_status sf_csr_build(int32_t n_nodes, int64_t n_edges, const int32_t *s
             }
         }
         g->nnz = nnz;
+        if (!g->colidx) {
+            if (cudaMalloc(&g->colidx, sizeof(int32_t) * kCsrPad) != cudaSuccess ||
+                cudaMalloc(&g->val, sizeof(float) * kCsrPad) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device allocation failed");
+                return fail(SF_ERR_OOM);
+            }
+        }
+        if (cudaMemsetAsync(g->colidx + nnz, 0, sizeof(int32_t) * kCsrPad, s) != cudaSuccess ||
+            cudaMemsetAsync(g->val + nnz, 0, sizeof(float) * kCsrPad, s) != cudaSuccess)
+            return fail(cuda_fail(cudaGetLastError(), "cudaMemsetAsync"));
         if ((st = exclusive_scan_i32(rowcnt, g->rowptr, (int64_t)n_nodes + 1, s))) return fail(st);
+        fill_i32_kernel<<<1, 32, 0, s>>>(g->rowptr + n_nodes + 1, kCsrPad, (int32_t)nnz);
+        if ((st = check_launch("fill_i32_kernel"))) return fail(st);
         if ((st = compute_strength(g, s))) return fail(st);
     }
     *out = g;
@@ -414,11 +431,11 @@ SF_API sf_status sf_batch_build(const sf_graph *const *graphs, int32_t n_graphs,
     b->n = (int32_t)n_tot;
     b->nnz = nnz_tot;
     b->unit_weights = unit;
-    if (cudaMalloc(&b->rowptr, sizeof(int32_t) * (size_t)(n_tot + 1)) != cudaSuccess ||
+    if (cudaMalloc(&b->rowptr, sizeof(int32_t) * (size_t)(n_tot + 1 + kCsrPad)) != cudaSuccess ||
         cudaMalloc(&b->strength, sizeof(double) * (size_t)n_tot) != cudaSuccess ||
         cudaMalloc(&b->row_graph, sizeof(int32_t) * (size_t)n_tot) != cudaSuccess ||
-        (nnz_tot > 0 && (cudaMalloc(&b->colidx, sizeof(int32_t) * (size_t)nnz_tot) != cudaSuccess ||
-                         cudaMalloc(&b->val, sizeof(float) * (size_t)nnz_tot) != cudaSuccess))) {
+        cudaMalloc(&b->colidx, sizeof(int32_t) * (size_t)(nnz_tot + kCsrPad)) != cudaSuccess ||
+        cudaMalloc(&b->val, sizeof(float) * (size_t)(nnz_tot + kCsrPad)) != cudaSuccess) {
         cudaGetLastError();
         batch_release(b);
         set_error("device allocation failed for a batch of %lld rows", (long long)n_tot);
@@ -443,8 +460,13 @@ SF_API sf_status sf_batch_build(const sf_graph *const *graphs, int32_t n_graphs,
             }
         }
     }
-    int32_t last = (int32_t)nnz_tot;
-    if (cudaMemcpyAsync(b->rowptr + n_tot, &last, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    fill_i32_kernel<<<1, 32, 0, s>>>(b->rowptr + n_tot, kCsrPad + 1, (int32_t)nnz_tot);
+    if ((st = check_launch("fill_i32_kernel"))) {
+        batch_release(b);
+        return st;
+    }
+    if (cudaMemsetAsync(b->colidx + nnz_tot, 0, sizeof(int32_t) * kCsrPad, s) != cudaSuccess ||
+        cudaMemsetAsync(b->val + nnz_tot, 0, sizeof(float) * kCsrPad, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         st = cuda_fail(cudaGetLastError(), "finishing batch");
         batch_release(b);

@@ -84,6 +84,11 @@ double tridiag_max_eig_host(int k, const double *a, const double *b);
 
 }  // namespace sf
 
+// Extra entries after rowptr[n] (holding nnz) and after colidx/val (zeros),
+// so that 16-byte aligned bulk copies of any row or entry range stay inside
+// the allocations.
+constexpr int kCsrPad = 4;
+
 // ---------------------------------------------------------------- objects
 struct sf_graph {
     int32_t n = 0;

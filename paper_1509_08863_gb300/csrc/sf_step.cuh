@@ -4,11 +4,8 @@
 //
 // Layout: the signal block is processed in column slabs. A slab buffer is
 // row-major [N][ld] with ld = LPR * VEC elements, so one row of the slab is
-// LPR lanes x 16 bytes. One warp owns one row at a time; its 32 lanes form
-// NG = 32 / LPR groups, each group reading a different neighbour's 16-byte
-// chunks, so a warp keeps U * NG neighbour rows in flight. The groups' partial
-// sums are combined with a butterfly of shuffles and group 0 runs the
-// epilogue for the row.
+// LPR lanes x 16 bytes; a group of LPR lanes owns a row. The CSR of each tile
+// of rows is staged in shared memory by the TMA bulk-copy engine.
 #pragma once
 
 #include "sf_internal.cuh"
@@ -94,81 +91,182 @@ struct StepParams {
     int32_t j;              // coefficient index used by this order
     // moments
     double *part;           // [gridDim.x][2]: sum t.t, sum t.x
+    int32_t *status;        // device error word (bit 0: a bounded wait gave up)
 };
 
+// ------------------------------------------------------------ async copies
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Polls are bounded: a copy that never lands makes the kernel record an
+// error in *status and return instead of waiting forever.
+constexpr uint32_t kWaitPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitPolls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // ------------------------------------------------------------ the sweep
+// A CTA walks tiles of kTileRows consecutive rows. For each tile one thread
+// issues bulk copies of the tile's rowptr slice and of its colidx (and val)
+// range into shared memory; the range is widened to 16-byte boundaries and
+// the CSR arrays carry padding so the widened copy stays in bounds. Tiles
+// whose entries do not fit read the CSR from global memory instead.
+// Within a tile, lane group g (LPR lanes) owns rows g, g + G, ... (G groups
+// per CTA): the group loads the row's epilogue operands first, then walks
+// the row's entries from shared memory with U gathers in flight per lane.
+constexpr int kTileRows = 128;
+constexpr int kTileEntries = 6144;
+
+__host__ __device__ constexpr int step_smem_bytes(bool weighted) {
+    return 16 /*barrier*/ + 16 /*meta*/ + (kTileRows + 8) * 4 + kTileEntries * 4 * (weighted ? 2 : 1);
+}
+
 template <typename TS, int LPR, int MODE>
 __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
     using V = VT<TS>;
     constexpr int VEC = V::V;
-    constexpr int NG = 32 / LPR;
-    constexpr int U = (NG == 1) ? 8 : 4;
-    __shared__ double red[8][2];
-    const int lane = threadIdx.x & 31;
-    const int q = lane % LPR, grp = lane / LPR;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int U = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);
+    int32_t *s_rp = reinterpret_cast<int32_t *>(smem_raw + 32);
+    int32_t *s_col = s_rp + (kTileRows + 8);
+    float *s_val = reinterpret_cast<float *>(s_col + kTileEntries);
+    __shared__ double s_red[8][2];
+
+    const int tid = threadIdx.x;
+    const int q = tid % LPR, grp = tid / LPR;
+    const int ngrp = blockDim.x / LPR;
+    const int32_t n = P.n;
+    const int n_tiles = (n + kTileRows - 1) / kTileRows;
+    const bool weighted = P.val != nullptr;
     const TS *__restrict__ X = static_cast<const TS *>(P.X);
     const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
     TS *__restrict__ out = static_cast<TS *>(P.out);
     const int32_t ld = P.ld;
+    const float m = P.m;
     double mtt = 0.0, mtx = 0.0;
 
-    for (int64_t i = warp0; i < P.n; i += nwarps) {
-        const int32_t beg = __ldg(P.rowptr + i), end = __ldg(P.rowptr + i + 1);
-        float acc[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-        for (int32_t base = beg; base < end; base += U * NG) {
-            int32_t k[U];
-            float wv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int32_t e = base + u * NG + grp;
-                const bool ok = e < end;
-                k[u] = ok ? __ldcs(P.colidx + e) : -1;
-                wv[u] = ok ? (P.val ? __ldcs(P.val + e) : 1.0f) : 0.0f;
+    if (tid == 0) {
+        mbar_init(s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int32_t r0 = tile * kTileRows;
+        const int32_t nr = min(kTileRows, n - r0);
+        if (tid == 0) {
+            const int32_t e0 = P.rowptr[r0], e1 = P.rowptr[r0 + nr];
+            const int32_t a0 = e0 & ~3;
+            const int64_t a1 = ((int64_t)e1 + 3) & ~(int64_t)3;
+            const int32_t cnt = (int32_t)(a1 - a0);
+            const int32_t rp_cnt = (nr + 1 + 3) & ~3;
+            const bool fits = cnt <= kTileEntries;
+            const uint32_t bytes = rp_cnt * 4 + (fits ? (uint32_t)cnt * 4u * (weighted ? 2u : 1u) : 0u);
+            s_meta[0] = a0;
+            s_meta[1] = fits ? 1 : 0;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(s_bar, bytes);
+            bulk_g2s(s_rp, P.rowptr + r0, rp_cnt * 4, s_bar);
+            if (fits && cnt > 0) {
+                bulk_g2s(s_col, P.colidx + a0, cnt * 4, s_bar);
+                if (weighted) bulk_g2s(s_val, P.val + a0, cnt * 4, s_bar);
             }
-            float xv[U][VEC];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (k[u] >= 0) {
-                    V::ld_gather(X + (int64_t)k[u] * ld + q * VEC, xv[u]);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) xv[u][v] = 0.f;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[u][v], acc[v]);
         }
-#pragma unroll
-        for (int off = LPR; off < 32; off <<= 1)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+        __syncthreads();
+        const bool landed = mbar_wait_bounded(s_bar, phase);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicOr(P.status, 1);
+            mbar_wait_bounded(s_bar, phase);  // give a late copy one more bounded chance to land
+            return;
+        }
+        phase ^= 1u;
+        const int32_t a0 = s_meta[0];
+        const bool fits = s_meta[1] != 0;
+        const int32_t *colp = fits ? s_col : P.colidx + a0;
+        const float *valp = fits ? s_val : (weighted ? P.val + a0 : nullptr);
 
-        if (grp == 0) {
+        for (int rr = grp; rr < nr; rr += ngrp) {
+            const int64_t i = (int64_t)r0 + rr;
+            const int32_t beg = s_rp[rr] - a0, end = s_rp[rr + 1] - a0;
             const int64_t ro = i * ld + q * VEC;
-            float xi[VEC], t[VEC];
+            // epilogue operands first: their latency overlaps the gathers
+            float xi[VEC], z[VEC], qv[VEC];
             V::ld_gather(X + ro, xi);
+            if (Z) {
+                V::ld_stream(Z + ro, z);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) z[v] = 0.f;
+            }
+            if (MODE == MODE_CLEN) V::ld_stream(Qb + ro, qv);
             const float d = __ldcs(P.dtil + i);
             const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
             const int g = P.gid ? __ldcs(P.gid + i) : 0;
+
+            float acc[VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) t[v] = P.m * fmaf(d, xi[v], -sc * acc[v]);
-            if (Z) {
-                float z[VEC];
-                V::ld_stream(Z + ro, z);
+            for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+            for (int32_t e = beg; e < end; e += U) {
+                int32_t k[U];
+                float wv[U];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) t[v] -= z[v];
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = e + u < end;
+                    k[u] = ok ? colp[e + u] : 0;
+                    wv[u] = ok ? (weighted ? valp[e + u] : 1.0f) : 0.0f;
+                }
+                float xv[U][VEC];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (e + u < end) {
+                        V::ld_gather(X + (int64_t)k[u] * ld + q * VEC, xv[u]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) xv[u][v] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[u][v], acc[v]);
             }
+
+            float t[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) t[v] = m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
             if (MODE == MODE_CLEN) {
                 const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
-                float qv[VEC];
-                V::ld_stream(Qb + ro, qv);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
             }
@@ -203,30 +301,30 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
                     tt = fmaf(ts, ts, tt);
                     tx = fmaf(ts, xi[v], tx);
                 }
-#pragma unroll
-                for (int off = 1; off < LPR; off <<= 1) {
-                    tt += __shfl_xor_sync((LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u), tt, off);
-                    tx += __shfl_xor_sync((LPR == 32) ? 0xffffffffu : ((1u << LPR) - 1u), tx, off);
-                }
-                if (q == 0) {
-                    mtt += (double)tt;
-                    mtx += (double)tx;
-                }
+                mtt += (double)tt;
+                mtx += (double)tx;
             }
         }
+        __syncthreads();  // shared tile fully consumed before the next copy
     }
     if (MODE == MODE_MOM) {
-        const int w = threadIdx.x >> 5;
-        if (lane == 0) {
-            red[w][0] = mtt;
-            red[w][1] = mtx;
+        // fixed-order reduction: lanes of a warp, then warps of the block
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mtt += __shfl_xor_sync(0xffffffffu, mtt, off);
+            mtx += __shfl_xor_sync(0xffffffffu, mtx, off);
+        }
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            s_red[w][0] = mtt;
+            s_red[w][1] = mtx;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             double a = 0.0, b = 0.0;
             for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                a += red[k][0];
-                b += red[k][1];
+                a += s_red[k][0];
+                b += s_red[k][1];
             }
             P.part[2 * blockIdx.x] = a;
             P.part[2 * blockIdx.x + 1] = b;
@@ -341,11 +439,15 @@ struct SweepShape {
     int ld;           // slab columns (= lpr * vec)
     int block;        // threads per block
     int grid;         // blocks
+    int smem;         // dynamic shared memory per block
 };
 
 // Picks the slab width (columns) for n rows and n_sig signals.
 int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t l2_budget_bytes);
-sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, SweepShape *sh);
+sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
+                     SweepShape *sh);
+// Device error word written by the sweep kernels (bounded waits).
+int32_t *device_status();
 sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes);
 
 }  // namespace sf

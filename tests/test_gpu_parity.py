@@ -255,9 +255,10 @@ def test_moments_and_counts_match_oracle(sf, oracle_mod):
     co = oracle_mod.eigencount(go, lh, a, R)
     bound = 2e-6 * (2 * p + 1) * muo[0] * np.sum(np.abs(a), axis=1) ** 2
     assert np.all(np.abs(counts - co) <= bound), (counts, co)
-    # slabs and blocks per SM do not change the moments beyond rounding
+    # other slab widths regroup the FP32 row partials: same bound
     mu2 = sf.cheb_moments(g, lh, Rt, p, sf.Opts(slab_cols=8))
-    np.testing.assert_allclose(mu2, mu, rtol=0, atol=1e-9 * muo[0])
+    for m in range(2 * p + 1):
+        assert abs(mu2[m] - muo[m]) <= 2e-6 * (m + 1) * muo[0]
 
 
 def test_moments_deterministic(sf, oracle_mod):
