@@ -32,7 +32,22 @@ struct VT<float> {
     }
     // value as it is stored (identity for fp32)
     __device__ __forceinline__ static float rt(float x) { return x; }
-    __device__ __forceinline__ static float from(float x) { return x; }
+    using raw_t = float4;
+    __device__ __forceinline__ static raw_t ld_raw(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    __device__ __forceinline__ static raw_t zero_raw() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ static raw_t ld_raw_stream(const float *p) {
+        return __ldcs(reinterpret_cast<const float4 *>(p));
+    }
+    __device__ __forceinline__ static void to_float(raw_t x, float (&f)[4]) {
+        f[0] = x.x; f[1] = x.y; f[2] = x.z; f[3] = x.w;
+    }
+    // acc += w * x for the 4 values held in a raw register quad
+    __device__ __forceinline__ static void fma_raw(float (&acc)[4], float w, raw_t x) {
+        acc[0] = fmaf(w, x.x, acc[0]);
+        acc[1] = fmaf(w, x.y, acc[1]);
+        acc[2] = fmaf(w, x.z, acc[2]);
+        acc[3] = fmaf(w, x.w, acc[3]);
+    }
 };
 
 template <>
@@ -61,6 +76,33 @@ struct VT<__nv_bfloat16> {
         *reinterpret_cast<uint4 *>(p) = v;
     }
     __device__ __forceinline__ static float rt(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+    using raw_t = uint4;
+    __device__ __forceinline__ static raw_t ld_raw(const __nv_bfloat16 *p) {
+        return __ldg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static raw_t zero_raw() { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ static raw_t ld_raw_stream(const __nv_bfloat16 *p) {
+        return __ldcs(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static void to_float(raw_t x, float (&f)[8]) {
+        const uint32_t h[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            f[2 * k] = __uint_as_float(h[k] << 16);
+            f[2 * k + 1] = __uint_as_float(h[k] & 0xffff0000u);
+        }
+    }
+    // a bf16 is the high half of an fp32: widening is a shift or a mask
+    __device__ __forceinline__ static void fma_pair(float &a0, float &a1, float w, uint32_t h) {
+        a0 = fmaf(w, __uint_as_float(h << 16), a0);
+        a1 = fmaf(w, __uint_as_float(h & 0xffff0000u), a1);
+    }
+    __device__ __forceinline__ static void fma_raw(float (&acc)[8], float w, raw_t x) {
+        fma_pair(acc[0], acc[1], w, x.x);
+        fma_pair(acc[2], acc[3], w, x.y);
+        fma_pair(acc[4], acc[5], w, x.z);
+        fma_pair(acc[6], acc[7], w, x.w);
+    }
 };
 
 // ------------------------------------------------------------ parameters
@@ -220,16 +262,11 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
             const int64_t i = (int64_t)r0 + rr;
             const int32_t beg = s_rp[rr] - a0, end = s_rp[rr + 1] - a0;
             const int64_t ro = i * ld + q * VEC;
-            // epilogue operands first: their latency overlaps the gathers
-            float xi[VEC], z[VEC], qv[VEC];
-            V::ld_gather(X + ro, xi);
-            if (Z) {
-                V::ld_stream(Z + ro, z);
-            } else {
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) z[v] = 0.f;
-            }
-            if (MODE == MODE_CLEN) V::ld_stream(Qb + ro, qv);
+            // epilogue operands first (kept packed): their latency overlaps the gathers
+            const typename V::raw_t xi_r = V::ld_raw(X + ro);
+            const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
+            typename V::raw_t q_r = V::zero_raw();
+            if (MODE == MODE_CLEN) q_r = V::ld_raw_stream(Qb + ro);
             const float d = __ldcs(P.dtil + i);
             const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
             const int g = P.gid ? __ldcs(P.gid + i) : 0;
@@ -246,27 +283,26 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
                     k[u] = ok ? colp[e + u] : 0;
                     wv[u] = ok ? (weighted ? valp[e + u] : 1.0f) : 0.0f;
                 }
-                float xv[U][VEC];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (e + u < end) {
-                        V::ld_gather(X + (int64_t)k[u] * ld + q * VEC, xv[u]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) xv[u][v] = 0.f;
-                    }
-                }
+                typename V::raw_t xr[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
+                    xr[u] = (e + u < end) ? V::ld_raw(X + (int64_t)k[u] * ld + q * VEC) : V::zero_raw();
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[u][v], acc[v]);
+                for (int u = 0; u < U; ++u) V::fma_raw(acc, wv[u], xr[u]);
             }
 
-            float t[VEC];
+            float t[VEC], xi[VEC];
+            {
+                float z[VEC];
+                V::to_float(xi_r, xi);
+                V::to_float(z_r, z);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) t[v] = m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
+                for (int v = 0; v < VEC; ++v) t[v] = m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
+            }
             if (MODE == MODE_CLEN) {
                 const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
+                float qv[VEC];
+                V::to_float(q_r, qv);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
             }
