@@ -54,6 +54,16 @@ static const void *kernel_for(int storage, int lpr, int mode) {
 
 __device__ int32_t g_sweep_status;
 
+static int step_smem(int lpr, bool weighted) {
+    switch (lpr) {
+        case 2: return TileCfg<2>::smem_bytes(weighted);
+        case 4: return TileCfg<4>::smem_bytes(weighted);
+        case 8: return TileCfg<8>::smem_bytes(weighted);
+        case 16: return TileCfg<16>::smem_bytes(weighted);
+        default: return TileCfg<32>::smem_bytes(weighted);
+    }
+}
+
 int32_t *device_status() {
     static int32_t *cache[64] = {nullptr};
     const int d = current_device();
@@ -80,8 +90,8 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
     const void *fn = kernel_for(storage, lpr, mode);
     SF_ARG(fn, "no kernel for this shape");
-    const int smem = step_smem_bytes(weighted);
-    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_bytes(true)));
+    const int smem = step_smem(lpr, weighted);
+    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem(lpr, true)));
     int occ = 0;
     SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, smem));
     if (occ < 1) occ = 1;

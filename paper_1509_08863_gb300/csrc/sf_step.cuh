@@ -176,40 +176,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // ------------------------------------------------------------ the sweep
-// A CTA walks tiles of kTileRows consecutive rows. For each tile one thread
-// issues bulk copies of the tile's rowptr slice and of its colidx (and val)
-// range into shared memory; the range is widened to 16-byte boundaries and
-// the CSR arrays carry padding so the widened copy stays in bounds. Tiles
-// whose entries do not fit read the CSR from global memory instead.
-// Within a tile, lane group g (LPR lanes) owns rows g, g + G, ... (G groups
-// per CTA): the group loads the row's epilogue operands first, then walks
-// the row's entries from shared memory with U gathers in flight per lane.
-constexpr int kTileRows = 128;
-constexpr int kTileEntries = 6144;
-
-__host__ __device__ constexpr int step_smem_bytes(bool weighted) {
-    return 16 /*barrier*/ + 16 /*meta*/ + (kTileRows + 8) * 4 + kTileEntries * 4 * (weighted ? 2 : 1);
-}
+// A CTA walks tiles of consecutive rows (tile k of the CTA is
+// blockIdx.x + k * gridDim.x). The CSR slice of each tile -- its rowptr
+// entries and its colidx (and val) range, widened to 16-byte boundaries; the
+// CSR arrays carry padding so the widened copy stays in bounds -- is staged
+// in shared memory by TMA bulk copies into one of two buffers: the copy for
+// tile k + 1 is issued before tile k is processed, so its latency overlaps
+// the compute. Tiles whose entries do not fit read the CSR from global
+// memory instead. Within a tile, lane group g (LPR lanes) owns rows g, g + G,
+// ... (G groups per CTA): the group loads the row's epilogue operands first,
+// then walks the row's entries from shared memory with U gathers in flight
+// per lane.
+template <int LPR>
+struct TileCfg {
+    static constexpr int rows = (LPR == 2) ? 128 : 64;
+    static constexpr int entries = rows * 48;
+    static constexpr int rp_ints = rows + 8;
+    // per buffer: rowptr slice, colidx, val (weighted graphs only)
+    __host__ __device__ static constexpr int buf_bytes(bool weighted) {
+        return rp_ints * 4 + entries * 4 * (weighted ? 2 : 1);
+    }
+    __host__ __device__ static constexpr int smem_bytes(bool weighted) { return 64 + 2 * buf_bytes(weighted); }
+};
 
 template <typename TS, int LPR, int MODE>
-__global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
+__global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
     using V = VT<TS>;
+    using C = TileCfg<LPR>;
     constexpr int VEC = V::V;
     constexpr int U = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);
-    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);
-    int32_t *s_rp = reinterpret_cast<int32_t *>(smem_raw + 32);
-    int32_t *s_col = s_rp + (kTileRows + 8);
-    float *s_val = reinterpret_cast<float *>(s_col + kTileEntries);
+    const bool weighted = P.val != nullptr;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: a0, fits
+    unsigned char *s_buf0 = smem_raw + 64;
+    const int buf_bytes = C::buf_bytes(weighted);
     __shared__ double s_red[8][2];
 
     const int tid = threadIdx.x;
     const int q = tid % LPR, grp = tid / LPR;
     const int ngrp = blockDim.x / LPR;
     const int32_t n = P.n;
-    const int n_tiles = (n + kTileRows - 1) / kTileRows;
-    const bool weighted = P.val != nullptr;
+    const int n_tiles = (n + C::rows - 1) / C::rows;
     const TS *__restrict__ X = static_cast<const TS *>(P.X);
     const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
@@ -218,43 +226,60 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
     const float m = P.m;
     double mtt = 0.0, mtx = 0.0;
 
+    // thread 0: stage tile `tile` into buffer `b`
+    auto issue = [&](int tile, int b) {
+        unsigned char *base = s_buf0 + b * buf_bytes;
+        int32_t *rp = reinterpret_cast<int32_t *>(base);
+        int32_t *col = rp + C::rp_ints;
+        float *val = reinterpret_cast<float *>(col + C::entries);
+        const int32_t r0 = tile * C::rows;
+        const int32_t nr = min(C::rows, n - r0);
+        const int32_t e0 = P.rowptr[r0], e1 = P.rowptr[r0 + nr];
+        const int32_t a0 = e0 & ~3;
+        const int64_t a1 = ((int64_t)e1 + 3) & ~(int64_t)3;
+        const int32_t cnt = (int32_t)(a1 - a0);
+        const int32_t rp_cnt = (nr + 1 + 3) & ~3;
+        const bool fits = cnt <= C::entries;
+        const uint32_t bytes = rp_cnt * 4 + (fits ? (uint32_t)cnt * 4u * (weighted ? 2u : 1u) : 0u);
+        s_meta[2 * b] = a0;
+        s_meta[2 * b + 1] = fits ? 1 : 0;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&s_bar[b], bytes);
+        bulk_g2s(rp, P.rowptr + r0, rp_cnt * 4, &s_bar[b]);
+        if (fits && cnt > 0) {
+            bulk_g2s(col, P.colidx + a0, cnt * 4, &s_bar[b]);
+            if (weighted) bulk_g2s(val, P.val + a0, cnt * 4, &s_bar[b]);
+        }
+    };
+
     if (tid == 0) {
-        mbar_init(s_bar, 1);
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
         fence_mbar_init();
+        if ((int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
     }
     __syncthreads();
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int32_t r0 = tile * kTileRows;
-        const int32_t nr = min(kTileRows, n - r0);
-        if (tid == 0) {
-            const int32_t e0 = P.rowptr[r0], e1 = P.rowptr[r0 + nr];
-            const int32_t a0 = e0 & ~3;
-            const int64_t a1 = ((int64_t)e1 + 3) & ~(int64_t)3;
-            const int32_t cnt = (int32_t)(a1 - a0);
-            const int32_t rp_cnt = (nr + 1 + 3) & ~3;
-            const bool fits = cnt <= kTileEntries;
-            const uint32_t bytes = rp_cnt * 4 + (fits ? (uint32_t)cnt * 4u * (weighted ? 2u : 1u) : 0u);
-            s_meta[0] = a0;
-            s_meta[1] = fits ? 1 : 0;
-            fence_proxy_async();
-            mbar_arrive_expect_tx(s_bar, bytes);
-            bulk_g2s(s_rp, P.rowptr + r0, rp_cnt * 4, s_bar);
-            if (fits && cnt > 0) {
-                bulk_g2s(s_col, P.colidx + a0, cnt * 4, s_bar);
-                if (weighted) bulk_g2s(s_val, P.val + a0, cnt * 4, s_bar);
-            }
-        }
-        __syncthreads();
-        const bool landed = mbar_wait_bounded(s_bar, phase);
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= n_tiles) break;
+        const int b = k & 1;
+        // buffer b^1 was released by the barrier that ended the previous tile
+        if (tid == 0 && tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
+        const bool landed = mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
         if (__syncthreads_or(!landed)) {
             if (tid == 0) atomicOr(P.status, 1);
-            mbar_wait_bounded(s_bar, phase);  // give a late copy one more bounded chance to land
+            // one more bounded chance for copies still in flight before leaving
+            mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
+            if (tile + (int)gridDim.x < n_tiles) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
             return;
         }
-        phase ^= 1u;
-        const int32_t a0 = s_meta[0];
-        const bool fits = s_meta[1] != 0;
+        const int32_t r0 = tile * C::rows;
+        const int32_t nr = min(C::rows, n - r0);
+        const int32_t *s_rp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
+        const int32_t *s_col = s_rp + C::rp_ints;
+        const float *s_val = reinterpret_cast<const float *>(s_col + C::entries);
+        const int32_t a0 = s_meta[2 * b];
+        const bool fits = s_meta[2 * b + 1] != 0;
         const int32_t *colp = fits ? s_col : P.colidx + a0;
         const float *valp = fits ? s_val : (weighted ? P.val + a0 : nullptr);
 
@@ -341,7 +366,7 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const StepParams P) {
                 mtx += (double)tx;
             }
         }
-        __syncthreads();  // shared tile fully consumed before the next copy
+        __syncthreads();  // buffer b fully consumed before it is refilled
     }
     if (MODE == MODE_MOM) {
         // fixed-order reduction: lanes of a warp, then warps of the block
