@@ -221,7 +221,13 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int ld = sh.ld;
-    const size_t blk = (size_t)n * ld;
+    // one block = n + 1 rows: row n stays zero (padding of the sliced-ELL layout)
+    const size_t blk = (size_t)(n + 1) * ld;
+    SF_ARG((int64_t)(n + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
+    {
+        std::lock_guard<std::mutex> lk(g->sell_mu);
+        if ((st = sell_build(&g->sell, g->n, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, s))) return st;
+    }
     const int64_t cap_mb = o.mem_cap_mb > 0 ? o.mem_cap_mb : 16384;
     int k = o.ckpt_every;
     if (k <= 0) k = ((double)(p + 1) * blk * 4 <= (double)cap_mb * (1 << 20)) ? 1 : (int)ceil(sqrt((double)p));
@@ -248,6 +254,12 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         return st;
     if (g->nnz > 0 && (st = sc.get(&moff, (size_t)g->nnz))) return st;
     if (grad_R && (st = sc.get(&gR, blk))) return st;
+    SF_CHECK_CUDA(cudaMemsetAsync(store, 0, sizeof(float) * (size_t)nslots * blk, s));
+    if (seg) SF_CHECK_CUDA(cudaMemsetAsync(seg, 0, sizeof(float) * (size_t)(k + 1) * blk, s));
+    for (int q = 0; q < 3; ++q) {
+        SF_CHECK_CUDA(cudaMemsetAsync(work[q], 0, sizeof(float) * blk, s));
+        SF_CHECK_CUDA(cudaMemsetAsync(bb[q], 0, sizeof(float) * blk, s));
+    }
     {
         std::vector<float> cf((size_t)p + 1);
         for (int j = 0; j <= p; ++j) cf[j] = (float)coeffs[j];
@@ -278,6 +290,10 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         P.rowptr = g->rowptr;
         P.colidx = g->colidx;
         P.val = val;
+        P.sell_ptr = g->sell.sptr;
+        P.sell_perm = g->sell.perm;
+        P.sell_idx = g->sell.idx;
+        P.sell_val = g->sell.val;
         P.dtil = dtil;
         P.wscale_u = (float)two_over_lam;
         P.ld = ld;

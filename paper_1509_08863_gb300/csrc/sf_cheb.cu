@@ -25,30 +25,31 @@ int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t budget) {
     return w;
 }
 
-template <typename TS, int LPR>
+template <typename TS, int LPR, bool W>
 static const void *step_fn(int mode) {
     switch (mode) {
-        case MODE_FWD: return (const void *)cheb_step_kernel<TS, LPR, MODE_FWD>;
-        case MODE_MOM: return (const void *)cheb_step_kernel<TS, LPR, MODE_MOM>;
-        default: return (const void *)cheb_step_kernel<TS, LPR, MODE_CLEN>;
+        case MODE_FWD: return (const void *)cheb_step_kernel<TS, LPR, MODE_FWD, W>;
+        case MODE_MOM: return (const void *)cheb_step_kernel<TS, LPR, MODE_MOM, W>;
+        default: return (const void *)cheb_step_kernel<TS, LPR, MODE_CLEN, W>;
     }
 }
 
-template <typename TS>
+template <typename TS, bool W>
 static const void *step_fn_lpr(int lpr, int mode) {
     switch (lpr) {
-        case 2: return step_fn<TS, 2>(mode);
-        case 4: return step_fn<TS, 4>(mode);
-        case 8: return step_fn<TS, 8>(mode);
-        case 16: return step_fn<TS, 16>(mode);
-        case 32: return step_fn<TS, 32>(mode);
+        case 2: return step_fn<TS, 2, W>(mode);
+        case 4: return step_fn<TS, 4, W>(mode);
+        case 8: return step_fn<TS, 8, W>(mode);
+        case 16: return step_fn<TS, 16, W>(mode);
+        case 32: return step_fn<TS, 32, W>(mode);
         default: return nullptr;
     }
 }
 
-static const void *kernel_for(int storage, int lpr, int mode) {
-    if (storage == SF_F32) return step_fn_lpr<float>(lpr, mode);
-    if (storage == SF_BF16) return step_fn_lpr<__nv_bfloat16>(lpr, mode);
+static const void *kernel_for(int storage, int lpr, int mode, bool weighted) {
+    if (storage == SF_F32) return weighted ? step_fn_lpr<float, true>(lpr, mode) : step_fn_lpr<float, false>(lpr, mode);
+    if (storage == SF_BF16)
+        return weighted ? step_fn_lpr<__nv_bfloat16, true>(lpr, mode) : step_fn_lpr<__nv_bfloat16, false>(lpr, mode);
     return nullptr;
 }
 
@@ -88,10 +89,10 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
            "slab_cols %d gives %d lanes per row (need 2..32, power of two)", slab_cols, lpr);
     if (block_warps <= 0) block_warps = 8;
     SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
-    const void *fn = kernel_for(storage, lpr, mode);
+    const void *fn = kernel_for(storage, lpr, mode, weighted);
     SF_ARG(fn, "no kernel for this shape");
     const int smem = step_smem(lpr, weighted);
-    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem(lpr, true)));
+    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
     SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, smem));
     if (occ < 1) occ = 1;
@@ -102,26 +103,27 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     sh->block = block_warps * 32;
     sh->grid = occ * sm_count();
     sh->smem = smem;
+    sh->weighted = weighted;
     return SF_OK;
 }
 
-template <typename TS, int LPR>
+template <typename TS, int LPR, bool W>
 static void launch_mode(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
     switch (mode) {
-        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
-        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
-        default: cheb_step_kernel<TS, LPR, MODE_CLEN><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        default: cheb_step_kernel<TS, LPR, MODE_CLEN, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
     }
 }
 
-template <typename TS>
+template <typename TS, bool W>
 static void launch_lpr(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
     switch (sh.lpr) {
-        case 2: launch_mode<TS, 2>(mode, sh, P, s); break;
-        case 4: launch_mode<TS, 4>(mode, sh, P, s); break;
-        case 8: launch_mode<TS, 8>(mode, sh, P, s); break;
-        case 16: launch_mode<TS, 16>(mode, sh, P, s); break;
-        default: launch_mode<TS, 32>(mode, sh, P, s); break;
+        case 2: launch_mode<TS, 2, W>(mode, sh, P, s); break;
+        case 4: launch_mode<TS, 4, W>(mode, sh, P, s); break;
+        case 8: launch_mode<TS, 8, W>(mode, sh, P, s); break;
+        case 16: launch_mode<TS, 16, W>(mode, sh, P, s); break;
+        default: launch_mode<TS, 32, W>(mode, sh, P, s); break;
     }
 }
 
@@ -129,8 +131,13 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     cudaEvent_t ea = nullptr, eb = nullptr;
     const bool prof = profiling_on() && profile_events(&ea, &eb);
     if (prof) cudaEventRecord(ea, s);
-    if (sh.storage == SF_F32) launch_lpr<float>(mode, sh, P, s);
-    else launch_lpr<__nv_bfloat16>(mode, sh, P, s);
+    if (sh.storage == SF_F32) {
+        if (sh.weighted) launch_lpr<float, true>(mode, sh, P, s);
+        else launch_lpr<float, false>(mode, sh, P, s);
+    } else {
+        if (sh.weighted) launch_lpr<__nv_bfloat16, true>(mode, sh, P, s);
+        else launch_lpr<__nv_bfloat16, false>(mode, sh, P, s);
+    }
     sf_status st = check_launch("cheb_step_kernel");
     if (prof) {
         cudaEventRecord(eb, s);
@@ -165,10 +172,19 @@ struct GraphView {
     const double *strength;
     const int32_t *gid;  // batches
     int32_t n_graphs;
+    const SellMatrix *sell;
 };
 
-static GraphView view_of(const sf_graph *g) {
-    return GraphView{g->n, g->nnz, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, g->strength, nullptr, 1};
+// The graph's sliced-ELL copy, built on first use (synchronises the stream).
+static sf_status view_of(const sf_graph *g, cudaStream_t s, GraphView *v) {
+    {
+        std::lock_guard<std::mutex> lk(g->sell_mu);
+        sf_status st = sell_build(&g->sell, g->n, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, s);
+        if (st) return st;
+    }
+    *v = GraphView{g->n, g->nnz, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, g->strength, nullptr, 1,
+                   &g->sell};
+    return SF_OK;
 }
 
 static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r) {
@@ -216,8 +232,12 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     float *yacc = nullptr, *coef = nullptr, *dtil = nullptr, *wscale = nullptr;
     double *part = nullptr, *tol = nullptr;
     const int nbuf = 3;
-    for (int k = 0; k < nbuf; ++k)
-        if ((st = sc.get((char **)&buf[k], (size_t)n * ld * eb))) return st;
+    SF_ARG((int64_t)(n + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
+    for (int k = 0; k < nbuf; ++k) {
+        // row n stays zero: padding entries of the sliced-ELL layout gather it
+        if ((st = sc.get((char **)&buf[k], (size_t)(n + 1) * ld * eb))) return st;
+        SF_CHECK_CUDA(cudaMemsetAsync((char *)buf[k] + (size_t)n * ld * eb, 0, (size_t)ld * eb, s));
+    }
     if (mode == MODE_CLEN && (st = sc.get((char **)&qbuf, (size_t)n * ld * eb))) return st;
     const int ncy = (mode == MODE_FWD) ? n_cut : (mode == MODE_CLEN ? 1 : 0);
     if (ncy && (st = sc.get(&yacc, (size_t)ncy * n * ld))) return st;
@@ -252,6 +272,10 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         P.rowptr = G.rowptr;
         P.colidx = G.colidx;
         P.val = G.val;
+        P.sell_ptr = G.sell->sptr;
+        P.sell_perm = G.sell->perm;
+        P.sell_idx = G.sell->idx;
+        P.sell_val = G.sell->val;
         P.dtil = dtil;
         P.wscale = wscale;
         P.wscale_u = (float)two_over_lam;
@@ -386,7 +410,8 @@ SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double 
     int algo = o.algo;
     if (algo == SF_ALGO_AUTO) algo = (n_cut == 1) ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
     SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
-    GraphView G = view_of(g);
+    GraphView G;
+    if ((st = view_of(g, s, &G))) return st;
     if (algo == SF_ALGO_FORWARD)
         return run_sweeps(G, nullptr, 2.0 / lam_max, MODE_FWD, coeffs, n_cut, p, R, r_dtype, n_sig, Y, nullptr, o, s);
     for (int c = 0; c < n_cut; ++c) {
@@ -410,7 +435,8 @@ SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *
     double *dots = nullptr;
     if ((st = sc.get(&dots, (size_t)2 * (p + 1)))) return st;
     SF_CHECK_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * 2 * (p + 1), s));
-    GraphView G = view_of(g);
+    GraphView G;
+    if ((st = view_of(g, s, &G))) return st;
     if ((st = run_sweeps(G, nullptr, 2.0 / lam_max, MODE_MOM, nullptr, 0, p, R, r_dtype, n_sig, nullptr, dots, o,
                          s)))
         return st;
@@ -461,8 +487,14 @@ SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max
     if (st) return st;
     int algo = o.algo == SF_ALGO_AUTO ? SF_ALGO_CLENSHAW : o.algo;
     SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
-    GraphView G{b->n, b->nnz, b->rowptr, b->colidx, b->unit_weights ? nullptr : b->val, b->strength, b->row_graph,
-                b->n_graphs};
+    {
+        std::lock_guard<std::mutex> lk(b->sell_mu);
+        if ((st = sell_build(&b->sell, b->n, b->rowptr, b->colidx, b->unit_weights ? nullptr : b->val,
+                             (cudaStream_t)stream)))
+            return st;
+    }
+    GraphView G{b->n,          b->nnz,         b->rowptr,   b->colidx, b->unit_weights ? nullptr : b->val,
+                b->strength,   b->row_graph,   b->n_graphs, &b->sell};
     return run_sweeps(G, tol.data(), 0.0, algo == SF_ALGO_FORWARD ? MODE_FWD : MODE_CLEN, coeffs, 1, p, R, r_dtype,
                       n_sig, Y, nullptr, o, (cudaStream_t)stream);
 }

@@ -207,6 +207,7 @@ static sf_status radix_sort(uint64_t *&keys, float *&vals, uint64_t *&keys_alt, 
 
 static void graph_release(sf_graph *g) {
     if (!g) return;
+    sell_release(&g->sell);
     cudaFree(g->rowptr);
     cudaFree(g->colidx);
     cudaFree(g->val);
@@ -354,6 +355,12 @@ SF_API sf_status sf_graph_set_values(sf_graph *g, const float *val, void *stream
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nnz > 0)
         SF_CHECK_CUDA(cudaMemcpyAsync(g->val, val, sizeof(float) * (size_t)g->nnz, cudaMemcpyDeviceToDevice, s));
+    {
+        // the sliced-ELL copy holds the old weights: rebuild it on next use
+        std::lock_guard<std::mutex> lk(g->sell_mu);
+        SF_CHECK_CUDA(cudaStreamSynchronize(s));
+        sell_release(&g->sell);
+    }
     return compute_strength(g, s);
 }
 
@@ -387,6 +394,7 @@ __global__ void batch_copy_entries_kernel(const int32_t *colidx, const float *va
 
 static void batch_release(sf_batch *b) {
     if (!b) return;
+    sell_release(&b->sell);
     cudaFree(b->rowptr);
     cudaFree(b->colidx);
     cudaFree(b->val);

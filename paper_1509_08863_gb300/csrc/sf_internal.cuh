@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,24 @@ double tridiag_max_eig_host(int k, const double *a, const double *b);
 constexpr int kCsrPad = 4;
 
 // ---------------------------------------------------------------- objects
+// Sliced-ELL copy of a CSR used by the sweep kernels (see sf_sell.cu).
+struct SellMatrix {
+    int32_t n = 0;
+    int32_t n_slices = 0;
+    int64_t entries = 0;
+    int32_t *sptr = nullptr;  // [n_slices + 1 + pad] entry offset of each slice
+    int32_t *perm = nullptr;  // [n_slices * 8] original row of each slice row, -1 for none
+    int32_t *idx = nullptr;   // [entries + pad] column index, n for padding
+    float *val = nullptr;     // [entries + pad] weight, 0 for padding; nullptr for unit weights
+    bool built = false;
+};
+
+namespace sf {
+sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                     cudaStream_t s);
+void sell_release(SellMatrix *S);
+}  // namespace sf
+
 struct sf_graph {
     int32_t n = 0;
     int64_t nnz = 0;  // stored off-diagonal entries
@@ -100,6 +119,8 @@ struct sf_graph {
     double max_strength = 0.0;
     int32_t unit_weights = 1;
     int device = 0;
+    mutable SellMatrix sell;
+    mutable std::mutex sell_mu;
 };
 
 struct sf_batch {
@@ -115,6 +136,8 @@ struct sf_batch {
     std::vector<int32_t> offsets;   // host, n_graphs + 1
     std::vector<int64_t> nnz_offsets;
     int device = 0;
+    mutable SellMatrix sell;
+    mutable std::mutex sell_mu;
 };
 
 // Strength recomputation (shared by build and set_values).

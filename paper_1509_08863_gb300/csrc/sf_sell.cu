@@ -1,0 +1,127 @@
+// Sliced-ELL copy of a CSR for the sweep kernels.
+//
+// Rows are sorted by decreasing length (ties by index) inside windows of
+// kSellWindow consecutive rows, then cut into slices of kSliceRows rows. A
+// slice is padded to the length of its longest row rounded up to a multiple
+// of 4 and stored row after row; padding entries carry index n (a zero row
+// appended to every gathered block) and weight 0. Slice offsets are
+// therefore multiples of 32 entries (128 bytes) and every row starts on a
+// 16-byte boundary. The slice count is padded to a multiple of
+// kSellSliceAlign with empty slices so that whole tiles can be bulk-copied.
+// Every step is deterministic (rank sort, max, prefix sum, copy).
+#include "sf_step.cuh"
+
+namespace sf {
+
+constexpr int kSellWindow = 256;
+constexpr int kSellSliceAlign = 16;
+
+// perm[w * 256 + rank] = row, ranking rows of window w by (length desc, index asc).
+__global__ void sell_rank_kernel(int32_t n, const int32_t *rowptr, int32_t *perm) {
+    __shared__ int32_t len[kSellWindow];
+    const int32_t base = blockIdx.x * kSellWindow;
+    const int32_t i = base + threadIdx.x;
+    len[threadIdx.x] = (i < n) ? (rowptr[i + 1] - rowptr[i]) : -1;
+    __syncthreads();
+    const int32_t li = len[threadIdx.x];
+    int32_t rank = 0;
+    for (int j = 0; j < kSellWindow; ++j) {
+        const int32_t lj = len[j];
+        rank += (lj > li) || (lj == li && j < (int)threadIdx.x);
+    }
+    perm[base + rank] = (i < n) ? i : -1;
+}
+
+// entries of slice s = 8 * (longest row length rounded up to 4)
+__global__ void sell_slice_len_kernel(int32_t n_slices, const int32_t *rowptr, const int32_t *perm,
+                                      int32_t *slen) {
+    const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slices) return;
+    int32_t mx = 0;
+    for (int k = 0; k < kSliceRows; ++k) {
+        const int32_t r = perm[(int64_t)s * kSliceRows + k];
+        if (r >= 0) mx = max(mx, rowptr[r + 1] - rowptr[r]);
+    }
+    slen[s] = kSliceRows * ((mx + 3) & ~3);
+}
+
+// One thread per slice row: copy the row's entries, pad with (n, 0).
+__global__ void sell_fill_kernel(int32_t n, int32_t n_slices, const int32_t *rowptr, const int32_t *colidx,
+                                 const float *val, const int32_t *perm, const int32_t *sptr, int32_t *idx,
+                                 float *sval) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_slices * kSliceRows) return;
+    const int32_t s = (int32_t)(t / kSliceRows), pos = (int32_t)(t % kSliceRows);
+    const int32_t so = sptr[s], ls = (sptr[s + 1] - so) / kSliceRows;
+    const int32_t r = perm[t];
+    const int32_t beg = r >= 0 ? rowptr[r] : 0, len = r >= 0 ? rowptr[r + 1] - beg : 0;
+    int32_t *ip = idx + so + (int64_t)pos * ls;
+    float *wp = sval ? sval + so + (int64_t)pos * ls : nullptr;
+    for (int32_t j = 0; j < ls; ++j) {
+        const bool real = j < len;
+        ip[j] = real ? colidx[beg + j] : n;
+        if (wp) wp[j] = real ? val[beg + j] : 0.0f;
+    }
+}
+
+__global__ void sell_fill_pad_kernel(int32_t *p, int count, int32_t v) {
+    if ((int)threadIdx.x < count) p[threadIdx.x] = v;
+}
+
+void sell_release(SellMatrix *S) {
+    cudaFree(S->sptr);
+    cudaFree(S->perm);
+    cudaFree(S->idx);
+    cudaFree(S->val);
+    *S = SellMatrix();
+}
+
+sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                     cudaStream_t s) {
+    if (S->built) return SF_OK;
+    sell_release(S);
+    const int32_t n_windows = (n + kSellWindow - 1) / kSellWindow;
+    int32_t n_slices = (n + kSliceRows - 1) / kSliceRows;
+    n_slices = (n_slices + kSellSliceAlign - 1) / kSellSliceAlign * kSellSliceAlign;
+    const int64_t perm_len = std::max<int64_t>((int64_t)n_slices * kSliceRows, (int64_t)n_windows * kSellWindow);
+    sf_status st;
+    auto oom = [&]() {
+        cudaGetLastError();
+        sell_release(S);
+        set_error("device allocation failed for the sliced-ELL copy");
+        return SF_ERR_OOM;
+    };
+    if (cudaMalloc(&S->perm, sizeof(int32_t) * (size_t)perm_len) != cudaSuccess ||
+        cudaMalloc(&S->sptr, sizeof(int32_t) * (size_t)(n_slices + 1 + kCsrPad)) != cudaSuccess)
+        return oom();
+    SF_CHECK_CUDA(cudaMemsetAsync(S->perm, 0xff, sizeof(int32_t) * (size_t)perm_len, s));  // -1
+    sell_rank_kernel<<<n_windows, kSellWindow, 0, s>>>(n, rowptr, S->perm);
+    if ((st = check_launch("sell_rank_kernel"))) return st;
+    {
+        Scratch sc(s);
+        int32_t *slen = nullptr;
+        if ((st = sc.get(&slen, (size_t)n_slices + 1))) return st;
+        sell_slice_len_kernel<<<(n_slices + 255) / 256, 256, 0, s>>>(n_slices, rowptr, S->perm, slen);
+        if ((st = check_launch("sell_slice_len_kernel"))) return st;
+        SF_CHECK_CUDA(cudaMemsetAsync(slen + n_slices, 0, sizeof(int32_t), s));
+        if ((st = exclusive_scan_i32(slen, S->sptr, (int64_t)n_slices + 1, s))) return st;
+    }
+    int32_t total = 0;
+    SF_CHECK_CUDA(cudaMemcpyAsync(&total, S->sptr + n_slices, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    sell_fill_pad_kernel<<<1, 32, 0, s>>>(S->sptr + n_slices + 1, kCsrPad, total);
+    if ((st = check_launch("sell_fill_pad_kernel"))) return st;
+    if (cudaMalloc(&S->idx, sizeof(int32_t) * (size_t)(total + kCsrPad)) != cudaSuccess) return oom();
+    if (val && cudaMalloc(&S->val, sizeof(float) * (size_t)(total + kCsrPad)) != cudaSuccess) return oom();
+    const int64_t threads = (int64_t)n_slices * kSliceRows;
+    sell_fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, n_slices, rowptr, colidx, val, S->perm,
+                                                                       S->sptr, S->idx, S->val);
+    if ((st = check_launch("sell_fill_kernel"))) return st;
+    S->n = n;
+    S->n_slices = n_slices;
+    S->entries = total;
+    S->built = true;
+    return SF_OK;
+}
+
+}  // namespace sf

@@ -41,6 +41,12 @@ struct VT<float> {
     __device__ __forceinline__ static void to_float(raw_t x, float (&f)[4]) {
         f[0] = x.x; f[1] = x.y; f[2] = x.z; f[3] = x.w;
     }
+    __device__ __forceinline__ static void add_raw(float (&acc)[4], raw_t x) {
+        acc[0] += x.x;
+        acc[1] += x.y;
+        acc[2] += x.z;
+        acc[3] += x.w;
+    }
     // acc += w * x for the 4 values held in a raw register quad
     __device__ __forceinline__ static void fma_raw(float (&acc)[4], float w, raw_t x) {
         acc[0] = fmaf(w, x.x, acc[0]);
@@ -97,6 +103,14 @@ struct VT<__nv_bfloat16> {
         a0 = fmaf(w, __uint_as_float(h << 16), a0);
         a1 = fmaf(w, __uint_as_float(h & 0xffff0000u), a1);
     }
+    __device__ __forceinline__ static void add_raw(float (&acc)[8], raw_t x) {
+        const uint32_t h[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k] += __uint_as_float(h[k] << 16);
+            acc[2 * k + 1] += __uint_as_float(h[k] & 0xffff0000u);
+        }
+    }
     __device__ __forceinline__ static void fma_raw(float (&acc)[8], float w, raw_t x) {
         fma_pair(acc[0], acc[1], w, x.x);
         fma_pair(acc[2], acc[3], w, x.y);
@@ -113,6 +127,10 @@ struct StepParams {
     const int32_t *rowptr;
     const int32_t *colidx;
     const float *val;       // nullptr: all weights 1
+    const int32_t *sell_ptr;   // sliced-ELL: entry offset of each slice
+    const int32_t *sell_perm;  // original row of each slice row (-1: none)
+    const int32_t *sell_idx;   // column indices (n for padding)
+    const float *sell_val;     // weights (0 for padding), nullptr for unit weights
     const float *dtil;      // per row: 2 s_i / lam - 1
     const float *wscale;    // per row 2 / lam (batches) or nullptr
     float wscale_u;         // uniform 2 / lam
@@ -176,79 +194,147 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // ------------------------------------------------------------ the sweep
-// A CTA walks tiles of consecutive rows (tile k of the CTA is
-// blockIdx.x + k * gridDim.x). The CSR slice of each tile -- its rowptr
-// entries and its colidx (and val) range, widened to 16-byte boundaries; the
-// CSR arrays carry padding so the widened copy stays in bounds -- is staged
-// in shared memory by TMA bulk copies into one of two buffers: the copy for
-// tile k + 1 is issued before tile k is processed, so its latency overlaps
-// the compute. Tiles whose entries do not fit read the CSR from global
-// memory instead. Within a tile, lane group g (LPR lanes) owns rows g, g + G,
-// ... (G groups per CTA): the group loads the row's epilogue operands first,
-// then walks the row's entries from shared memory with U gathers in flight
-// per lane.
+// The sweep reads the graph in a sliced-ELL layout (built from the CSR by
+// the library, see sell_build): rows are sorted by length inside windows of
+// 256 rows and grouped into slices of 8 rows padded to a common length (a
+// multiple of 4); padding entries point at the zero row n appended to every
+// gathered block. Each slice is stored row after row, so a row's indices
+// are 16-byte aligned and read four at a time.
+//
+// A CTA walks tiles of consecutive slices (tile k of the CTA is
+// blockIdx.x + k * gridDim.x). A tile's slice offsets, row permutation and
+// index (and weight) range are staged in shared memory by TMA bulk copies
+// into one of two buffers; the copy for tile k + 1 is issued before tile k is
+// processed. Tiles whose entries do not fit read the indices from global
+// memory. Lane group g (LPR lanes, 16 bytes each) owns tile rows g, g + G,
+// ...; the groups of one warp share a slice, so their trip counts match.
+constexpr int kSliceRows = 8;
+
 template <int LPR>
 struct TileCfg {
     static constexpr int rows = (LPR == 2) ? 128 : 64;
+    static constexpr int slices = rows / kSliceRows;
+    static constexpr int sp_ints = slices + 4;  // slices + 1 offsets, rounded up to 16 bytes
     static constexpr int entries = rows * 48;
-    static constexpr int rp_ints = rows + 8;
-    // per buffer: rowptr slice, colidx, val (weighted graphs only)
+    // per buffer: slice offsets, permutation, indices, weights (weighted graphs only)
     __host__ __device__ static constexpr int buf_bytes(bool weighted) {
-        return rp_ints * 4 + entries * 4 * (weighted ? 2 : 1);
+        return (sp_ints + rows) * 4 + entries * 4 * (weighted ? 2 : 1);
     }
     __host__ __device__ static constexpr int smem_bytes(bool weighted) { return 64 + 2 * buf_bytes(weighted); }
 };
 
-template <typename TS, int LPR, int MODE>
+__device__ __forceinline__ int4 lds_int4(const int32_t *p) {
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+__device__ __forceinline__ float4 lds_float4(const float *p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+
+template <bool SMEM>
+__device__ __forceinline__ int4 ld_idx4(const int32_t *p) {
+    if constexpr (SMEM) return lds_int4(p);
+    else return __ldg(reinterpret_cast<const int4 *>(p));
+}
+template <bool SMEM>
+__device__ __forceinline__ float4 ld_val4(const float *p) {
+    if constexpr (SMEM) return lds_float4(p);
+    else return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+// acc += sum over the row's ls entries of w_e * X[idx_e] (this lane's 16 bytes)
+template <typename TS, bool W, bool SMEM>
+__device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rstride, const int32_t *ip,
+                                           const float *wp, int32_t ls, float (&acc)[VT<TS>::V]) {
+    using V = VT<TS>;
+    int32_t j = 0;
+    for (; j + 8 <= ls; j += 8) {
+        const int4 a = ld_idx4<SMEM>(ip + j), b = ld_idx4<SMEM>(ip + j + 4);
+        const int32_t k[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        typename V::raw_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = V::ld_raw(Xq + (uint32_t)k[u] * (uint32_t)rstride);
+        if constexpr (W) {
+            const float4 wa = ld_val4<SMEM>(wp + j), wb = ld_val4<SMEM>(wp + j + 4);
+            const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) V::fma_raw(acc, w[u], x[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) V::add_raw(acc, x[u]);
+        }
+    }
+    if (j < ls) {  // ls is a multiple of 4
+        const int4 a = ld_idx4<SMEM>(ip + j);
+        const int32_t k[4] = {a.x, a.y, a.z, a.w};
+        typename V::raw_t x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = V::ld_raw(Xq + (uint32_t)k[u] * (uint32_t)rstride);
+        if constexpr (W) {
+            const float4 wa = ld_val4<SMEM>(wp + j);
+            const float w[4] = {wa.x, wa.y, wa.z, wa.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) V::fma_raw(acc, w[u], x[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) V::add_raw(acc, x[u]);
+        }
+    }
+}
+
+template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
     using V = VT<TS>;
     using C = TileCfg<LPR>;
     constexpr int VEC = V::V;
-    constexpr int U = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const bool weighted = P.val != nullptr;
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
-    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: a0, fits
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
     unsigned char *s_buf0 = smem_raw + 64;
-    const int buf_bytes = C::buf_bytes(weighted);
+    constexpr int buf_bytes = C::buf_bytes(W);
     __shared__ double s_red[8][2];
 
     const int tid = threadIdx.x;
     const int q = tid % LPR, grp = tid / LPR;
     const int ngrp = blockDim.x / LPR;
-    const int32_t n = P.n;
-    const int n_tiles = (n + C::rows - 1) / C::rows;
+    const int n_tiles = (P.n + C::rows - 1) / C::rows;
     const TS *__restrict__ X = static_cast<const TS *>(P.X);
     const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
     TS *__restrict__ out = static_cast<TS *>(P.out);
     const int32_t ld = P.ld;
     const float m = P.m;
+    const TS *__restrict__ Xq = X + q * VEC;
     double mtt = 0.0, mtx = 0.0;
 
     // thread 0: stage tile `tile` into buffer `b`
     auto issue = [&](int tile, int b) {
         unsigned char *base = s_buf0 + b * buf_bytes;
-        int32_t *rp = reinterpret_cast<int32_t *>(base);
-        int32_t *col = rp + C::rp_ints;
-        float *val = reinterpret_cast<float *>(col + C::entries);
-        const int32_t r0 = tile * C::rows;
-        const int32_t nr = min(C::rows, n - r0);
-        const int32_t e0 = P.rowptr[r0], e1 = P.rowptr[r0 + nr];
-        const int32_t a0 = e0 & ~3;
-        const int64_t a1 = ((int64_t)e1 + 3) & ~(int64_t)3;
-        const int32_t cnt = (int32_t)(a1 - a0);
-        const int32_t rp_cnt = (nr + 1 + 3) & ~3;
+        int32_t *sp = reinterpret_cast<int32_t *>(base);
+        int32_t *pm = sp + C::sp_ints;
+        int32_t *ix = pm + C::rows;
+        float *wv = reinterpret_cast<float *>(ix + C::entries);
+        const int32_t s0 = tile * C::slices;
+        const int32_t e0 = P.sell_ptr[s0], e1 = P.sell_ptr[s0 + C::slices];
+        const int32_t cnt = e1 - e0;  // multiple of 32
         const bool fits = cnt <= C::entries;
-        const uint32_t bytes = rp_cnt * 4 + (fits ? (uint32_t)cnt * 4u * (weighted ? 2u : 1u) : 0u);
-        s_meta[2 * b] = a0;
+        const uint32_t bytes = (C::sp_ints + C::rows) * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
+        s_meta[2 * b] = e0;
         s_meta[2 * b + 1] = fits ? 1 : 0;
         fence_proxy_async();
         mbar_arrive_expect_tx(&s_bar[b], bytes);
-        bulk_g2s(rp, P.rowptr + r0, rp_cnt * 4, &s_bar[b]);
+        bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
+        bulk_g2s(pm, P.sell_perm + (int64_t)s0 * kSliceRows, C::rows * 4, &s_bar[b]);
         if (fits && cnt > 0) {
-            bulk_g2s(col, P.colidx + a0, cnt * 4, &s_bar[b]);
-            if (weighted) bulk_g2s(val, P.val + a0, cnt * 4, &s_bar[b]);
+            bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
+            if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
         }
     };
 
@@ -273,20 +359,20 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
             if (tile + (int)gridDim.x < n_tiles) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
             return;
         }
-        const int32_t r0 = tile * C::rows;
-        const int32_t nr = min(C::rows, n - r0);
-        const int32_t *s_rp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
-        const int32_t *s_col = s_rp + C::rp_ints;
-        const float *s_val = reinterpret_cast<const float *>(s_col + C::entries);
-        const int32_t a0 = s_meta[2 * b];
+        const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
+        const int32_t *s_pm = s_sp + C::sp_ints;
+        const int32_t *s_ix = s_pm + C::rows;
+        const float *s_wv = reinterpret_cast<const float *>(s_ix + C::entries);
+        const int32_t e0 = s_meta[2 * b];
         const bool fits = s_meta[2 * b + 1] != 0;
-        const int32_t *colp = fits ? s_col : P.colidx + a0;
-        const float *valp = fits ? s_val : (weighted ? P.val + a0 : nullptr);
 
-        for (int rr = grp; rr < nr; rr += ngrp) {
-            const int64_t i = (int64_t)r0 + rr;
-            const int32_t beg = s_rp[rr] - a0, end = s_rp[rr + 1] - a0;
-            const int64_t ro = i * ld + q * VEC;
+        for (int tr = grp; tr < C::rows; tr += ngrp) {
+            const int32_t i = s_pm[tr];
+            if (i < 0) continue;
+            const int sl = tr / kSliceRows, pos = tr % kSliceRows;
+            const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
+            const int32_t eo = so - e0 + pos * ls;  // offset of the row's first entry in the tile
+            const int64_t ro = (int64_t)i * ld + q * VEC;
             // epilogue operands first (kept packed): their latency overlaps the gathers
             const typename V::raw_t xi_r = V::ld_raw(X + ro);
             const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
@@ -299,22 +385,9 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
             float acc[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-            for (int32_t e = beg; e < end; e += U) {
-                int32_t k[U];
-                float wv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const bool ok = e + u < end;
-                    k[u] = ok ? colp[e + u] : 0;
-                    wv[u] = ok ? (weighted ? valp[e + u] : 1.0f) : 0.0f;
-                }
-                typename V::raw_t xr[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    xr[u] = (e + u < end) ? V::ld_raw(X + (int64_t)k[u] * ld + q * VEC) : V::zero_raw();
-#pragma unroll
-                for (int u = 0; u < U; ++u) V::fma_raw(acc, wv[u], xr[u]);
-            }
+            if (fits) gather_row<TS, W, true>(Xq, ld, s_ix + eo, s_wv + eo, ls, acc);
+            else gather_row<TS, W, false>(Xq, ld, P.sell_idx + e0 + eo, P.sell_val + e0 + eo, ls, acc);
+
 
             float t[VEC], xi[VEC];
             {
@@ -501,6 +574,7 @@ struct SweepShape {
     int block;        // threads per block
     int grid;         // blocks
     int smem;         // dynamic shared memory per block
+    bool weighted;    // kernel reads weights
 };
 
 // Picks the slab width (columns) for n rows and n_sig signals.
