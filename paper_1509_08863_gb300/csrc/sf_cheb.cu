@@ -67,6 +67,19 @@ static int step_smem(int lpr, bool weighted, int warps) {
     return per * warps;
 }
 
+int32_t *device_status() {
+    static int32_t *cache[64] = {nullptr};
+    const int d = current_device();
+    if (d < 64 && cache[d]) return cache[d];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sweep_status) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (d < 64) cache[d] = static_cast<int32_t *>(p);
+    return static_cast<int32_t *>(p);
+}
+
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
                      SweepShape *sh) {
     SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage type %d is not supported (SF_F32 or SF_BF16)",
