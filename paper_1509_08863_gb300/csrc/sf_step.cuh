@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
         const int32_t cnt = sp[C::spw] - sp[0];  // multiple of 32
         const bool fits = cnt <= C::entries;
         const uint32_t bytes = C::rows * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
-        fence_proxy_async();
+        // The buffer's previous contents were only read (generic proxy) before
+        // the warp's __syncwarp; the copy engine's writes are ordered after that
+        // barrier, so no proxy fence is needed here.
         mbar_arrive_expect_tx(&s_bar[b], bytes);
         bulk_g2s_hint(pm, P.sell_perm + t * C::rows, C::rows * 4, &s_bar[b], pol);
         if (fits && cnt > 0) {
