@@ -290,7 +290,6 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         P.rowptr = g->rowptr;
         P.colidx = g->colidx;
         P.val = val;
-        P.sell_slices = g->sell.n_slices;
         P.sell_ptr = g->sell.sptr;
         P.sell_perm = g->sell.perm;
         P.sell_idx = g->sell.idx;

@@ -55,16 +55,14 @@ static const void *kernel_for(int storage, int lpr, int mode, bool weighted) {
 
 __device__ int32_t g_sweep_status;
 
-static int step_smem(int lpr, bool weighted, int warps) {
-    int per = 0;
+static int step_smem(int lpr, bool weighted) {
     switch (lpr) {
-        case 2: per = weighted ? WarpCfg<2, true>::warp_bytes() : WarpCfg<2, false>::warp_bytes(); break;
-        case 4: per = weighted ? WarpCfg<4, true>::warp_bytes() : WarpCfg<4, false>::warp_bytes(); break;
-        case 8: per = weighted ? WarpCfg<8, true>::warp_bytes() : WarpCfg<8, false>::warp_bytes(); break;
-        case 16: per = weighted ? WarpCfg<16, true>::warp_bytes() : WarpCfg<16, false>::warp_bytes(); break;
-        default: per = weighted ? WarpCfg<32, true>::warp_bytes() : WarpCfg<32, false>::warp_bytes(); break;
+        case 2: return TileCfg<2>::smem_bytes(weighted);
+        case 4: return TileCfg<4>::smem_bytes(weighted);
+        case 8: return TileCfg<8>::smem_bytes(weighted);
+        case 16: return TileCfg<16>::smem_bytes(weighted);
+        default: return TileCfg<32>::smem_bytes(weighted);
     }
-    return per * warps;
 }
 
 int32_t *device_status() {
@@ -93,7 +91,7 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
     const void *fn = kernel_for(storage, lpr, mode, weighted);
     SF_ARG(fn, "no kernel for this shape");
-    const int smem = step_smem(lpr, weighted, block_warps);
+    const int smem = step_smem(lpr, weighted);
     SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        cudaSharedmemCarveoutMaxShared));
@@ -252,8 +250,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         if ((st = sc.get(&wscale, (size_t)n))) return st;
         if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
     }
-    const int n_warps = sh.grid * (sh.block / 32);
-    if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * n_warps + 2 * sm_count() + 2))) return st;
+    if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * sh.grid + 2))) return st;
 
     if (ncoef) {
         std::vector<float> cf((size_t)ncoef);
@@ -277,7 +274,6 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         P.rowptr = G.rowptr;
         P.colidx = G.colidx;
         P.val = G.val;
-        P.sell_slices = G.sell->n_slices;
         P.sell_ptr = G.sell->sptr;
         P.sell_perm = G.sell->perm;
         P.sell_idx = G.sell->idx;
@@ -315,7 +311,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false);
                 if ((st = launch_step(sh, mode, P, s, by))) return st;
                 if (mode == MODE_MOM) {
-                    pair_sum_kernel<<<1, 256, 0, s>>>(part, n_warps, 2, mom + 2 * j);
+                    pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 2, mom + 2 * j);
                     if ((st = check_launch("pair_sum_kernel"))) return st;
                 }
             }

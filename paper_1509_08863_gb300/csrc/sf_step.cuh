@@ -127,7 +127,6 @@ struct StepParams {
     const int32_t *rowptr;
     const int32_t *colidx;
     const float *val;       // nullptr: all weights 1
-    int64_t sell_slices;       // sliced-ELL: number of slices (a multiple of 16)
     const int32_t *sell_ptr;   // sliced-ELL: entry offset of each slice
     const int32_t *sell_perm;  // original row of each slice row (-1: none)
     const int32_t *sell_idx;   // column indices (n for padding)
@@ -151,7 +150,7 @@ struct StepParams {
     int32_t coef_ld;        // p + 1
     int32_t j;              // coefficient index used by this order
     // moments
-    double *part;           // [warps][2]: sum t.t, sum t.x
+    double *part;           // [gridDim.x][2]: sum t.t, sum t.x
     int32_t *status;        // device error word (bit 0: a bounded wait gave up)
 };
 
@@ -196,32 +195,32 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ------------------------------------------------------------ the sweep
 // The sweep reads the graph in a sliced-ELL layout (built from the CSR by
-// the library, see sf_sell.cu): rows are sorted by length inside windows of
+// the library, see sell_build): rows are sorted by length inside windows of
 // 256 rows and grouped into slices of 8 rows padded to a common length (a
 // multiple of 4); padding entries point at the zero row n appended to every
 // gathered block. Each slice is stored row after row, so a row's indices
-// are 16-byte aligned and read four at a time, and the groups of one warp
-// (which share a slice) have equal trip counts.
+// are 16-byte aligned and read four at a time.
 //
-// Every warp runs its own pipeline: warp tile k of global warp w is
-// SPW consecutive slices starting at SPW * (w + k * warps). Lane 0 stages
-// a tile's row permutation and index (and weight) range in the warp's
-// shared memory by TMA bulk copies (L2 evict-first: the index stream is read
-// once per sweep) into one of two buffers, issuing tile k + 1 before tile k
-// is processed; the slice offsets it needs are loaded two tiles ahead. No
-// barrier spans warps. A tile whose entries do not fit is read from global
-// memory.
+// A CTA walks tiles of consecutive slices (tile k of the CTA is
+// blockIdx.x + k * gridDim.x). A tile's slice offsets, row permutation and
+// index (and weight) range are staged in shared memory by TMA bulk copies
+// into one of two buffers; the copy for tile k + 1 is issued before tile k is
+// processed. Tiles whose entries do not fit read the indices from global
+// memory. Lane group g (LPR lanes, 16 bytes each) owns tile rows g, g + G,
+// ...; the groups of one warp share a slice, so their trip counts match.
 constexpr int kSliceRows = 8;
 
-template <int LPR, bool W>
-struct WarpCfg {
-    static constexpr int spw = (LPR == 2) ? 2 : 1;         // slices per warp tile
-    static constexpr int rows = spw * kSliceRows;          // rows per warp tile
-    static constexpr int groups = 32 / LPR;                // lane groups per warp
-    static constexpr int entries = rows * (W ? 40 : 56);   // staged entries per buffer
-    // per buffer: permutation, indices, weights (weighted graphs only)
-    __host__ __device__ static constexpr int buf_bytes() { return rows * 4 + entries * 4 * (W ? 2 : 1); }
-    __host__ __device__ static constexpr int warp_bytes() { return 16 + 2 * buf_bytes(); }
+template <int LPR>
+struct TileCfg {
+    static constexpr int rows = (LPR == 2) ? 128 : 64;
+    static constexpr int slices = rows / kSliceRows;
+    static constexpr int sp_ints = slices + 4;  // slices + 1 offsets, rounded up to 16 bytes
+    static constexpr int entries = rows * 48;
+    // per buffer: slice offsets, permutation, indices, weights (weighted graphs only)
+    __host__ __device__ static constexpr int buf_bytes(bool weighted) {
+        return (sp_ints + rows) * 4 + entries * 4 * (weighted ? 2 : 1);
+    }
+    __host__ __device__ static constexpr int smem_bytes(bool weighted) { return 64 + 2 * buf_bytes(weighted); }
 };
 
 __device__ __forceinline__ int4 lds_int4(const int32_t *p) {
@@ -248,21 +247,6 @@ template <bool SMEM>
 __device__ __forceinline__ float4 ld_val4(const float *p) {
     if constexpr (SMEM) return lds_float4(p);
     else return __ldg(reinterpret_cast<const float4 *>(p));
-}
-
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-// bulk copy with an L2 eviction-priority hint
-__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
-                                              uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
 }
 
 // acc += sum over the row's ls entries of w_e * X[idx_e] (this lane's 16 bytes)
@@ -308,19 +292,19 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
 template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
     using V = VT<TS>;
-    using C = WarpCfg<LPR, W>;
+    using C = TileCfg<LPR>;
     constexpr int VEC = V::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    unsigned char *wbase = smem_raw + wib * C::warp_bytes();
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(wbase);  // [2]
-    unsigned char *s_buf0 = wbase + 16;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
+    unsigned char *s_buf0 = smem_raw + 64;
+    constexpr int buf_bytes = C::buf_bytes(W);
+    __shared__ double s_red[8][2];
 
-    const int q = lane % LPR, grp = lane / LPR;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t n_wt = P.sell_slices / C::spw;  // slice count is padded to a multiple of 16
+    const int tid = threadIdx.x;
+    const int q = tid % LPR, grp = tid / LPR;
+    const int ngrp = blockDim.x / LPR;
+    const int n_tiles = (P.n + C::rows - 1) / C::rows;
     const TS *__restrict__ X = static_cast<const TS *>(P.X);
     const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
@@ -329,77 +313,64 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
     const float m = P.m;
     const TS *__restrict__ Xq = X + q * VEC;
     double mtt = 0.0, mtx = 0.0;
-    uint64_t pol = 0;
 
-    // slice offsets of warp tile t: sptr[s0 .. s0 + spw]
-    auto load_sp = [&](int64_t t, int32_t (&sp)[C::spw + 1]) {
-        if (t < n_wt) {
-#pragma unroll
-            for (int k = 0; k <= C::spw; ++k) sp[k] = __ldg(P.sell_ptr + t * C::spw + k);
-        }
-    };
-    // lane 0: stage warp tile t (offsets sp) into buffer b
-    auto issue = [&](int64_t t, const int32_t (&sp)[C::spw + 1], int b) {
-        unsigned char *base = s_buf0 + b * C::buf_bytes();
-        int32_t *pm = reinterpret_cast<int32_t *>(base);
+    // thread 0: stage tile `tile` into buffer `b`
+    auto issue = [&](int tile, int b) {
+        unsigned char *base = s_buf0 + b * buf_bytes;
+        int32_t *sp = reinterpret_cast<int32_t *>(base);
+        int32_t *pm = sp + C::sp_ints;
         int32_t *ix = pm + C::rows;
         float *wv = reinterpret_cast<float *>(ix + C::entries);
-        const int32_t cnt = sp[C::spw] - sp[0];  // multiple of 32
+        const int32_t s0 = tile * C::slices;
+        const int32_t e0 = P.sell_ptr[s0], e1 = P.sell_ptr[s0 + C::slices];
+        const int32_t cnt = e1 - e0;  // multiple of 32
         const bool fits = cnt <= C::entries;
-        const uint32_t bytes = C::rows * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
-        // The buffer's previous contents were only read (generic proxy) before
-        // the warp's __syncwarp; the copy engine's writes are ordered after that
-        // barrier, so no proxy fence is needed here.
+        const uint32_t bytes = (C::sp_ints + C::rows) * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
+        s_meta[2 * b] = e0;
+        s_meta[2 * b + 1] = fits ? 1 : 0;
+        fence_proxy_async();
         mbar_arrive_expect_tx(&s_bar[b], bytes);
-        bulk_g2s_hint(pm, P.sell_perm + t * C::rows, C::rows * 4, &s_bar[b], pol);
+        bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
+        bulk_g2s(pm, P.sell_perm + (int64_t)s0 * kSliceRows, C::rows * 4, &s_bar[b]);
         if (fits && cnt > 0) {
-            bulk_g2s_hint(ix, P.sell_idx + sp[0], cnt * 4, &s_bar[b], pol);
-            if (W) bulk_g2s_hint(wv, P.sell_val + sp[0], cnt * 4, &s_bar[b], pol);
+            bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
+            if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
         }
     };
 
-    int32_t sp0[C::spw + 1], sp1[C::spw + 1], sp2[C::spw + 1];
-#pragma unroll
-    for (int k = 0; k <= C::spw; ++k) sp0[k] = sp1[k] = sp2[k] = 0;
-    load_sp(gw, sp0);
-    load_sp(gw + nw, sp1);
-    if (lane == 0) {
-        pol = l2_evict_first_policy();
+    if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         fence_mbar_init();
-        if (gw < n_wt) issue(gw, sp0, 0);
+        if ((int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
     }
-    __syncwarp();
-    for (int64_t k = 0;; ++k) {
-        const int64_t t = gw + k * nw;
-        if (t >= n_wt) break;
-        const int b = (int)(k & 1);
-        // buffer b^1 was released by the __syncwarp that ended the previous tile
-        if (lane == 0 && t + nw < n_wt) issue(t + nw, sp1, b ^ 1);
-        load_sp(t + 2 * nw, sp2);
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= n_tiles) break;
+        const int b = k & 1;
+        // buffer b^1 was released by the barrier that ended the previous tile
+        if (tid == 0 && tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
         const bool landed = mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
-        if (__any_sync(0xffffffffu, !landed)) {
-            if (lane == 0) atomicOr(P.status, 1);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicOr(P.status, 1);
             // one more bounded chance for copies still in flight before leaving
             mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
-            if (t + nw < n_wt) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            if (tile + (int)gridDim.x < n_tiles) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
             return;
         }
-        const int32_t *s_pm = reinterpret_cast<const int32_t *>(s_buf0 + b * C::buf_bytes());
+        const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
+        const int32_t *s_pm = s_sp + C::sp_ints;
         const int32_t *s_ix = s_pm + C::rows;
         const float *s_wv = reinterpret_cast<const float *>(s_ix + C::entries);
-        const int32_t e0 = sp0[0];
-        const bool fits = (sp0[C::spw] - e0) <= C::entries;
+        const int32_t e0 = s_meta[2 * b];
+        const bool fits = s_meta[2 * b + 1] != 0;
 
-#pragma unroll 1
-        for (int tr = grp; tr < C::rows; tr += C::groups) {
+        for (int tr = grp; tr < C::rows; tr += ngrp) {
             const int32_t i = s_pm[tr];
             if (i < 0) continue;
             const int sl = tr / kSliceRows, pos = tr % kSliceRows;
-            const int32_t so = (C::spw == 1 || sl == 0) ? sp0[0] : sp0[1];
-            const int32_t se = (C::spw == 1 || sl == 1) ? sp0[C::spw] : sp0[1];
-            const int32_t ls = (se - so) / kSliceRows;
+            const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
             const int32_t eo = so - e0 + pos * ls;  // offset of the row's first entry in the tile
             const int64_t ro = (int64_t)i * ld + q * VEC;
             // epilogue operands first (kept packed): their latency overlaps the gathers
@@ -416,6 +387,7 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
             for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
             if (fits) gather_row<TS, W, true>(Xq, ld, s_ix + eo, s_wv + eo, ls, acc);
             else gather_row<TS, W, false>(Xq, ld, P.sell_idx + e0 + eo, P.sell_val + e0 + eo, ls, acc);
+
 
             float t[VEC], xi[VEC];
             {
@@ -467,23 +439,29 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
                 mtx += (double)tx;
             }
         }
-        __syncwarp();  // buffer b fully consumed before lane 0 refills it
-#pragma unroll
-        for (int c = 0; c <= C::spw; ++c) {
-            sp0[c] = sp1[c];
-            sp1[c] = sp2[c];
-        }
+        __syncthreads();  // buffer b fully consumed before it is refilled
     }
     if (MODE == MODE_MOM) {
-        // fixed-order reduction over the warp's lanes; one partial per warp
+        // fixed-order reduction: lanes of a warp, then warps of the block
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             mtt += __shfl_xor_sync(0xffffffffu, mtt, off);
             mtx += __shfl_xor_sync(0xffffffffu, mtx, off);
         }
-        if (lane == 0) {
-            P.part[2 * gw] = mtt;
-            P.part[2 * gw + 1] = mtx;
+        const int w = tid >> 5;
+        if ((tid & 31) == 0) {
+            s_red[w][0] = mtt;
+            s_red[w][1] = mtx;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                a += s_red[k][0];
+                b += s_red[k][1];
+            }
+            P.part[2 * blockIdx.x] = a;
+            P.part[2 * blockIdx.x + 1] = b;
         }
     }
 }
