@@ -239,17 +239,29 @@ def main():
     src_d, dst_d, R_d = src_h.to(dev), dst_h.to(dev), R_h.to(dev)
     stream = torch.cuda.current_stream()
 
+    # tile shapes from the autotuner (untimed; cached per graph size)
+    g0 = sf.csr_build(n, src_d, dst_d, None)
+    tuned = {sf.F32: sf.autotune(g0, eta, sf.F32, 1), storage: sf.autotune(g0, eta, storage, 1)}
+    g0.free()
+
+    def opts_for(st):
+        t = tuned[st]
+        return sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW, slab_cols=t.slab_cols, block_warps=t.block_warps,
+                       blocks_per_sm=t.blocks_per_sm)
+
     def step(src, dst, Rt, st, collect=None):
         g = sf.csr_build(n, src, dst, None)
         _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
-        mu = sf.cheb_moments(g, lh, Rt, p, sf.Opts(storage=sf.F32))
+        mu = sf.cheb_moments(g, lh, Rt, p, opts_for(sf.F32))
         if dist:
             t = torch.as_tensor(mu, device=dev)
             dist.all_reduce(t)
             mu = t.cpu().numpy()
         lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
         a = sf.cheb_coeffs(lh, lk, p, True)
-        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW))[0]
+        if st not in tuned:
+            tuned[st] = sf.autotune(g, eta, st, 1)
+        Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st))[0]
         F = sf.features(Y, True, out=Y)
         if collect is not None:
             collect.update(lam_hat=lh, lam_k=lk, nnz=g.nnz, Y=Y)
@@ -278,6 +290,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = sf.launch_count()
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(steps):
             if e2e:
@@ -287,6 +300,7 @@ def main():
             else:
                 step(src_d, dst_d, R_d, st)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         launches = sf.launch_count() - l0
         ms = e0.elapsed_time(e1) / steps
@@ -306,6 +320,7 @@ def main():
     ms, launches = timed(storage, args.steps, 0)
     k_launches, k_ms, k_bytes = sf.profile_end()
     clocks = clk.stop()
+    sf.device_check()
     value = updates * world / (ms * 1e-3)
 
     # the same step with FP32 blocks in the filter (moment sweep is FP32 in both)
@@ -347,6 +362,9 @@ def main():
         "config": {"workload": args.workload, "N": n, "nnz_off": nnz, "R": eta, "p": p, "k": k,
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
                    "filter_storage": wl["storage"], "moment_storage": "f32", "algo": "clenshaw",
+                   "tiles": {("f32" if k == sf.F32 else "bf16"): {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
+                                                                  "blocks_per_sm": v.blocks_per_sm}
+                             for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"column-shard x{world}" if world > 1 else "single GPU"},
         "gpu_launches": launches,

@@ -15,14 +15,15 @@ namespace sf {
 static int vec_of(int storage) { return storage == SF_F32 ? 4 : 8; }
 static int bytes_of(int storage) { return storage == SF_F32 ? 4 : 2; }
 
+// Default slab: the whole block when it is small enough to stay in L2
+// (n * n_sig * b <= budget), else 4 lanes x 16 bytes per row (16 FP32 or 32
+// BF16 columns), the fastest shape measured on the 1M-node workload.
 int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t budget) {
     const int vec = vec_of(storage), b = bytes_of(storage);
-    // smallest admissible width covering all signals
     int full = vec * 2;
     while (full < n_sig && full < vec * 32) full *= 2;
-    int w = full;
-    while (w > vec * 2 && (int64_t)n * w * b > budget) w /= 2;
-    return w;
+    if ((int64_t)n * full * b <= budget) return full;
+    return full < vec * 4 ? full : vec * 4;
 }
 
 template <typename TS, int LPR, bool W>
@@ -196,7 +197,7 @@ static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r
         set_error("storage type %d is not supported (SF_F32 or SF_BF16)", r->storage);
         return SF_ERR_ARG;
     }
-    if (r->slab_cols <= 0) r->slab_cols = auto_slab_cols(n, n_sig, r->storage, 48ll << 20);
+    if (r->slab_cols <= 0) r->slab_cols = auto_slab_cols(n, n_sig, r->storage, 32ll << 20);
     return SF_OK;
 }
 
