@@ -314,8 +314,11 @@ SF_API sf_status sf_device_check(void *stream);
  * Time candidate tile shapes (slab width, warps per block, blocks per SM) of
  * the sweep kernel on this graph for n_sig signals and the given storage
  * type, a few orders each, and write the fastest into *best (other fields
- * copied from *base, which may be NULL). Results are cached per
- * (N, nnz, n_sig, storage, n_cut) in the process. Synchronises `stream`.
+ * copied from *base, which may be NULL). Candidates are ranked by the summed
+ * duration of their sweep-kernel launches (the kernel timing hooks below,
+ * which this call uses and leaves off). Results are cached per
+ * (N, nnz, n_sig, storage, n_cut, device) in the process. Synchronises
+ * `stream`.
  */
 SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, int32_t n_cut,
                              const sf_opts *base, void *stream, sf_opts *best);

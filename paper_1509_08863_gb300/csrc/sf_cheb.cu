@@ -528,7 +528,10 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
     const int vec = vec_of(storage);
     int full = vec * 2;
     while (full < n_sig && full < vec * 32) full *= 2;
-    const int p_try = 6;
+    // Candidates are compared on the summed duration of their sweep-kernel
+    // launches (kernel timing hooks), so per-call overheads that a long
+    // filter amortises do not bias the choice.
+    const int p_try = 8;
     Scratch sc(s);
     float *R = nullptr, *Y = nullptr;
     sf_status st;
@@ -536,32 +539,27 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
     if ((st = sc.get(&Y, (size_t)g->n * n_sig * n_cut))) return st;
     SF_CHECK_CUDA(cudaMemsetAsync(R, 0, sizeof(float) * g->n * n_sig, s));
     std::vector<double> cf((size_t)n_cut * (p_try + 1), 0.1);
-    cudaEvent_t e0, e1;
-    SF_CHECK_CUDA(cudaEventCreate(&e0));
-    SF_CHECK_CUDA(cudaEventCreate(&e1));
-    float best_ms = 1e30f;
+    double best_ms = 1e300;
     sf_opts bo = b0;
     const int warps_opts[2] = {4, 8};
+    const int bps_opts[3] = {0, 2, 3};
+    const double lam = 2.0 * g->max_strength + 1.0;
     for (int w = full; w >= vec * 2; w /= 2) {
         for (int wi = 0; wi < 2; ++wi) {
-            for (int bps = 0; bps <= 4; bps += 2) {
+            for (int bi = 0; bi < 3; ++bi) {
                 sf_opts t = b0;
                 t.slab_cols = w;
                 t.block_warps = warps_opts[wi];
-                t.blocks_per_sm = bps;
+                t.blocks_per_sm = bps_opts[bi];
                 t.algo = n_cut == 1 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
-                // warm-up then time
-                st = sf_cheb_filter(g, 2.0 * g->max_strength + 1.0, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t,
-                                    stream);
+                st = sf_cheb_filter(g, lam, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t, stream);  // warm-up
                 if (st) continue;
-                cudaEventRecord(e0, s);
-                st = sf_cheb_filter(g, 2.0 * g->max_strength + 1.0, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t,
-                                    stream);
-                cudaEventRecord(e1, s);
-                if (st) continue;
-                if (cudaEventSynchronize(e1) != cudaSuccess) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
+                sf_profile_begin();
+                st = sf_cheb_filter(g, lam, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t, stream);
+                int64_t nl = 0;
+                double ms = 0.0, by = 0.0;
+                sf_status st2 = sf_profile_end(&nl, &ms, &by);
+                if (st || st2) continue;
                 if (ms < best_ms) {
                     best_ms = ms;
                     bo = t;
@@ -569,8 +567,6 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     SF_CHECK_CUDA(cudaGetLastError());
     bo.algo = base ? base->algo : SF_ALGO_AUTO;
     {
