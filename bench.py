@@ -408,8 +408,9 @@ def cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev):
     Rt = torch.as_tensor(R, dtype=torch.float32, device=dev)
     acc = {}
     rows = np.random.default_rng(5).choice(n, size=min(50_000, n), replace=False)
-    for name, st in (("f32", sf.F32), ("bf16", sf.BF16)):
-        Y = sf.cheb_filter(gg, lh, a, Rt, sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW))[0][:, 0].cpu().numpy()
+    for name, st, algo in (("f32", sf.F32, sf.ALGO_CLENSHAW), ("bf16", sf.BF16, sf.ALGO_CLENSHAW),
+                           ("f32_forward", sf.F32, sf.ALGO_FORWARD), ("bf16_forward", sf.BF16, sf.ALGO_FORWARD)):
+        Y = sf.cheb_filter(gg, lh, a, Rt, sf.Opts(storage=st, algo=algo))[0][:, 0].cpu().numpy()
         acc[name] = {
             "rel_fro_all_rows": float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),
             "rel_fro_50k_rows": float(np.linalg.norm(Y[rows] - Yo[rows]) / np.linalg.norm(Yo[rows])),
