@@ -82,6 +82,11 @@ enum {
  *                   under mem_cap_mb, else checkpoint), 1 = store all, k > 1 =
  *                   keep every k-th pair of blocks and recompute the rest.
  *   mem_cap_mb      adjoint only: memory budget for stored T_j blocks (0 = 16384).
+ *   carveout_pct    shared-memory share of the L1/shared array requested for
+ *                   the sweep kernel, in percent (0 = driver default). The L1
+ *                   share holds the gathers in flight, so large values slow
+ *                   the sweep down.
+ *   reserved        must be 0.
  */
 typedef struct sf_opts {
     int32_t storage;
@@ -91,6 +96,8 @@ typedef struct sf_opts {
     int32_t blocks_per_sm;
     int32_t ckpt_every;
     int64_t mem_cap_mb;
+    int32_t carveout_pct;
+    int32_t reserved;
 } sf_opts;
 
 typedef struct sf_graph sf_graph; /* device-resident CSR of W, owned by the library */

@@ -71,6 +71,8 @@ class _Opts(C.Structure):
         ("blocks_per_sm", C.c_int32),
         ("ckpt_every", C.c_int32),
         ("mem_cap_mb", C.c_int64),
+        ("carveout_pct", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -85,10 +87,11 @@ class Opts:
     blocks_per_sm: int = 0
     ckpt_every: int = 0
     mem_cap_mb: int = 0
+    carveout_pct: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.storage, self.algo, self.slab_cols, self.block_warps, self.blocks_per_sm,
-                      self.ckpt_every, self.mem_cap_mb)
+                      self.ckpt_every, self.mem_cap_mb, self.carveout_pct, 0)
 
 
 _vp = C.c_void_p
@@ -427,7 +430,7 @@ def autotune(g: Graph, n_sig: int, storage: int = F32, n_cut: int = 1, base: Opt
     _check(lib().sf_autotune(g.handle, int(n_sig), int(storage), int(n_cut), bp, _stream(), C.byref(best)),
            "sf_autotune")
     return Opts(best.storage, best.algo, best.slab_cols, best.block_warps, best.blocks_per_sm, best.ckpt_every,
-                best.mem_cap_mb)
+                best.mem_cap_mb, best.carveout_pct)
 
 
 def profile_begin():

@@ -80,7 +80,7 @@ int32_t *device_status() {
 }
 
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
-                     SweepShape *sh) {
+                     SweepShape *sh, int carveout_pct) {
     SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage type %d is not supported (SF_F32 or SF_BF16)",
            storage);
     const int vec = vec_of(storage);
@@ -94,8 +94,10 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     SF_ARG(fn, "no kernel for this shape");
     const int smem = step_smem(lpr, weighted);
     SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // The L1 part of the unified L1/shared array tracks the gathers in flight:
+    // by default ask for no more shared memory than the resident blocks need.
     SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       cudaSharedmemCarveoutMaxShared));
+                                       carveout_pct > 0 ? carveout_pct : cudaSharedmemCarveoutDefault));
     int occ = 0;
     SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block_warps * 32, smem));
     if (occ < 1) occ = 1;
@@ -222,7 +224,8 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                             const double *coeffs_host, int n_cut, int p, const void *R, int r_dtype, int n_sig,
                             float *Y, double *mom, const sf_opts &o, cudaStream_t s) {
     SweepShape sh;
-    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh);
+    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh,
+                              o.carveout_pct);
     if (st) return st;
     int32_t *status = device_status();
     SF_ARG(status, "device status word unavailable");

@@ -580,7 +580,7 @@ struct SweepShape {
 // Picks the slab width (columns) for n rows and n_sig signals.
 int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t l2_budget_bytes);
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
-                     SweepShape *sh);
+                     SweepShape *sh, int carveout_pct = 0);
 // Device error word written by the sweep kernels (bounded waits).
 int32_t *device_status();
 sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes);
