@@ -247,7 +247,7 @@ def main():
     def opts_for(st):
         t = tuned[st]
         return sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW, slab_cols=t.slab_cols, block_warps=t.block_warps,
-                       blocks_per_sm=t.blocks_per_sm)
+                       blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct)
 
     def step(src, dst, Rt, st, collect=None):
         g = sf.csr_build(n, src, dst, None)
@@ -363,7 +363,7 @@ def main():
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
                    "filter_storage": wl["storage"], "moment_storage": "f32", "algo": "clenshaw",
                    "tiles": {("f32" if k == sf.F32 else "bf16"): {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
-                                                                  "blocks_per_sm": v.blocks_per_sm}
+                                                                  "carveout_pct": v.carveout_pct}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"column-shard x{world}" if world > 1 else "single GPU"},

@@ -564,15 +564,16 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
     double best_ms = 1e300;
     sf_opts bo = b0;
     const int warps_opts[2] = {4, 8};
-    const int bps_opts[3] = {0, 2, 3};
+    const int carve_opts[3] = {0, 40, 50};
     const double lam = 2.0 * g->max_strength + 1.0;
     for (int w = full; w >= vec * 2; w /= 2) {
         for (int wi = 0; wi < 2; ++wi) {
-            for (int bi = 0; bi < 3; ++bi) {
+            for (int ci = 0; ci < 3; ++ci) {
                 sf_opts t = b0;
                 t.slab_cols = w;
                 t.block_warps = warps_opts[wi];
-                t.blocks_per_sm = bps_opts[bi];
+                t.blocks_per_sm = 0;
+                t.carveout_pct = carve_opts[ci];
                 t.algo = n_cut == 1 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
                 st = sf_cheb_filter(g, lam, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t, stream);  // warm-up
                 if (st) continue;

@@ -215,7 +215,7 @@ struct TileCfg {
     static constexpr int rows = (LPR == 2) ? 128 : 64;
     static constexpr int slices = rows / kSliceRows;
     static constexpr int sp_ints = slices + 4;  // slices + 1 offsets, rounded up to 16 bytes
-    static constexpr int entries = rows * 48;
+    static constexpr int entries = rows * 44;  // 4 blocks of 256 threads fit a 100 KB shared carveout
     // per buffer: slice offsets, permutation, indices, weights (weighted graphs only)
     __host__ __device__ static constexpr int buf_bytes(bool weighted) {
         return (sp_ints + rows) * 4 + entries * 4 * (weighted ? 2 : 1);
