@@ -305,6 +305,33 @@ SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max
                                         const sf_opts *opts, void *stream);
 
 /*
+ * sf_cheb_moments without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the moments -- code running while a stream
+ * is captured into a CUDA graph, frameworks whose own caching allocator owns
+ * all device memory, latency-bound loops that cannot afford an allocator
+ * call. Its working memory is one fixed 64 MiB array in the library's device
+ * image, held by every GPU that loads the library until the process exits.
+ *   R        device float[N][n_sig] (FP32 signals; blocks are FP32)
+ *   moments  host double[2p + 1], same values as sf_cheb_moments with default
+ *            options
+ * Requirements and behaviour:
+ *   - the graph must already have its sweep layout, which the first
+ *     sf_cheb_moments / sf_cheb_filter / sf_autotune call on it builds
+ *     (SF_ERR_ARG otherwise);
+ *   - SF_ERR_ARG when the working memory, about 3 (N + 1) * 16 * 4 bytes plus
+ *     small tables, exceeds 64 MiB (roughly N > 340,000 for n_sig >= 16);
+ *   - the first call on a device looks up the array's address; make that
+ *     call before any stream capture;
+ *   - calls share the array: calls whose GPU work can overlap (unordered
+ *     streams) race; each call clears what must start at zero;
+ *   - no cudaMalloc, cudaFree or allocating library routine is called.
+ * Synchronises `stream`.
+ */
+SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double lam_max, const float *R, int32_t n_sig,
+                                         int32_t p, double *moments, void *stream);
+
+/*
  * Synchronise `stream` and report whether a sweep kernel gave up a bounded
  * wait for its staged CSR tile since the last check (SF_ERR_TIMEOUT; the
  * flag is then cleared). Entry points that synchronise check it themselves;

@@ -28,6 +28,7 @@ __all__ = [
     "cheb_coeffs",
     "cheb_filter",
     "cheb_moments",
+    "cheb_moments_noalloc",
     "count_from_moments",
     "eigencount",
     "dichotomy",
@@ -137,6 +138,7 @@ def lib():
         "sf_autotune": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_Opts), _vp, C.POINTER(_Opts)]),
         "sf_profile_begin": (_i32, []),
         "sf_device_check": (_i32, [_vp]),
+        "sf_cheb_moments_noalloc": (_i32, [_vp, _f64, _vp, _i32, _i32, _dp, _vp]),
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -311,6 +313,16 @@ def cheb_moments(g: Graph, lam_max: float, R, p: int, opts: Opts | None = None) 
     o, op = _opts_ptr(opts)
     _check(lib().sf_cheb_moments(g.handle, float(lam_max), _dev_ptr(R, None, "R"), _rdtype(R), n_sig, int(p),
                                  mu.ctypes.data_as(_dp), op, _stream()), "sf_cheb_moments")
+    return mu
+
+
+def cheb_moments_noalloc(g: Graph, lam_max: float, R, p: int) -> np.ndarray:
+    """sf_cheb_moments_noalloc: the moments with no device allocation (FP32 R)."""
+    torch = _torch()
+    n, n_sig = R.shape
+    mu = np.zeros(2 * p + 1)
+    _check(lib().sf_cheb_moments_noalloc(g.handle, float(lam_max), _dev_ptr(R, torch.float32, "R"), n_sig, int(p),
+                                         mu.ctypes.data_as(_dp), _stream()), "sf_cheb_moments_noalloc")
     return mu
 
 
