@@ -142,15 +142,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(workload):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def traffic_from_profile(workload, variant):
+    """DRAM bytes per sweep launch of a kernel variant from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"cheb_step_{workload}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("kernel_source_sha") == kernel_source_hash():
-            return d.get("dram_bytes_per_launch")
+            return d["variants"][variant]["dram_bytes_per_launch"]
     except Exception:
         pass
     return None
@@ -319,6 +319,7 @@ def main():
     sf.profile_begin()
     ms, launches = timed(storage, args.steps, 0)
     k_launches, k_ms, k_bytes = sf.profile_end()
+    variants = sf.profile_variants()
     clocks = clk.stop()
     sf.device_check()
     value = updates * world / (ms * 1e-3)
@@ -339,12 +340,17 @@ def main():
 
     # accuracy of this step's features/filter against the FP64 oracle on one column
     hbm, peak_kind = peaks()
-    kernel_gbs = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
-    roof = {"bound": "hbm", "achieved": kernel_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": kernel_gbs / hbm, "traffic": traffic_from_profile(args.workload),
-            "kernel": "cheb_step_kernel", "launches_timed": k_launches,
-            "avg_launch_ms": k_ms / max(k_launches, 1), "bytes_per_launch": k_bytes / max(k_launches, 1),
-            "peak_source": f"{peak_kind} hbm_gbs"}
+
+    def roof_of(name, n_l, ms_, by_):
+        gbs = by_ / (ms_ * 1e-3) / 1e9 if ms_ > 0 else 0.0
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": traffic_from_profile(args.workload, name), "kernel": f"cheb_step_kernel ({name})",
+                "launches_timed": n_l, "avg_launch_ms": ms_ / max(n_l, 1), "bytes_per_launch": by_ / max(n_l, 1),
+                "share_of_sweep_time": ms_ / k_ms if k_ms > 0 else None, "peak_source": f"{peak_kind} hbm_gbs"}
+
+    by_variant = {name: roof_of(name, *v) for name, v in variants.items()}
+    dominant = max(variants.items(), key=lambda kv: kv[1][1])[0] if variants else None
+    roof = by_variant.get(dominant) if dominant else None
 
     result = {
         "metric": "filtered nnz*R*p updates/s",
@@ -369,6 +375,7 @@ def main():
                    "parallelism": f"column-shard x{world}" if world > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_by_variant": by_variant,
         "clocks": clocks,
         "e2e": e2e,
         "fp32_storage": fp32,

@@ -366,6 +366,11 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
  */
 SF_API sf_status sf_profile_begin(void);
 SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
+/*
+ * Per-variant totals of the last sf_profile_end: tag = 2 * mode + b, with
+ * mode 0 forward, 1 moments, 2 Clenshaw and b = 1 for BF16 blocks.
+ */
+SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes);
 
 #ifdef __cplusplus
 }

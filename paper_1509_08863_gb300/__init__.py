@@ -39,6 +39,7 @@ __all__ = [
     "autotune",
     "profile_begin",
     "profile_end",
+    "profile_variants",
     "launch_count",
     "device_check",
     "ChebFilter",
@@ -140,6 +141,7 @@ def lib():
         "sf_device_check": (_i32, [_vp]),
         "sf_cheb_moments_noalloc": (_i32, [_vp, _f64, _vp, _i32, _i32, _dp, _vp]),
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
+        "sf_profile_variant": (_i32, [_i32, C.POINTER(_i64), _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -459,6 +461,21 @@ def profile_end():
 def device_check():
     """Synchronise the current stream; raise if a sweep kernel gave up a bounded wait."""
     _check(lib().sf_device_check(_stream()), "sf_device_check")
+
+
+PROFILE_TAGS = {0: "forward_f32", 1: "forward_bf16", 2: "moments_f32", 3: "moments_bf16", 4: "clenshaw_f32",
+                5: "clenshaw_bf16"}
+
+
+def profile_variants():
+    """{variant name: (launches, ms, bytes)} of the last profile_end()."""
+    out = {}
+    for tag, name in PROFILE_TAGS.items():
+        n, ms, by = _i64(), _f64(), _f64()
+        _check(lib().sf_profile_variant(tag, C.byref(n), C.byref(ms), C.byref(by)), "sf_profile_variant")
+        if n.value:
+            out[name] = (n.value, ms.value, by.value)
+    return out
 
 
 def launch_count() -> int:

@@ -146,7 +146,7 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     sf_status st = check_launch("cheb_step_kernel");
     if (prof) {
         cudaEventRecord(eb, s);
-        profile_record(ea, eb, bytes);
+        profile_record(ea, eb, bytes, mode * 2 + (sh.storage == SF_BF16 ? 1 : 0));
     }
     return st;
 }

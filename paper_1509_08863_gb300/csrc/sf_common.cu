@@ -235,12 +235,22 @@ double tridiag_max_eig_host(int k, const double *a, const double *b) {
 }
 
 // ---------------------------------------------------------------- profiling
+struct ProfRec {
+    int ev;        // index of the first event of the pair
+    double bytes;  // algorithmic bytes of the launch
+    int tag;       // kernel variant
+};
+struct ProfTotals {
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
 struct ProfState {
     std::mutex mu;
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<int, double>> recs;  // index of first event of a pair, bytes
+    std::vector<ProfRec> recs;
     size_t used = 0;
+    ProfTotals last[kProfTags];  // per-variant totals of the last sf_profile_end
 };
 static ProfState &prof() {
     static ProfState p;
@@ -263,12 +273,12 @@ bool profile_events(cudaEvent_t *a, cudaEvent_t *b) {
     return true;
 }
 
-void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes) {
+void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag) {
     ProfState &P = prof();
     std::lock_guard<std::mutex> lk(P.mu);
     (void)a;
     (void)b;
-    P.recs.push_back({(int)P.used, bytes});
+    P.recs.push_back({(int)P.used, bytes, (tag >= 0 && tag < kProfTags) ? tag : 0});
     P.used += 2;
 }
 
@@ -343,20 +353,34 @@ SF_API sf_status sf_profile_begin(void) {
     return SF_OK;
 }
 
+SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes) {
+    SF_ARG(tag >= 0 && tag < kProfTags, "tag must be in [0, %d)", kProfTags);
+    ProfState &P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (launches) *launches = P.last[tag].launches;
+    if (ms) *ms = P.last[tag].ms;
+    if (bytes) *bytes = P.last[tag].bytes;
+    return SF_OK;
+}
+
 SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes) {
     ProfState &P = prof();
     std::lock_guard<std::mutex> lk(P.mu);
     P.on = false;
     double tot = 0.0, by = 0.0;
+    for (auto &t : P.last) t = ProfTotals();
     for (auto &r : P.recs) {
-        cudaEvent_t a = P.pool[r.first], b = P.pool[r.first + 1];
+        cudaEvent_t a = P.pool[r.ev], b = P.pool[r.ev + 1];
         cudaError_t e = cudaEventSynchronize(b);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
         float t = 0.f;
         e = cudaEventElapsedTime(&t, a, b);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
         tot += t;
-        by += r.second;
+        by += r.bytes;
+        P.last[r.tag].launches += 1;
+        P.last[r.tag].ms += t;
+        P.last[r.tag].bytes += r.bytes;
     }
     if (launches) *launches = (int64_t)P.recs.size();
     if (ms) *ms = tot;

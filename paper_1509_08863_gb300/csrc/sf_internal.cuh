@@ -74,8 +74,11 @@ sf_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStr
 sf_status reduce_sum_f64(const double *in, int64_t count, double *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- profiling
+// Kernel variants are tagged mode * 2 + (storage == BF16): forward 0/1,
+// moments 2/3, Clenshaw 4/5.
+constexpr int kProfTags = 8;
 bool profiling_on();
-void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes);
+void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag);
 bool profile_events(cudaEvent_t *a, cudaEvent_t *b);
 
 // ---------------------------------------------------------------- host math
