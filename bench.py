@@ -56,7 +56,43 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--kernel-case", default=None,
+                    help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT (MODE moments|clenshaw|forward, "
+                         "STORAGE f32|bf16) runs two sweeps of --case-orders orders over one column slab of "
+                         "the workload and exits")
+    ap.add_argument("--case-orders", type=int, default=6)
     return ap.parse_args()
+
+
+def run_kernel_case(args, wl):
+    """Two sweeps of one kernel variant over one slab of the workload, for ncu."""
+    import torch
+
+    import paper_1509_08863_gb300 as sf
+    from paper_1509_08863_gb300 import build as sfbuild
+
+    sfbuild.build()
+    mode, stor, slab, warps, carve = args.kernel_case.split(":")
+    slab, warps, carve = int(slab), int(warps), int(carve)
+    st = sf.BF16 if stor == "bf16" else sf.F32
+    algo = {"moments": sf.ALGO_CLENSHAW, "clenshaw": sf.ALGO_CLENSHAW, "forward": sf.ALGO_FORWARD}[mode]
+    gr, R = make_inputs(wl)
+    dev = torch.device("cuda")
+    g = sf.csr_build(wl["n"], torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+    Rs = torch.as_tensor(R[:, :slab], dtype=torch.float32, device=dev).contiguous()
+    _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
+    p = args.case_orders
+    a = sf.cheb_coeffs(lh, 0.05 * lh, p, True)
+    o = sf.Opts(storage=st, algo=algo, slab_cols=slab, block_warps=warps, carveout_pct=carve)
+    for _ in range(2):
+        if mode == "moments":
+            sf.cheb_moments(g, lh, Rs, p, o)
+        else:
+            sf.cheb_filter(g, lh, a, Rs, o)
+    torch.cuda.synchronize()
+    sf.device_check()
+    print(json.dumps({"kernel_case": args.kernel_case, "orders": p, "status": "ok"}))
+    return 0
 
 
 def make_inputs(wl, rank=0):
@@ -209,6 +245,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.kernel_case:
+        return run_kernel_case(args, wl)
 
     import torch
 
