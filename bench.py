@@ -454,7 +454,8 @@ def cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev):
     acc = {}
     rows = np.random.default_rng(5).choice(n, size=min(50_000, n), replace=False)
     for name, st, algo in (("f32", sf.F32, sf.ALGO_CLENSHAW), ("bf16", sf.BF16, sf.ALGO_CLENSHAW),
-                           ("f32_forward", sf.F32, sf.ALGO_FORWARD), ("bf16_forward", sf.BF16, sf.ALGO_FORWARD)):
+                           ("f16", sf.F16, sf.ALGO_CLENSHAW), ("f32_forward", sf.F32, sf.ALGO_FORWARD),
+                           ("bf16_forward", sf.BF16, sf.ALGO_FORWARD), ("f16_forward", sf.F16, sf.ALGO_FORWARD)):
         Y = sf.cheb_filter(gg, lh, a, Rt, sf.Opts(storage=st, algo=algo))[0][:, 0].cpu().numpy()
         acc[name] = {
             "rel_fro_all_rows": float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),

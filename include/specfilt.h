@@ -68,10 +68,13 @@ enum {
 
 /*
  * Tuning and precision options; a NULL sf_opts* means all zero (defaults).
- *   storage         SF_F32 / SF_BF16: element type of the T_j (or Clenshaw
- *                   b_j) blocks kept between orders. Products and
+ *   storage         SF_F32 / SF_BF16 / SF_F16: element type of the T_j (or
+ *                   Clenshaw b_j) blocks kept between orders. Products and
  *                   accumulations are FP32 in every case; the output Y is FP32.
- *                   SF_F16 is reserved and rejected with SF_ERR_ARG.
+ *                   With SF_F16 each column slab of R is first scaled by the
+ *                   power of two that puts its largest magnitude in (1/2, 1]
+ *                   (exact, undone on output), which keeps the blocks inside
+ *                   the FP16 range. The moment sweep rejects SF_F16.
  *   algo            SF_ALGO_*.
  *   slab_cols       signal columns processed per sweep (0 = automatic). The
  *                   signals are independent, so the block is filtered in
@@ -367,8 +370,9 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
 SF_API sf_status sf_profile_begin(void);
 SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
 /*
- * Per-variant totals of the last sf_profile_end: tag = 2 * mode + b, with
- * mode 0 forward, 1 moments, 2 Clenshaw and b = 1 for BF16 blocks.
+ * Per-variant totals of the last sf_profile_end: tag = 3 * mode + storage,
+ * with mode 0 forward, 1 moments, 2 Clenshaw and storage SF_F32 / SF_BF16 /
+ * SF_F16.
  */
 SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes);
 

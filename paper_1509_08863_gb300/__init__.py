@@ -45,6 +45,7 @@ __all__ = [
     "ChebFilter",
     "F32",
     "BF16",
+    "F16",
     "ALGO_AUTO",
     "ALGO_FORWARD",
     "ALGO_CLENSHAW",
@@ -463,8 +464,8 @@ def device_check():
     _check(lib().sf_device_check(_stream()), "sf_device_check")
 
 
-PROFILE_TAGS = {0: "forward_f32", 1: "forward_bf16", 2: "moments_f32", 3: "moments_bf16", 4: "clenshaw_f32",
-                5: "clenshaw_bf16"}
+PROFILE_TAGS = {3 * m + s: f"{mn}_{sn}" for m, mn in enumerate(("forward", "moments", "clenshaw"))
+                for s, sn in enumerate(("f32", "bf16", "f16"))}
 
 
 def profile_variants():

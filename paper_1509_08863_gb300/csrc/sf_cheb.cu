@@ -51,6 +51,8 @@ static const void *kernel_for(int storage, int lpr, int mode, bool weighted) {
     if (storage == SF_F32) return weighted ? step_fn_lpr<float, true>(lpr, mode) : step_fn_lpr<float, false>(lpr, mode);
     if (storage == SF_BF16)
         return weighted ? step_fn_lpr<__nv_bfloat16, true>(lpr, mode) : step_fn_lpr<__nv_bfloat16, false>(lpr, mode);
+    if (storage == SF_F16)
+        return weighted ? step_fn_lpr<__half, true>(lpr, mode) : step_fn_lpr<__half, false>(lpr, mode);
     return nullptr;
 }
 
@@ -81,7 +83,7 @@ int32_t *device_status() {
 
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
                      SweepShape *sh, int carveout_pct) {
-    SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage type %d is not supported (SF_F32 or SF_BF16)",
+    SF_ARG(storage == SF_F32 || storage == SF_BF16 || storage == SF_F16, "storage type %d is not supported",
            storage);
     const int vec = vec_of(storage);
     SF_ARG(slab_cols % vec == 0, "slab_cols %d is not a multiple of %d", slab_cols, vec);
@@ -139,14 +141,17 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     if (sh.storage == SF_F32) {
         if (sh.weighted) launch_lpr<float, true>(mode, sh, P, s);
         else launch_lpr<float, false>(mode, sh, P, s);
-    } else {
+    } else if (sh.storage == SF_BF16) {
         if (sh.weighted) launch_lpr<__nv_bfloat16, true>(mode, sh, P, s);
         else launch_lpr<__nv_bfloat16, false>(mode, sh, P, s);
+    } else {
+        if (sh.weighted) launch_lpr<__half, true>(mode, sh, P, s);
+        else launch_lpr<__half, false>(mode, sh, P, s);
     }
     sf_status st = check_launch("cheb_step_kernel");
     if (prof) {
         cudaEventRecord(eb, s);
-        profile_record(ea, eb, bytes, mode * 2 + (sh.storage == SF_BF16 ? 1 : 0));
+        profile_record(ea, eb, bytes, mode * 3 + sh.storage);
     }
     return st;
 }
@@ -195,8 +200,8 @@ static sf_status view_of(const sf_graph *g, cudaStream_t s, GraphView *v) {
 static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r) {
     sf_opts z = {};
     *r = o ? *o : z;
-    if (r->storage != SF_F32 && r->storage != SF_BF16) {
-        set_error("storage type %d is not supported (SF_F32 or SF_BF16)", r->storage);
+    if (r->storage != SF_F32 && r->storage != SF_BF16 && r->storage != SF_F16) {
+        set_error("storage type %d is not supported (SF_F32, SF_BF16 or SF_F16)", r->storage);
         return SF_ERR_ARG;
     }
     if (r->slab_cols <= 0) r->slab_cols = auto_slab_cols(n, n_sig, r->storage, 32ll << 20);
@@ -206,14 +211,17 @@ static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r
 static sf_status launch_pack(int storage, int grid, cudaStream_t s, const void *R, int r_dtype, int32_t n,
                              int32_t n_sig, int32_t c0, int32_t w, int32_t ld, void *T0, float *Y, int64_t ystride,
                              int32_t n_cut, const float *coef, int32_t coef_ld, int32_t jcoef, const int32_t *gid,
-                             void *bstart, double *part) {
+                             void *bstart, double *part, const uint32_t *maxbits) {
     if (storage == SF_F32)
         pack_kernel<float><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (float *)T0, Y, ystride, n_cut, coef,
-                                                coef_ld, jcoef, gid, (float *)bstart, part);
-    else
+                                                coef_ld, jcoef, gid, (float *)bstart, part, maxbits);
+    else if (storage == SF_BF16)
         pack_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (__nv_bfloat16 *)T0, Y,
                                                         ystride, n_cut, coef, coef_ld, jcoef, gid,
-                                                        (__nv_bfloat16 *)bstart, part);
+                                                        (__nv_bfloat16 *)bstart, part, maxbits);
+    else
+        pack_kernel<__half><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (__half *)T0, Y, ystride, n_cut,
+                                                 coef, coef_ld, jcoef, gid, (__half *)bstart, part, maxbits);
     return check_launch("pack_kernel");
 }
 
@@ -255,6 +263,14 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
     }
     if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * sh.grid + 2))) return st;
+    // FP16 blocks: each slab is scaled by a power of two so that its largest
+    // magnitude lies in (1/2, 1]; the filter is linear, so the output is
+    // unscaled exactly at unpack time
+    uint32_t *maxbits = nullptr;
+    if (o.storage == SF_F16) {
+        SF_ARG(mode != MODE_MOM, "the moment sweep needs SF_F32 or SF_BF16 blocks");
+        if ((st = sc.get(&maxbits, 1))) return st;
+    }
 
     if (ncoef) {
         std::vector<float> cf((size_t)ncoef);
@@ -296,10 +312,16 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         P.status = status;
         const bool unit = G.val == nullptr;
         const bool batched = G.gid != nullptr;
+        if (maxbits) {
+            SF_CHECK_CUDA(cudaMemsetAsync(maxbits, 0, sizeof(uint32_t), s));
+            absmax_kernel<<<pack_grid, 256, 0, s>>>(R, r_dtype, (int32_t)n, n_sig, c0, w, maxbits);
+            if ((st = check_launch("absmax_kernel"))) return st;
+        }
         if (mode == MODE_FWD || mode == MODE_MOM) {
             // T_0 = R (and Y_c = a_c0 T_0, or <T0,T0>)
             if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, buf[0], yacc,
-                                  n * ld, n_cut, coef, p + 1, 0, G.gid, nullptr, mode == MODE_MOM ? part : nullptr)))
+                                  n * ld, n_cut, coef, p + 1, 0, G.gid, nullptr, mode == MODE_MOM ? part : nullptr,
+                                  maxbits)))
                 return st;
             if (mode == MODE_MOM) {
                 pair_sum_kernel<<<1, 256, 0, s>>>(part, pack_grid, 1, mom);
@@ -323,7 +345,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
             // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};
             // Y = a_0 R + Lt b_1 - b_2.
             if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, nullptr,
-                                  0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr)))
+                                  0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr, maxbits)))
                 return st;
             P.Q = qbuf;
             for (int j = p - 1; j >= 0; --j) {
@@ -346,12 +368,12 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
             if (p == 0) {
                 // Y = a_0 R: b_0 computed by the pack as a_p R with p = 0, widen to fp32
                 if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, yacc,
-                                      n * ld, 1, coef, 1, 0, G.gid, nullptr, nullptr)))
+                                      n * ld, 1, coef, 1, 0, G.gid, nullptr, nullptr, maxbits)))
                     return st;
             }
         }
         if (ncy) {
-            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0);
+            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0, maxbits);
             if ((st = check_launch("unpack_kernel"))) return st;
         }
     }
@@ -526,7 +548,7 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
                              const sf_opts *base, void *stream, sf_opts *best) {
     SF_ARG(g && best, "null pointer");
     SF_ARG(n_sig >= 1 && n_cut >= 1, "need n_sig >= 1 and n_cut >= 1");
-    SF_ARG(storage == SF_F32 || storage == SF_BF16, "storage must be SF_F32 or SF_BF16");
+    SF_ARG(storage == SF_F32 || storage == SF_BF16 || storage == SF_F16, "storage must be SF_F32, SF_BF16 or SF_F16");
     static std::mutex mu;
     static std::map<std::tuple<int, int64_t, int, int, int, int>, sf_opts> cache;
     sf_opts b0 = {};

@@ -74,9 +74,9 @@ sf_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStr
 sf_status reduce_sum_f64(const double *in, int64_t count, double *out, cudaStream_t s);
 
 // ---------------------------------------------------------------- profiling
-// Kernel variants are tagged mode * 2 + (storage == BF16): forward 0/1,
-// moments 2/3, Clenshaw 4/5.
-constexpr int kProfTags = 8;
+// Kernel variants are tagged mode * 3 + storage (SF_F32 0, SF_BF16 1,
+// SF_F16 2) with mode 0 forward, 1 moments, 2 Clenshaw.
+constexpr int kProfTags = 9;
 bool profiling_on();
 void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag);
 bool profile_events(cudaEvent_t *a, cudaEvent_t *b);

@@ -32,6 +32,7 @@ struct VT<float> {
     }
     // value as it is stored (identity for fp32)
     __device__ __forceinline__ static float rt(float x) { return x; }
+    __device__ __forceinline__ static float cvt(float x) { return x; }
     using raw_t = float4;
     __device__ __forceinline__ static raw_t ld_raw(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
     __device__ __forceinline__ static raw_t zero_raw() { return make_float4(0.f, 0.f, 0.f, 0.f); }
@@ -82,6 +83,7 @@ struct VT<__nv_bfloat16> {
         *reinterpret_cast<uint4 *>(p) = v;
     }
     __device__ __forceinline__ static float rt(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+    __device__ __forceinline__ static __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
     using raw_t = uint4;
     __device__ __forceinline__ static raw_t ld_raw(const __nv_bfloat16 *p) {
         return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -118,6 +120,87 @@ struct VT<__nv_bfloat16> {
         fma_pair(acc[6], acc[7], w, x.w);
     }
 };
+
+template <>
+struct VT<__half> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void st(__half *p, const float (&x)[8]) {
+        uint4 v;
+        __half2 *h = reinterpret_cast<__half2 *>(&v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(x[2 * k], x[2 * k + 1]);
+        *reinterpret_cast<uint4 *>(p) = v;
+    }
+    __device__ __forceinline__ static float rt(float x) { return __half2float(__float2half_rn(x)); }
+    __device__ __forceinline__ static __half cvt(float x) { return __float2half_rn(x); }
+    using raw_t = uint4;
+    __device__ __forceinline__ static raw_t ld_raw(const __half *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+    __device__ __forceinline__ static raw_t ld_raw_stream(const __half *p) {
+        return __ldcs(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static raw_t zero_raw() { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ static float2 pair(uint32_t h) {
+        return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+    }
+    __device__ __forceinline__ static void to_float(raw_t x, float (&f)[8]) {
+        const uint32_t h[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 v = pair(h[k]);
+            f[2 * k] = v.x;
+            f[2 * k + 1] = v.y;
+        }
+    }
+    __device__ __forceinline__ static void add_raw(float (&acc)[8], raw_t x) {
+        const uint32_t h[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 v = pair(h[k]);
+            acc[2 * k] += v.x;
+            acc[2 * k + 1] += v.y;
+        }
+    }
+    __device__ __forceinline__ static void fma_raw(float (&acc)[8], float w, raw_t x) {
+        const uint32_t h[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 v = pair(h[k]);
+            acc[2 * k] = fmaf(w, v.x, acc[2 * k]);
+            acc[2 * k + 1] = fmaf(w, v.y, acc[2 * k + 1]);
+        }
+    }
+};
+
+// Power-of-two scale that brings the largest magnitude of a block into
+// (1/2, 1] (FP16 blocks; 1 when maxbits is null or the block is zero). Being
+// a power of two, scaling and unscaling are exact.
+__device__ __forceinline__ float block_scale(const uint32_t *maxbits) {
+    if (!maxbits) return 1.0f;
+    const float mx = __uint_as_float(*maxbits);
+    if (!(mx > 0.0f) || isinf(mx)) return 1.0f;
+    int e;
+    frexpf(mx, &e);  // mx = f * 2^e, f in [1/2, 1)
+    return ldexpf(1.0f, -e);
+}
+
+// *maxbits = bits of max |R| over the slab's columns [c0, c0 + w)
+static __global__ void absmax_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0, int32_t w,
+                              uint32_t *maxbits) {
+    float mx = 0.0f;
+    const int64_t total = (int64_t)n * w;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / w;
+        const int64_t src = i * n_sig + c0 + (idx - i * w);
+        const float x = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
+                                             : static_cast<const float *>(R)[src];
+        mx = fmaxf(mx, fabsf(x));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(mx));
+}
 
 // ------------------------------------------------------------ parameters
 enum StepMode { MODE_FWD = 0, MODE_MOM = 1, MODE_CLEN = 2 };
@@ -473,9 +556,11 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
 template <typename TS>
 __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0, int32_t w,
                             int32_t ld, TS *T0, float *Y, int64_t ystride, int32_t n_cut, const float *coef,
-                            int32_t coef_ld, int32_t jcoef, const int32_t *gid, TS *bstart, double *part) {
+                            int32_t coef_ld, int32_t jcoef, const int32_t *gid, TS *bstart, double *part,
+                            const uint32_t *maxbits = nullptr) {
     __shared__ double red[256];
     const int64_t total = (int64_t)n * ld;
+    const float scale = block_scale(maxbits);
     double acc = 0.0;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -486,11 +571,9 @@ __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig
             const int64_t src = i * n_sig + c0 + c;
             x = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
                                      : static_cast<const float *>(R)[src];
+            x *= scale;
         }
-        TS xs;
-        if constexpr (sizeof(TS) == 4) xs = x;
-        else xs = __float2bfloat16_rn(x);
-        T0[idx] = xs;
+        T0[idx] = VT<TS>::cvt(x);
         const float xr = VT<TS>::rt(x);
         acc += (double)xr * (double)xr;
         const int g = gid ? gid[i] : 0;
@@ -502,8 +585,7 @@ __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig
         }
         if (bstart) {
             const float a = coef[(int64_t)g * coef_ld + jcoef];
-            if constexpr (sizeof(TS) == 4) bstart[idx] = a * xr;
-            else bstart[idx] = __float2bfloat16_rn(a * xr);
+            bstart[idx] = VT<TS>::cvt(a * xr);
         }
     }
     if (part) {
@@ -519,15 +601,16 @@ __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig
 
 // Y_out[c][i][c0 + col] = Yslab[c][i][col] for col < w.
 static __global__ void unpack_kernel(const float *Yslab, int32_t n, int32_t ld, int32_t w, int32_t n_cut,
-                              float *Y, int32_t n_sig, int32_t c0) {
+                              float *Y, int32_t n_sig, int32_t c0, const uint32_t *maxbits = nullptr) {
     const int64_t total = (int64_t)n_cut * n * w;
+    const float inv = 1.0f / block_scale(maxbits);  // exact: a power of two
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t cc = idx / ((int64_t)n * w);
         const int64_t rem = idx - cc * n * w;
         const int64_t i = rem / w;
         const int32_t col = (int32_t)(rem - i * w);
-        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * n + i) * ld + col);
+        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * n + i) * ld + col) * inv;
     }
 }
 
@@ -568,7 +651,7 @@ static __global__ void pair_sum_kernel(const double *part, int32_t count, int32_
 
 // ------------------------------------------------------------ host side
 struct SweepShape {
-    int storage;      // SF_F32 / SF_BF16
+    int storage;      // SF_F32 / SF_BF16 / SF_F16
     int lpr;          // lanes per row-chunk
     int ld;           // slab columns (= lpr * vec)
     int block;        // threads per block

@@ -234,6 +234,25 @@ def test_filter_bf16_storage_error(sf, oracle_mod):
         assert err <= 2.0 ** -8 * math.sqrt(p), (algo, err)
 
 
+@pytest.mark.parametrize("algo", ["forward", "clenshaw"])
+def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo):
+    """FP16 blocks (10-bit mantissa) with the per-slab power-of-two prescale:
+    error against the FP64 oracle below 2^-11 * p (one FP16 rounding per
+    order, growing at most linearly through the recurrence); inputs far
+    outside the FP16 range give the same relative error."""
+    gr, g, go, lam, R, lh = _setup_config1(sf, oracle_mod)
+    p = 50
+    a = oracle_mod.cheb_coeffs(lh, 0.5 * (lam[9] + lam[10]), p, True)
+    Yo = oracle_mod.cheb_filter(go, lh, a, R)[0]
+    A = sf.ALGO_FORWARD if algo == "forward" else sf.ALGO_CLENSHAW
+    for scale in (1.0, 1e5, 1e-6):
+        Rt = torch.as_tensor(R * scale, dtype=torch.float32, device="cuda")
+        Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.F16, algo=A))[0].cpu().numpy() / scale
+        assert np.all(np.isfinite(Y))
+        err = rel(Y, Yo)
+        assert err <= 2.0 ** -11 * p, (scale, err)
+
+
 # ------------------------------------------------------------------ moments / count
 def test_moments_and_counts_match_oracle(sf, oracle_mod):
     from paper_1509_08863_gb300 import synth
