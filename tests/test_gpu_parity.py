@@ -412,7 +412,9 @@ def test_argument_errors(sf):
     with pytest.raises(sf.SpecFiltError):
         sf.cheb_filter(g, -1.0, np.ones((1, 3)), R)
     with pytest.raises(sf.SpecFiltError):
-        sf.cheb_filter(g, 10.0, np.ones((1, 3)), R, sf.Opts(storage=sf.F16))
+        sf.cheb_moments(g, 10.0, R, 3, sf.Opts(storage=sf.F16))  # moments need FP32 or BF16 blocks
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter(g, 10.0, np.ones((1, 3)), R, sf.Opts(storage=7))
     with pytest.raises(sf.SpecFiltError):
         sf.cheb_filter(g, 10.0, np.array([[1.0, float("nan")]]), R)
     with pytest.raises(sf.SpecFiltError):
