@@ -61,6 +61,10 @@ def parse():
                          "STORAGE f32|bf16) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
+    ap.add_argument("--filter-algo", default="clenshaw", choices=["clenshaw", "forward"],
+                    help="algorithm of the filter sweep (the moment sweep is always the forward recurrence)")
+    ap.add_argument("--compare-storage", action="store_true",
+                    help="also time the step with FP16 blocks in the filter")
     return ap.parse_args()
 
 
@@ -282,9 +286,11 @@ def main():
     tuned = {sf.F32: sf.autotune(g0, eta, sf.F32, 1), storage: sf.autotune(g0, eta, storage, 1)}
     g0.free()
 
-    def opts_for(st):
+    filter_algo = sf.ALGO_FORWARD if args.filter_algo == "forward" else sf.ALGO_CLENSHAW
+
+    def opts_for(st, algo=sf.ALGO_CLENSHAW):
         t = tuned[st]
-        return sf.Opts(storage=st, algo=sf.ALGO_CLENSHAW, slab_cols=t.slab_cols, block_warps=t.block_warps,
+        return sf.Opts(storage=st, algo=algo, slab_cols=t.slab_cols, block_warps=t.block_warps,
                        blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct)
 
     def step(src, dst, Rt, st, collect=None):
@@ -299,7 +305,7 @@ def main():
         a = sf.cheb_coeffs(lh, lk, p, True)
         if st not in tuned:
             tuned[st] = sf.autotune(g, eta, st, 1)
-        Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st))[0]
+        Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st, filter_algo))[0]
         F = sf.features(Y, True, out=Y)
         if collect is not None:
             collect.update(lam_hat=lh, lam_k=lk, nnz=g.nnz, Y=Y)
@@ -368,6 +374,10 @@ def main():
         ms32, _ = timed(sf.F32, max(3, args.steps // 2), 1)
         fp32 = {"value": updates * world / (ms32 * 1e-3), "ms_per_step": ms32,
                 "speedup_of_storage": ms32 / ms}
+    f16 = None
+    if args.compare_storage and storage != sf.F16:
+        ms16, _ = timed(sf.F16, max(3, args.steps // 2), 1)
+        f16 = {"value": updates * world / (ms16 * 1e-3), "ms_per_step": ms16}
     # end to end from pinned host buffers, features copied back
     e2e = None
     if not args.no_e2e:
@@ -405,7 +415,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "N": n, "nnz_off": nnz, "R": eta, "p": p, "k": k,
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
-                   "filter_storage": wl["storage"], "moment_storage": "f32", "algo": "clenshaw",
+                   "filter_storage": wl["storage"], "moment_storage": "f32", "filter_algo": args.filter_algo,
                    "tiles": {("f32" if k == sf.F32 else "bf16"): {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
                                                                   "carveout_pct": v.carveout_pct}
                              for k, v in tuned.items()},
@@ -417,6 +427,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "fp32_storage": fp32,
+        "fp16_storage": f16,
         "lam_hat": info["lam_hat"],
         "lam_k_estimate": info["lam_k"],
     }
@@ -461,6 +472,17 @@ def cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev):
             "rel_fro_all_rows": float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),
             "rel_fro_50k_rows": float(np.linalg.norm(Y[rows] - Yo[rows]) / np.linalg.norm(Yo[rows])),
         }
+    # moments in BF16 blocks vs FP32 blocks: effect on the counts and on the dichotomy
+    mu32 = sf.cheb_moments(gg, lh, Rt, p, sf.Opts(storage=sf.F32))
+    mu16 = sf.cheb_moments(gg, lh, Rt, p, sf.Opts(storage=sf.BF16))
+    cuts = np.array([0.5, 0.8, 1.0, 1.25, 2.0]) * lk
+    acc["moments"] = {
+        "cutoffs_over_lam_k": [0.5, 0.8, 1.0, 1.25, 2.0],
+        "counts_f32_blocks": sf.eigencount_from(mu32, p, lh, cuts).tolist(),
+        "counts_bf16_blocks": sf.eigencount_from(mu16, p, lh, cuts).tolist(),
+        "lam_k_f32_blocks": sf.dichotomy(mu32, p, lh, wl["k"] - 0.5),
+        "lam_k_bf16_blocks": sf.dichotomy(mu16, p, lh, wl["k"] - 0.5),
+    }
     gg.free()
     acc["reference"] = "FP64 oracle, column 0, same lam_hat and coefficients"
     return cpu, acc

@@ -31,6 +31,7 @@ __all__ = [
     "cheb_moments_noalloc",
     "count_from_moments",
     "eigencount",
+    "eigencount_from",
     "dichotomy",
     "features",
     "cheb_filter_backward",
@@ -349,6 +350,11 @@ def eigencount(g: Graph, lam_max: float, R, p: int, cutoffs, jackson: bool = Tru
                                cut.shape[0], int(bool(jackson)), counts.ctypes.data_as(_dp), mu.ctypes.data_as(_dp),
                                op, _stream()), "sf_eigencount")
     return counts, mu
+
+
+def eigencount_from(mu, p: int, lam_max: float, cutoffs, jackson: bool = True) -> np.ndarray:
+    """Counts of §3.2 at the given cutoffs from already computed moments (host only)."""
+    return count_from_moments(mu, p, cheb_coeffs(lam_max, cutoffs, p, jackson))
 
 
 def dichotomy(mu, p: int, lam_max: float, k: float, jackson: bool = True, max_iter: int = 40,
