@@ -61,8 +61,9 @@ def parse():
                          "STORAGE f32|bf16) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
-    ap.add_argument("--filter-algo", default="clenshaw", choices=["clenshaw", "forward"],
-                    help="algorithm of the filter sweep (the moment sweep is always the forward recurrence)")
+    ap.add_argument("--filter-algo", default="auto", choices=["auto", "clenshaw", "forward"],
+                    help="algorithm of the filter sweep (auto: Clenshaw for FP32 blocks, forward otherwise); "
+                         "the moment sweep is always the forward recurrence")
     ap.add_argument("--compare-storage", action="store_true",
                     help="also time the step with FP16 blocks in the filter")
     return ap.parse_args()
@@ -283,10 +284,10 @@ def main():
 
     # tile shapes from the autotuner (untimed; cached per graph size)
     g0 = sf.csr_build(n, src_d, dst_d, None)
-    tuned = {sf.F32: sf.autotune(g0, eta, sf.F32, 1), storage: sf.autotune(g0, eta, storage, 1)}
+    tuned = {storage: sf.autotune(g0, eta, storage, 1)}
     g0.free()
 
-    filter_algo = sf.ALGO_FORWARD if args.filter_algo == "forward" else sf.ALGO_CLENSHAW
+    filter_algo = {"auto": sf.ALGO_AUTO, "forward": sf.ALGO_FORWARD, "clenshaw": sf.ALGO_CLENSHAW}[args.filter_algo]
 
     def opts_for(st, algo=sf.ALGO_CLENSHAW):
         t = tuned[st]
@@ -294,9 +295,14 @@ def main():
                        blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct)
 
     def step(src, dst, Rt, st, collect=None):
+        """One pass of the path; `st` is the block storage of both sweeps (FP16
+        applies to the filter, whose moments then use BF16 blocks)."""
         g = sf.csr_build(n, src, dst, None)
         _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
-        mu = sf.cheb_moments(g, lh, Rt, p, opts_for(sf.F32))
+        mst = sf.BF16 if st == sf.F16 else st
+        if mst not in tuned:
+            tuned[mst] = sf.autotune(g, eta, mst, 1)
+        mu = sf.cheb_moments(g, lh, Rt, p, opts_for(mst))
         if dist:
             t = torch.as_tensor(mu, device=dev)
             dist.all_reduce(t)
@@ -368,7 +374,7 @@ def main():
     sf.device_check()
     value = updates * world / (ms * 1e-3)
 
-    # the same step with FP32 blocks in the filter (moment sweep is FP32 in both)
+    # the same run with FP32 blocks in both sweeps
     fp32 = None
     if storage != sf.F32 and not args.no_fp32:
         ms32, _ = timed(sf.F32, max(3, args.steps // 2), 1)
@@ -377,7 +383,8 @@ def main():
     f16 = None
     if args.compare_storage and storage != sf.F16:
         ms16, _ = timed(sf.F16, max(3, args.steps // 2), 1)
-        f16 = {"value": updates * world / (ms16 * 1e-3), "ms_per_step": ms16}
+        f16 = {"value": updates * world / (ms16 * 1e-3), "ms_per_step": ms16,
+               "note": "FP16 blocks in the filter, BF16 blocks in the moment sweep"}
     # end to end from pinned host buffers, features copied back
     e2e = None
     if not args.no_e2e:
@@ -415,8 +422,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "N": n, "nnz_off": nnz, "R": eta, "p": p, "k": k,
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
-                   "filter_storage": wl["storage"], "moment_storage": "f32", "filter_algo": args.filter_algo,
-                   "tiles": {("f32" if k == sf.F32 else "bf16"): {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
+                   "block_storage": wl["storage"], "filter_algo": args.filter_algo,
+                   "tiles": {("f32", "bf16", "f16")[k]: {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
                                                                   "carveout_pct": v.carveout_pct}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
@@ -464,9 +471,9 @@ def cpu_baseline_and_accuracy(gr, R, info, wl, sf, dev):
     Rt = torch.as_tensor(R, dtype=torch.float32, device=dev)
     acc = {}
     rows = np.random.default_rng(5).choice(n, size=min(50_000, n), replace=False)
-    for name, st, algo in (("f32", sf.F32, sf.ALGO_CLENSHAW), ("bf16", sf.BF16, sf.ALGO_CLENSHAW),
-                           ("f16", sf.F16, sf.ALGO_CLENSHAW), ("f32_forward", sf.F32, sf.ALGO_FORWARD),
-                           ("bf16_forward", sf.BF16, sf.ALGO_FORWARD), ("f16_forward", sf.F16, sf.ALGO_FORWARD)):
+    for name, st, algo in (("f32", sf.F32, sf.ALGO_CLENSHAW), ("bf16", sf.BF16, sf.ALGO_FORWARD),
+                           ("f16", sf.F16, sf.ALGO_FORWARD), ("f32_forward", sf.F32, sf.ALGO_FORWARD),
+                           ("bf16_clenshaw", sf.BF16, sf.ALGO_CLENSHAW), ("f16_clenshaw", sf.F16, sf.ALGO_CLENSHAW)):
         Y = sf.cheb_filter(gg, lh, a, Rt, sf.Opts(storage=st, algo=algo))[0][:, 0].cpu().numpy()
         acc[name] = {
             "rel_fro_all_rows": float(np.linalg.norm(Y - Yo) / np.linalg.norm(Yo)),

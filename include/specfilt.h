@@ -61,7 +61,7 @@ enum { SF_F32 = 0, SF_BF16 = 1, SF_F16 = 2 };
 
 /* Filter algorithms. */
 enum {
-    SF_ALGO_AUTO = 0,     /* forward recurrence for several cutoffs, Clenshaw for one */
+    SF_ALGO_AUTO = 0,     /* Clenshaw for one cutoff with FP32 blocks, else the forward recurrence */
     SF_ALGO_FORWARD = 1,  /* T_j blocks forward, Y_c += a_cj T_j for every cutoff c */
     SF_ALGO_CLENSHAW = 2  /* backward Clenshaw sum, one cutoff at a time */
 };

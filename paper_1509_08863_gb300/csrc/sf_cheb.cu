@@ -436,7 +436,10 @@ SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double 
     if ((st = resolve_opts(opts, g->n, n_sig, &o))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     int algo = o.algo;
-    if (algo == SF_ALGO_AUTO) algo = (n_cut == 1) ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
+    // One FP32 cutoff: Clenshaw (fewest blocks per order). Reduced-precision
+    // blocks: the forward recurrence, whose FP32 accumulator halves the error
+    // of storing the Clenshaw partial sums b_j themselves in 16 bits.
+    if (algo == SF_ALGO_AUTO) algo = (n_cut == 1 && o.storage == SF_F32) ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
     SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
     GraphView G;
     if ((st = view_of(g, s, &G))) return st;
@@ -513,7 +516,7 @@ SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max
     sf_opts o;
     sf_status st = resolve_opts(opts, b->n, n_sig, &o);
     if (st) return st;
-    int algo = o.algo == SF_ALGO_AUTO ? SF_ALGO_CLENSHAW : o.algo;
+    int algo = o.algo == SF_ALGO_AUTO ? (o.storage == SF_F32 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD) : o.algo;
     SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
     {
         std::lock_guard<std::mutex> lk(b->sell_mu);
