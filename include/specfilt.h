@@ -213,6 +213,9 @@ SF_API sf_status sf_cheb_filter(const sf_graph *g, double lam_max, const double 
  * polynomials). Per-row partial sums in FP32, everything across rows in
  * FP64 with a fixed reduction order (deterministic).
  *   moments host double[2p + 1]. Synchronises `stream`.
+ * SF_ERR_NUMERIC when a moment is not finite or ||T_j R||^2 exceeds
+ * 16 ||R||^2 (lam_max below the largest Laplacian eigenvalue: the recurrence
+ * diverges for eigenvalues beyond it).
  */
 SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *R, int32_t r_dtype,
                                  int32_t n_sig, int32_t p, double *moments, const sf_opts *opts,
@@ -252,6 +255,22 @@ SF_API sf_status sf_dichotomy(const double *moments, int32_t p, double lam_max, 
  */
 SF_API sf_status sf_features(const float *Y, int32_t n, int32_t n_sig, int32_t normalize, float *F,
                              void *stream);
+
+/*
+ * Feature normalisation when the signal columns are spread over several
+ * devices (each holds a column shard of Y): every device computes its rows'
+ * partial sums of squares, the caller adds them across devices (one
+ * all-reduce of N doubles), then every device scales its shard by the total.
+ *   sf_row_sumsq:       sumsq[i] = sum_c Y[i][c]^2 (device double[N]; FP32
+ *                       per-lane partials combined in FP64)
+ *   sf_features_scaled: F[i][c] = Y[i][c] / sqrt(sumsq[i]), zero rows stay
+ *                       zero (F may alias Y)
+ * With the full Y on one device the two calls equal sf_features(..., 1, ...).
+ * Asynchronous.
+ */
+SF_API sf_status sf_row_sumsq(const float *Y, int32_t n, int32_t n_sig, double *sumsq, void *stream);
+SF_API sf_status sf_features_scaled(const float *Y, int32_t n, int32_t n_sig, const double *sumsq, float *F,
+                                    void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Adjoint (reverse mode) of the filter                                    */

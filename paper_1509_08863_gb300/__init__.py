@@ -34,6 +34,8 @@ __all__ = [
     "eigencount_from",
     "dichotomy",
     "features",
+    "row_sumsq",
+    "features_scaled",
     "cheb_filter_backward",
     "batch_build",
     "cheb_filter_batched",
@@ -132,6 +134,8 @@ def lib():
                                  _vp]),
         "sf_dichotomy": (_i32, [_dp, _i32, _f64, _f64, _i32, _i32, _f64, _dp]),
         "sf_features": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp]),
+        "sf_row_sumsq": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+        "sf_features_scaled": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),
         "sf_cheb_filter_backward": (_i32, [_vp, _f64, _dp, _i32, _vp, _i32, _vp, _vp, _dp, _vp,
                                            C.POINTER(_Opts), _vp]),
         "sf_batch_build": (_i32, [C.POINTER(_vp), _i32, _vp, C.POINTER(_vp)]),
@@ -373,6 +377,29 @@ def features(Y, normalize: bool = True, out=None):
         out = torch.empty_like(Y)
     _check(lib().sf_features(_dev_ptr(Y, torch.float32, "Y"), n, n_sig, int(bool(normalize)),
                              _dev_ptr(out, torch.float32, "F"), _stream()), "sf_features")
+    return out
+
+
+def row_sumsq(Y, out=None):
+    """Per-row sums of squares (float64 tensor) of a float32 block."""
+    torch = _torch()
+    n, n_sig = Y.shape
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=Y.device)
+    _check(lib().sf_row_sumsq(_dev_ptr(Y, torch.float32, "Y"), n, n_sig, _dev_ptr(out, torch.float64, "sumsq"),
+                              _stream()), "sf_row_sumsq")
+    return out
+
+
+def features_scaled(Y, sumsq, out=None):
+    """Rows of Y divided by sqrt(sumsq) (sumsq summed over all column shards)."""
+    torch = _torch()
+    n, n_sig = Y.shape
+    if out is None:
+        out = torch.empty_like(Y)
+    _check(lib().sf_features_scaled(_dev_ptr(Y, torch.float32, "Y"), n, n_sig,
+                                    _dev_ptr(sumsq, torch.float64, "sumsq"), _dev_ptr(out, torch.float32, "F"),
+                                    _stream()), "sf_features_scaled")
     return out
 
 

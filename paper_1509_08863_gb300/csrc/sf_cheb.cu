@@ -475,6 +475,19 @@ SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *
     SF_CHECK_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 2 * (p + 1), cudaMemcpyDeviceToHost, s));
     SF_CHECK_CUDA(cudaStreamSynchronize(s));
     if ((st = sf_device_check(stream))) return st;
+    // |T_j(x)| <= 1 on [-1, 1], so ||T_j R||^2 <= ||R||^2 when lam_max bounds the
+    // spectrum; eigencomponents beyond it grow like cosh(j acosh x)
+    for (int j = 0; j <= p; ++j) {
+        if (!isfinite(hd[2 * j]) || !isfinite(hd[2 * j + 1])) {
+            set_error("non-finite moment at order %d (non-finite input or lam_max below the spectrum)", j);
+            return SF_ERR_NUMERIC;
+        }
+        if (hd[2 * j] > 16.0 * hd[0] + 1e-300) {
+            set_error("||T_%d R||^2 = %g exceeds 16 ||R||^2 = %g: lam_max %g is below the Laplacian's spectrum", j,
+                      hd[2 * j], 16.0 * hd[0], lam_max);
+            return SF_ERR_NUMERIC;
+        }
+    }
     moments_from_dots(hd.data(), p, moments);
     return SF_OK;
 }

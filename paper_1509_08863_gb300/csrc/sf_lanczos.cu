@@ -125,11 +125,63 @@ __global__ void __launch_bounds__(256) features_kernel(const float *Y, int32_t n
     }
 }
 
+// Row sums of squares (FP64 per row from per-lane FP32 partials), one warp per row.
+__global__ void __launch_bounds__(256) row_sumsq_kernel(const float *Y, int32_t n, int32_t n_sig, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp0; i < n; i += nw) {
+        const float *y = Y + i * n_sig;
+        float part = 0.f;
+        for (int c = lane; c < n_sig; c += 32) part = fmaf(y[c], y[c], part);
+        double ss = (double)part;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+        if (lane == 0) out[i] = ss;
+    }
+}
+
+// F = Y / sqrt(sumsq) row by row (rows with sumsq == 0 become zero).
+__global__ void __launch_bounds__(256) row_scale_kernel(const float *Y, int32_t n, int32_t n_sig, const double *sumsq,
+                                                        float *F) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp0; i < n; i += nw) {
+        const double ss = sumsq[i];
+        const float inv = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.0f;
+        for (int c = lane; c < n_sig; c += 32) F[i * n_sig + c] = Y[i * n_sig + c] * inv;
+    }
+}
+
 }  // namespace sf
 
 using namespace sf;
 
 extern "C" {
+
+SF_API sf_status sf_row_sumsq(const float *Y, int32_t n, int32_t n_sig, double *sumsq, void *stream) {
+    SF_ARG(Y && sumsq, "Y/sumsq is NULL");
+    SF_ARG(n >= 0 && n_sig >= 1, "need n >= 0 and n_sig >= 1");
+    if (n == 0) return SF_OK;
+    int64_t grid = ((int64_t)n * 32 + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (grid > cap) grid = cap;
+    row_sumsq_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(Y, n, n_sig, sumsq);
+    return check_launch("row_sumsq_kernel");
+}
+
+SF_API sf_status sf_features_scaled(const float *Y, int32_t n, int32_t n_sig, const double *sumsq, float *F,
+                                    void *stream) {
+    SF_ARG(Y && sumsq && F, "Y/sumsq/F is NULL");
+    SF_ARG(n >= 0 && n_sig >= 1, "need n >= 0 and n_sig >= 1");
+    if (n == 0) return SF_OK;
+    int64_t grid = ((int64_t)n * 32 + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (grid > cap) grid = cap;
+    row_scale_kernel<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(Y, n, n_sig, sumsq, F);
+    return check_launch("row_scale_kernel");
+}
 
 SF_API sf_status sf_lambda_max_estimate(const sf_graph *g, int32_t iters, const double *v0, uint64_t seed,
                                         void *stream, double *theta_max, double *lam_hat) {

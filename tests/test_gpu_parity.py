@@ -421,6 +421,32 @@ def test_argument_errors(sf):
         sf.cheb_filter(g, 10.0, np.ones((1, 3)), R, sf.Opts(slab_cols=12))
 
 
+def test_fault_reports_without_fault(sf, oracle_mod):
+    """Host-visible failures: lam_max below the spectrum is caught by the
+    moment sweep's growth check, NaN signals by its finiteness check, and a
+    request larger than the device memory returns SF_ERR_OOM."""
+    gr = config1_graph()
+    g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst))
+    _, lh = sf.lambda_max_estimate(g, 60, None, seed=1)
+    R = torch.randn(gr.n, 16, device="cuda")
+    with pytest.raises(sf.SpecFiltError) as e:
+        sf.cheb_moments(g, 0.5 * lh, R, 60)
+    assert e.value.status == 5
+    Rn = R.clone()
+    Rn[3, 2] = float("nan")
+    with pytest.raises(sf.SpecFiltError) as e:
+        sf.cheb_moments(g, lh, Rn, 10)
+    assert e.value.status == 5
+    sf.cheb_moments(g, lh, R, 10)  # the library stays usable
+    n = 100_000
+    big = sf.csr_build(n, *cuda_edges(np.arange(n - 1), np.arange(1, n)))
+    Rb = torch.randn(n, 64, device="cuda")
+    with pytest.raises(sf.SpecFiltError) as e:  # (p + 1) stored blocks of 25.6 MB: ~2.6 TB
+        sf.cheb_filter_backward(big, 4.0, np.full(100_001, 1e-3), Rb, Rb, False, sf.Opts(ckpt_every=1))
+    assert e.value.status == 3
+    sf.cheb_moments(g, lh, R, 10)
+
+
 def test_autotune_and_profile(sf, oracle_mod):
     gr = config1_graph()
     g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst))
