@@ -257,11 +257,12 @@ def main():
 
     import paper_1509_08863_gb300 as sf
     from paper_1509_08863_gb300 import build as sfbuild
+    from paper_1509_08863_gb300 import sharded
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if "WORLD_SIZE" in os.environ:  # launched by torch.distributed.run (any world size)
         import torch.distributed as dist
 
         torch.cuda.set_device(local)
@@ -303,16 +304,17 @@ def main():
         if mst not in tuned:
             tuned[mst] = sf.autotune(g, eta, mst, 1)
         mu = sf.cheb_moments(g, lh, Rt, p, opts_for(mst))
-        if dist:
-            t = torch.as_tensor(mu, device=dev)
-            dist.all_reduce(t)
-            mu = t.cpu().numpy()
+        if dist:  # columns are sharded over ranks: moments add up
+            mu = sharded.combine_moments(mu, device=dev)
         lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
         a = sf.cheb_coeffs(lh, lk, p, True)
         if st not in tuned:
             tuned[st] = sf.autotune(g, eta, st, 1)
         Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st, filter_algo))[0]
-        F = sf.features(Y, True, out=Y)
+        if dist:  # row norms run over every rank's columns
+            F = sharded.normalize_rows_sharded(Y, sf.row_sumsq, lambda y, tot: sf.features_scaled(y, tot, out=y))
+        else:
+            F = sf.features(Y, True, out=Y)
         if collect is not None:
             collect.update(lam_hat=lh, lam_k=lk, nnz=g.nnz, Y=Y)
         g.free()
@@ -427,7 +429,9 @@ def main():
                                                                   "carveout_pct": v.carveout_pct}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"column-shard x{world}" if world > 1 else "single GPU"},
+                   "parallelism": (f"column shards x{world}: each rank filters its own {wl['R']} signals of one "
+                                   f"{wl['R'] * world}-signal block; moments and row norms all-reduced")
+                   if world > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roof,
         "roofline_by_variant": by_variant,
