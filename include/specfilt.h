@@ -89,7 +89,10 @@ enum {
  *                   the sweep kernel, in percent (0 = driver default). The L1
  *                   share holds the gathers in flight, so large values slow
  *                   the sweep down.
- *   reserved        must be 0.
+ *   l2_window       1: mark each order's gathered block as persisting in L2
+ *                   (access-policy window, up to the device's persisting
+ *                   carve-out, which the first such call raises to its maximum
+ *                   for this process); 0: no window.
  */
 typedef struct sf_opts {
     int32_t storage;
@@ -100,7 +103,7 @@ typedef struct sf_opts {
     int32_t ckpt_every;
     int64_t mem_cap_mb;
     int32_t carveout_pct;
-    int32_t reserved;
+    int32_t l2_window;
 } sf_opts;
 
 typedef struct sf_graph sf_graph; /* device-resident CSR of W, owned by the library */

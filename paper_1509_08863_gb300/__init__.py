@@ -78,7 +78,7 @@ class _Opts(C.Structure):
         ("ckpt_every", C.c_int32),
         ("mem_cap_mb", C.c_int64),
         ("carveout_pct", C.c_int32),
-        ("reserved", C.c_int32),
+        ("l2_window", C.c_int32),
     ]
 
 
@@ -94,10 +94,11 @@ class Opts:
     ckpt_every: int = 0
     mem_cap_mb: int = 0
     carveout_pct: int = 0
+    l2_window: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.storage, self.algo, self.slab_cols, self.block_warps, self.blocks_per_sm,
-                      self.ckpt_every, self.mem_cap_mb, self.carveout_pct, 0)
+                      self.ckpt_every, self.mem_cap_mb, self.carveout_pct, self.l2_window)
 
 
 _vp = C.c_void_p
@@ -478,7 +479,7 @@ def autotune(g: Graph, n_sig: int, storage: int = F32, n_cut: int = 1, base: Opt
     _check(lib().sf_autotune(g.handle, int(n_sig), int(storage), int(n_cut), bp, _stream(), C.byref(best)),
            "sf_autotune")
     return Opts(best.storage, best.algo, best.slab_cols, best.block_warps, best.blocks_per_sm, best.ckpt_every,
-                best.mem_cap_mb, best.carveout_pct)
+                best.mem_cap_mb, best.carveout_pct, best.l2_window)
 
 
 def profile_begin():

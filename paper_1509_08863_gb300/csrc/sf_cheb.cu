@@ -114,13 +114,35 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     return SF_OK;
 }
 
+// Launches one sweep; with a window, the gathered block is marked persisting
+// in L2 for this launch only (the stream's own attributes are left alone).
 template <typename TS, int LPR, bool W>
 static void launch_mode(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
+    void (*fn)(const StepParams);
     switch (mode) {
-        case MODE_FWD: cheb_step_kernel<TS, LPR, MODE_FWD, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
-        case MODE_MOM: cheb_step_kernel<TS, LPR, MODE_MOM, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
-        default: cheb_step_kernel<TS, LPR, MODE_CLEN, W><<<sh.grid, sh.block, sh.smem, s>>>(P); break;
+        case MODE_FWD: fn = cheb_step_kernel<TS, LPR, MODE_FWD, W>; break;
+        case MODE_MOM: fn = cheb_step_kernel<TS, LPR, MODE_MOM, W>; break;
+        default: fn = cheb_step_kernel<TS, LPR, MODE_CLEN, W>; break;
     }
+    if (sh.l2_window_bytes == 0) {
+        fn<<<sh.grid, sh.block, sh.smem, s>>>(P);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sh.grid);
+    cfg.blockDim = dim3(sh.block);
+    cfg.dynamicSmemBytes = sh.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    at[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(P.X);
+    at[0].val.accessPolicyWindow.num_bytes = sh.l2_window_bytes;
+    at[0].val.accessPolicyWindow.hitRatio = sh.l2_hit_ratio;
+    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, fn, P);
 }
 
 template <typename TS, bool W>
@@ -208,6 +230,26 @@ static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r
     return SF_OK;
 }
 
+// Persisting-L2 window over the gathered block: the context's persisting
+// carve-out is raised once (a per-process limit, gone with the context) and
+// each launch marks its gathered block (up to the carve-out) as persisting.
+static sf_status setup_l2_window(SweepShape *sh, size_t block_bytes) {
+    static size_t carve[64] = {0};
+    const int d = current_device();
+    int max_persist = 0, max_window = 0;
+    SF_CHECK_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, d));
+    SF_CHECK_CUDA(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, d));
+    if (max_persist <= 0 || max_window <= 0) return SF_OK;
+    if (d < 64 && carve[d] == 0) {
+        SF_CHECK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist));
+        carve[d] = (size_t)max_persist;
+    }
+    const size_t win = block_bytes < (size_t)max_window ? block_bytes : (size_t)max_window;
+    sh->l2_window_bytes = win;
+    sh->l2_hit_ratio = win <= (size_t)max_persist ? 1.0f : (float)max_persist / (float)win;
+    return SF_OK;
+}
+
 static sf_status launch_pack(int storage, int grid, cudaStream_t s, const void *R, int r_dtype, int32_t n,
                              int32_t n_sig, int32_t c0, int32_t w, int32_t ld, void *T0, float *Y, int64_t ystride,
                              int32_t n_cut, const float *coef, int32_t coef_ld, int32_t jcoef, const int32_t *gid,
@@ -238,6 +280,9 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     int32_t *status = device_status();
     SF_ARG(status, "device status word unavailable");
     const int ld = sh.ld;
+    if (o.l2_window > 0) {
+        if ((st = setup_l2_window(&sh, (size_t)(G.n + 1) * ld * bytes_of(o.storage)))) return st;
+    }
     const int64_t n = G.n;
     const size_t eb = bytes_of(o.storage);
     Scratch sc(s);

@@ -658,6 +658,8 @@ struct SweepShape {
     int grid;         // blocks
     int smem;         // dynamic shared memory per block
     bool weighted;    // kernel reads weights
+    size_t l2_window_bytes = 0;  // persisting-L2 window over the gathered block (0: none)
+    float l2_hit_ratio = 0.f;
 };
 
 // Picks the slab width (columns) for n rows and n_sig signals.
