@@ -43,6 +43,11 @@ WORKLOADS = {
     "sbm100k": dict(n=100_000, k=20, deg=20.0, eps=0.1, R=64, p=100, storage="f32", graph_seed=1002, r_seed=2002,
                     sizes=(2000, 8000)),
     "sbm1k": dict(n=1000, k=10, deg=16.0, eps=0.05, R=14, p=50, storage="f32", graph_seed=1001, r_seed=2001),
+    # differentiable filter: 10-NN Gaussian-kernel graph of a 10-component mixture in d = 8
+    "knn200k": dict(n=200_000, k=10, dim=8, knn=10, sigma=1.0, R=64, p=80, storage="f32", graph_seed=1004,
+                    r_seed=2004, g_seed=3000),
+    # many graphs: 256 SBMs of uneven size, one per-graph cutoff each
+    "batch256": dict(n_graphs=256, R=32, p=120, storage="bf16", graph_seed=10000, r_seed=2005),
 }
 
 
@@ -252,6 +257,10 @@ def main():
         return run_reference(args, wl)
     if args.kernel_case:
         return run_kernel_case(args, wl)
+    if args.workload == "knn200k":
+        return run_knn_grad(args, wl)
+    if args.workload == "batch256":
+        return run_batch(args, wl)
 
     import torch
 
@@ -293,7 +302,7 @@ def main():
     def opts_for(st, algo=sf.ALGO_CLENSHAW):
         t = tuned[st]
         return sf.Opts(storage=st, algo=algo, slab_cols=t.slab_cols, block_warps=t.block_warps,
-                       blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct)
+                       blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window)
 
     def step(src, dst, Rt, st, collect=None):
         """One pass of the path; `st` is the block storage of both sweeps (FP16
@@ -426,7 +435,7 @@ def main():
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
                    "block_storage": wl["storage"], "filter_algo": args.filter_algo,
                    "tiles": {("f32", "bf16", "f16")[k]: {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
-                                                                  "carveout_pct": v.carveout_pct}
+                                                                  "carveout_pct": v.carveout_pct, "l2_window": v.l2_window}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": (f"column shards x{world}: each rank filters its own {wl['R']} signals of one "
@@ -449,6 +458,206 @@ def main():
         print(json.dumps(result))
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def _clock_timed(fn, steps, warmup, sf):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    sf.profile_begin()
+    l0 = sf.launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    launches = sf.launch_count() - l0
+    sf.profile_end()
+    variants = sf.profile_variants()
+    clocks = clk.stop()
+    sf.device_check()
+    return e0.elapsed_time(e1) / steps, launches, variants, clocks
+
+
+def _roof_variants(variants, workload):
+    hbm, kind = peaks()
+    out = {}
+    tot = sum(v[1] for v in variants.values()) or 1.0
+    for name, (n_l, ms, by) in variants.items():
+        gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "traffic": traffic_from_profile(workload, name), "kernel": f"cheb_step_kernel ({name})",
+                     "launches_timed": n_l, "avg_launch_ms": ms / max(n_l, 1), "share_of_sweep_time": ms / tot,
+                     "peak_source": f"{kind} hbm_gbs"}
+    dom = max(out.items(), key=lambda kv: kv[1]["share_of_sweep_time"])[0] if out else None
+    return (out[dom] if dom else None), out
+
+
+def run_knn_grad(args, wl):
+    """Forward filter + reverse mode (edge weights, coefficients) on the 10-NN
+    Gaussian-kernel graph; updates = 3 sweeps x (nnz + N) x R x p per step
+    (the filter, its recomputation inside the backward call, the adjoint)."""
+    import torch
+
+    import paper_1509_08863_gb300 as sf
+    from paper_1509_08863_gb300 import build as sfbuild
+    from paper_1509_08863_gb300 import synth
+
+    sfbuild.build()
+    dev = torch.device("cuda")
+    n, eta, p = wl["n"], wl["R"], wl["p"]
+    src, dst, w, labels, _ = synth.knn_mixture_edges(n, wl["k"], wl["dim"], wl["knn"], wl["sigma"], 3.0,
+                                                     wl["graph_seed"])
+    g = sf.csr_build(n, torch.as_tensor(src, device=dev), torch.as_tensor(dst, device=dev),
+                     torch.as_tensor(w, device=dev))
+    nnz = g.nnz
+    _, lh = sf.lambda_max_estimate(g, 60, None, seed=11)
+    R = torch.as_tensor(synth.gaussian_block(n, eta, wl["r_seed"]), dtype=torch.float32, device=dev)
+    G = torch.as_tensor(synth.standard_normal_block(n, eta, wl["g_seed"]), dtype=torch.float32, device=dev)
+    mu = sf.cheb_moments(g, lh, R, p)
+    lk = sf.dichotomy(mu, p, lh, wl["k"] - 0.5)
+    a = sf.cheb_coeffs(lh, lk, p, True)[0]
+    opts = sf.Opts()
+
+    def step():
+        sf.cheb_filter(g, lh, a[None, :], R, opts)
+        sf.cheb_filter_backward(g, lh, a, R, G, False, opts)
+
+    ms, launches, variants, clocks = _clock_timed(step, args.steps, args.warmup, sf)
+    updates = 3.0 * (nnz + n) * eta * p
+    roof, by_variant = _roof_variants(variants, args.workload)
+    # directional finite difference at full size: l(W + h D) - l(W - h D) vs <grad, D>
+    gv, ga, _ = sf.cheb_filter_backward(g, lh, a, R, G, False, opts)
+    val0 = g.csr()[2]
+    rp, ci = g.csr()[0].cpu().numpy(), g.csr()[1].cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    rng = np.random.default_rng(7)
+    und = rng.standard_normal(len(ci))
+    # symmetric direction: entries (u, v) and (v, u) move together
+    key_lo, key_hi = np.minimum(rows, ci), np.maximum(rows, ci)
+    order = np.lexsort((key_hi, key_lo))
+    d = np.empty(len(ci))
+    d[order] = np.repeat(und[order][::2], 2)
+    D = torch.as_tensor(d, dtype=torch.float32, device=dev)
+    h = 1e-3
+
+    def loss(vals):
+        g.set_values(vals.contiguous())
+        Y = sf.cheb_filter(g, lh, a[None, :], R, sf.Opts(algo=sf.ALGO_FORWARD))[0]
+        return float((Y.double() * G.double()).sum())
+
+    lp, lm = loss(val0 + h * D), loss(val0 - h * D)
+    g.set_values(val0.contiguous())
+    fd = (lp - lm) / (2 * h)
+    an = float((gv.double() * D.double()).sum()) / 2.0  # each undirected edge appears twice in D and gv
+    out = {
+        "metric": "filtered nnz*R*p updates/s", "value": updates / (ms * 1e-3), "unit": "updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "knn200k", "N": n, "nnz_off": nnz, "R": eta, "p": p, "k_nn": wl["knn"],
+                   "sigma": wl["sigma"], "step": "filter + backward (edge weights, coefficients)",
+                   "sweeps_per_step": 3},
+        "gpu_launches": launches, "roofline": roof, "roofline_by_variant": by_variant, "clocks": clocks,
+        "e2e": None,
+        "gradient_check": {"directional_fd": fd, "adjoint": an, "rel_diff": abs(fd - an) / max(abs(fd), 1e-300),
+                           "h": h},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def run_batch(args, wl):
+    """256 graphs of uneven size filtered with per-graph cutoffs: one sweep
+    launch per order for the whole batch, against one filter call per graph."""
+    import torch
+
+    import paper_1509_08863_gb300 as sf
+    from paper_1509_08863_gb300 import build as sfbuild
+    from paper_1509_08863_gb300 import synth
+
+    sfbuild.build()
+    dev = torch.device("cuda")
+    eta, p = wl["R"], wl["p"]
+    st = sf.BF16 if wl["storage"] == "bf16" else sf.F32
+    graphs, ks = synth.batched_sbm(wl["n_graphs"], wl["graph_seed"])
+    gs, lams, cuts = [], [], []
+    for gr, kk in zip(graphs, ks):
+        g = sf.csr_build(gr.n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+        _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
+        gs.append(g)
+        lams.append(lh)
+    b = sf.batch_build(gs)
+    n_tot, nnz_tot, ng, offs = b.info()
+    R = torch.as_tensor(synth.gaussian_block(n_tot, eta, wl["r_seed"]), dtype=torch.float32, device=dev)
+    # per-graph cutoff: the dichotomy for that graph's community count (setup, untimed)
+    coeffs = np.zeros((ng, p + 1))
+    for i in range(ng):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        mu = sf.cheb_moments(gs[i], lams[i], R[sl].contiguous(), p)
+        lk = sf.dichotomy(mu, p, lams[i], float(ks[i]) - 0.5)
+        cuts.append(lk)
+        coeffs[i] = sf.cheb_coeffs(lams[i], lk, p, True)[0]
+    tuned = sf.autotune(gs[int(np.argmax(np.diff(offs)))], eta, st, 1)
+    opts = sf.Opts(storage=st, slab_cols=tuned.slab_cols, block_warps=tuned.block_warps,
+                   carveout_pct=tuned.carveout_pct, l2_window=tuned.l2_window)
+    Y = torch.empty((n_tot, eta), dtype=torch.float32, device=dev)
+    Rs = [R[int(offs[i]):int(offs[i + 1])].contiguous() for i in range(ng)]
+    Ys = [torch.empty_like(x) for x in Rs]
+
+    def batched():
+        sf.cheb_filter_batched(b, np.array(lams), coeffs, R, opts, out=Y)
+
+    def sequential():
+        for i in range(ng):
+            sf.cheb_filter(gs[i], lams[i], coeffs[i][None, :], Rs[i], opts, out=Ys[i][None])
+
+    ms_b, launches_b, variants_b, clocks = _clock_timed(batched, args.steps, args.warmup, sf)
+    # the same call with device tables, captured once into a CUDA graph and replayed
+    tol_d = torch.as_tensor(2.0 / np.array(lams), dtype=torch.float64, device=dev)
+    coef_d = torch.as_tensor(coeffs, dtype=torch.float32, device=dev)
+    Yg = torch.empty_like(Y)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Yg, opts)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Yg, opts)
+    ms_g, launches_g, _, _ = _clock_timed(cg.replay, args.steps, 1, sf)
+    graph_same = bool(torch.equal(Yg, Y))
+    ms_s, launches_s, _, _ = _clock_timed(sequential, max(1, args.steps // 2), 1, sf)
+    nnz_sum = sum(g.nnz for g in gs)
+    updates = (nnz_sum + n_tot) * eta * p
+    roof, by_variant = _roof_variants(variants_b, args.workload)
+    # the two forms compute the same rows bit for bit
+    same = all(torch.equal(Y[int(offs[i]):int(offs[i + 1])], Ys[i]) for i in range(ng))
+    out = {
+        "metric": "filtered nnz*R*p updates/s", "value": updates / (ms_b * 1e-3), "unit": "updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch256", "graphs": ng, "N_total": n_tot, "nnz_off_total": nnz_sum, "R": eta,
+                   "p": p, "block_storage": wl["storage"], "tiles": {"slab_cols": tuned.slab_cols,
+                                                                     "block_warps": tuned.block_warps}},
+        "gpu_launches": launches_b, "roofline": roof, "roofline_by_variant": by_variant, "clocks": clocks,
+        "e2e": None,
+        "sequential": {"value": updates / (ms_s * 1e-3), "ms_per_step": ms_s, "gpu_launches": launches_s,
+                       "speedup_of_batching": ms_s / ms_b},
+        "batched_equals_sequential": bool(same),
+        "cuda_graph": {"value": updates / (ms_g * 1e-3), "ms_per_step": ms_g, "equals_eager": graph_same,
+                       "note": "one capture of the device-table batched call, replayed"},
+    }
+    print(json.dumps(out))
     return 0
 
 

@@ -365,13 +365,28 @@ SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double lam_max, cons
  */
 SF_API sf_status sf_device_check(void *stream);
 
+/*
+ * sf_cheb_filter_batched with its tables already on the device, for capture
+ * into a CUDA graph: the call copies nothing between host and device and
+ * never synchronises (work buffers are stream-ordered allocations, which a
+ * graph captures as allocation nodes).
+ *   two_over_lam  device double[n_graphs]: 2 / lam_max of each graph
+ *   coeffs        device float[n_graphs][p + 1]
+ * The batch's sweep layout must exist (a first sf_cheb_filter_batched call
+ * builds it; SF_ERR_ARG otherwise), and so must the L2 set-up when
+ * opts->l2_window is 1 (done by the first call with a window).
+ */
+SF_API sf_status sf_cheb_filter_batched_dev(const sf_batch *b, const double *two_over_lam, const float *coeffs,
+                                            int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                            const sf_opts *opts, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Tile autotuner and kernel timing                                        */
 /* ---------------------------------------------------------------------- */
 
 /*
- * Time candidate tile shapes (slab width, warps per block, blocks per SM) of
- * the sweep kernel on this graph for n_sig signals and the given storage
+ * Time candidate tile shapes (slab width, warps per block, shared carveout,
+ * L2 window) of the sweep kernel on this graph for n_sig signals and the given storage
  * type, a few orders each, and write the fastest into *best (other fields
  * copied from *base, which may be NULL). Candidates are ranked by the summed
  * duration of their sweep-kernel launches (the kernel timing hooks below,

@@ -39,6 +39,7 @@ __all__ = [
     "cheb_filter_backward",
     "batch_build",
     "cheb_filter_batched",
+    "cheb_filter_batched_dev",
     "autotune",
     "profile_begin",
     "profile_end",
@@ -143,6 +144,7 @@ def lib():
         "sf_batch_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i32), C.POINTER(_i32)]),
         "sf_batch_free": (None, [_vp]),
         "sf_cheb_filter_batched": (_i32, [_vp, _dp, _dp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
+        "sf_cheb_filter_batched_dev": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
         "sf_autotune": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_Opts), _vp, C.POINTER(_Opts)]),
         "sf_profile_begin": (_i32, []),
         "sf_device_check": (_i32, [_vp]),
@@ -470,6 +472,20 @@ def cheb_filter_batched(b: Batch, lam_max, coeffs, R, opts: Opts | None = None, 
     o, op = _opts_ptr(opts)
     _check(lib().sf_cheb_filter_batched(b.handle, lp, ap, a.shape[1] - 1, _dev_ptr(R, None, "R"), _rdtype(R), n_sig,
                                         _dev_ptr(out, torch.float32, "Y"), op, _stream()), "sf_cheb_filter_batched")
+    return out
+
+
+def cheb_filter_batched_dev(b: Batch, two_over_lam, coeffs, R, out, opts: Opts | None = None):
+    """Batched filter with device tables (float64 2/lam per graph, float32 [graphs, p+1] coefficients):
+    no host copies and no synchronisation, so it can be captured in a CUDA graph."""
+    torch = _torch()
+    n, n_sig = R.shape
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_filter_batched_dev(b.handle, _dev_ptr(two_over_lam, torch.float64, "two_over_lam"),
+                                            _dev_ptr(coeffs, torch.float32, "coeffs"), coeffs.shape[1] - 1,
+                                            _dev_ptr(R, None, "R"), _rdtype(R), n_sig,
+                                            _dev_ptr(out, torch.float32, "Y"), op, _stream()),
+           "sf_cheb_filter_batched_dev")
     return out
 
 

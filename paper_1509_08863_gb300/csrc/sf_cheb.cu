@@ -270,9 +270,12 @@ static sf_status launch_pack(int storage, int grid, cudaStream_t s, const void *
 // Runs the filter over all slabs. mode: MODE_FWD (n_cut accumulators),
 // MODE_CLEN (one cutoff) or MODE_MOM (moment sums into mom[(p+1)][2] on the
 // device, accumulated over slabs; mom0 gets <T0,T0>).
+// coef_dev / tol_dev: device copies of the coefficient table (float) and of the
+// per-graph 2 / lam (double); when given, nothing is copied from the host.
 static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, double two_over_lam, int mode,
                             const double *coeffs_host, int n_cut, int p, const void *R, int r_dtype, int n_sig,
-                            float *Y, double *mom, const sf_opts &o, cudaStream_t s) {
+                            float *Y, double *mom, const sf_opts &o, cudaStream_t s, const float *coef_dev = nullptr,
+                            const double *tol_dev = nullptr) {
     SweepShape sh;
     sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh,
                               o.carveout_pct);
@@ -300,12 +303,14 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     if (mode == MODE_CLEN && (st = sc.get((char **)&qbuf, (size_t)n * ld * eb))) return st;
     const int ncy = (mode == MODE_FWD) ? n_cut : (mode == MODE_CLEN ? 1 : 0);
     if (ncy && (st = sc.get(&yacc, (size_t)ncy * n * ld))) return st;
-    const int ncoef = (mode == MODE_MOM) ? 0 : G.n_graphs * n_cut * (p + 1);
+    const int ncoef = (mode == MODE_MOM || coef_dev) ? 0 : G.n_graphs * n_cut * (p + 1);
     if (ncoef && (st = sc.get(&coef, (size_t)ncoef))) return st;
+    if (coef_dev) coef = const_cast<float *>(coef_dev);
     if ((st = sc.get(&dtil, (size_t)n))) return st;
     if (G.gid) {
         if ((st = sc.get(&wscale, (size_t)n))) return st;
-        if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
+        if (tol_dev) tol = const_cast<double *>(tol_dev);
+        else if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
     }
     if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * sh.grid + 2))) return st;
     // FP16 blocks: each slab is scaled by a power of two so that its largest
@@ -323,7 +328,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         SF_CHECK_CUDA(cudaMemcpyAsync(coef, cf.data(), sizeof(float) * ncoef, cudaMemcpyHostToDevice, s));
         // cf must outlive the copy: pageable copies complete before returning
     }
-    if (G.gid) {
+    if (G.gid && !tol_dev) {
         SF_CHECK_CUDA(cudaMemcpyAsync(tol, two_over_lam_g, sizeof(double) * G.n_graphs, cudaMemcpyHostToDevice, s));
     }
     if (n > 0) {
@@ -588,6 +593,29 @@ SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max
                       n_sig, Y, nullptr, o, (cudaStream_t)stream);
 }
 
+SF_API sf_status sf_cheb_filter_batched_dev(const sf_batch *b, const double *two_over_lam, const float *coeffs,
+                                            int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                            const sf_opts *opts, void *stream) {
+    SF_ARG(b, "batch is NULL");
+    SF_ARG(two_over_lam && coeffs && R && Y, "null pointer");
+    SF_ARG(p >= 0 && n_sig >= 1, "need p >= 0 and n_sig >= 1");
+    SF_ARG(r_dtype == SF_F32 || r_dtype == SF_BF16, "R dtype must be SF_F32 or SF_BF16");
+    SF_ARG(b->device == current_device(), "batch lives on another device");
+    {
+        std::lock_guard<std::mutex> lk(b->sell_mu);
+        SF_ARG(b->sell.built, "the batch has no sweep layout yet: call sf_cheb_filter_batched once first");
+    }
+    sf_opts o;
+    sf_status st = resolve_opts(opts, b->n, n_sig, &o);
+    if (st) return st;
+    int algo = o.algo == SF_ALGO_AUTO ? (o.storage == SF_F32 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD) : o.algo;
+    SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
+    GraphView G{b->n,          b->nnz,         b->rowptr,   b->colidx, b->unit_weights ? nullptr : b->val,
+                b->strength,   b->row_graph,   b->n_graphs, &b->sell};
+    return run_sweeps(G, nullptr, 0.0, algo == SF_ALGO_FORWARD ? MODE_FWD : MODE_CLEN, nullptr, 1, p, R, r_dtype,
+                      n_sig, Y, nullptr, o, (cudaStream_t)stream, coeffs, two_over_lam);
+}
+
 // ------------------------------------------------------------ autotuner
 }  // extern "C"
 
@@ -651,13 +679,13 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
     const double lam = 2.0 * g->max_strength + 1.0;
     for (int w = full; w >= vec * 2; w /= 2) {
         for (int wi = 0; wi < 2; ++wi) {
-            for (int ci = 0; ci < 3; ++ci) {
-                sf_opts t = b0;
+            for (int ci = 0; ci < 6; ++ci) {
+                sf_opts t = b0;  // algorithm as the caller will run it (AUTO resolves per storage)
                 t.slab_cols = w;
                 t.block_warps = warps_opts[wi];
                 t.blocks_per_sm = 0;
-                t.carveout_pct = carve_opts[ci];
-                t.algo = n_cut == 1 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
+                t.carveout_pct = carve_opts[ci % 3];
+                t.l2_window = ci / 3;
                 st = sf_cheb_filter(g, lam, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t, stream);  // warm-up
                 if (st) continue;
                 sf_profile_begin();

@@ -404,6 +404,41 @@ def test_batched_matches_oracle_and_single_launches(sf, oracle_mod):
             assert torch.equal(Ys, Y[sl])  # same per-row arithmetic, bit for bit
 
 
+def test_batched_device_tables_under_cuda_graph(sf, oracle_mod):
+    from paper_1509_08863_gb300 import synth
+
+    graphs, _ = synth.batched_sbm(4, seed=91, n_lo=400, n_hi=1500, k_lo=2, k_hi=5)
+    gs = [sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst, gr.w)) for gr in graphs]
+    lams = [sf.lambda_max_estimate(g, 30, None, seed=1)[1] for g in gs]
+    b = sf.batch_build(gs)
+    n_tot = b.info()[0]
+    p = 20
+    coeffs = np.stack([sf.cheb_coeffs(lams[i], 0.1 * lams[i], p, True)[0] for i in range(4)])
+    R = torch.randn(n_tot, 16, device="cuda")
+    for st in (sf.F32, sf.BF16):
+        opts = sf.Opts(storage=st, slab_cols=16 if st == sf.F32 else 32)
+        Yref = sf.cheb_filter_batched(b, lams, coeffs, R, opts)
+        tol_d = torch.as_tensor(2.0 / np.array(lams), dtype=torch.float64, device="cuda")
+        coef_d = torch.as_tensor(coeffs, dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(Yref)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Y, opts)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, Yref)
+        Y.zero_()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Y, opts)
+        for _ in range(2):
+            Y.zero_()
+            graph.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(Y, Yref)
+
+
 # ------------------------------------------------------------------ misc
 def test_argument_errors(sf):
     gr = config1_graph()
