@@ -541,7 +541,8 @@ def run_knn_grad(args, wl):
     rp, ci = g.csr()[0].cpu().numpy(), g.csr()[1].cpu().numpy()
     rows = np.repeat(np.arange(n), np.diff(rp))
     rng = np.random.default_rng(7)
-    und = rng.standard_normal(len(ci))
+    # relative perturbation of each undirected edge weight (weights span many decades)
+    und = rng.standard_normal(len(ci)) * val0.cpu().numpy()
     # symmetric direction: entries (u, v) and (v, u) move together
     key_lo, key_hi = np.minimum(rows, ci), np.maximum(rows, ci)
     order = np.lexsort((key_hi, key_lo))

@@ -409,7 +409,7 @@ SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
 /*
  * Per-variant totals of the last sf_profile_end: tag = 3 * mode + storage,
  * with mode 0 forward, 1 moments, 2 Clenshaw and storage SF_F32 / SF_BF16 /
- * SF_F16.
+ * SF_F16; tag 9 is the adjoint kernel of sf_cheb_filter_backward.
  */
 SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes);
 

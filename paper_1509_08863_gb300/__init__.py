@@ -516,6 +516,7 @@ def device_check():
 
 PROFILE_TAGS = {3 * m + s: f"{mn}_{sn}" for m, mn in enumerate(("forward", "moments", "clenshaw"))
                 for s, sn in enumerate(("f32", "bf16", "f16"))}
+PROFILE_TAGS[9] = "adjoint_f32"
 
 
 def profile_variants():

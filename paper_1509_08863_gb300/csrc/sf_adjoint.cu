@@ -177,12 +177,26 @@ __global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t
     }
 }
 
+static sf_status adj_launch_raw(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s);
+
 template <int LPR>
 static void launch_adj(const AdjParams &P, int grid, int block, cudaStream_t s) {
     adj_step_kernel<LPR><<<grid, block, 0, s>>>(P);
 }
 
-static sf_status adj_launch(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s) {
+static sf_status adj_launch(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s, double bytes) {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    const bool prof = profiling_on() && profile_events(&ea, &eb);
+    if (prof) cudaEventRecord(ea, s);
+    sf_status st = adj_launch_raw(lpr, P, grid, block, s);
+    if (prof) {
+        cudaEventRecord(eb, s);
+        profile_record(ea, eb, bytes, kProfTagAdjoint);
+    }
+    return st;
+}
+
+static sf_status adj_launch_raw(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s) {
     switch (lpr) {
         case 2: launch_adj<2>(P, grid, block, s); break;
         case 4: launch_adj<4>(P, grid, block, s); break;
@@ -299,13 +313,16 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         P.ld = ld;
         P.n_cut = 0;
         P.status = device_status();
+        // compulsory bytes: CSR once, gathered block once, T_{j-2} read, T_j written
+        const double csr_b = (double)(n + 1) * 4 + (double)n * 4 + (double)g->nnz * (val ? 8 : 4);
+        const double blk_b = (double)n * w * 4;
         auto fwd_step = [&](const float *Xp, const float *Zp, float *outp, int j) {
             P.X = Xp;
             P.Z = Zp;
             P.out = outp;
             P.m = (j == 1) ? 1.0f : 2.0f;
             P.j = j;
-            return launch_step(sh, MODE_FWD, P, s, 0.0);
+            return launch_step(sh, MODE_FWD, P, s, csr_b + blk_b * (Zp ? 3 : 2));
         };
         for (int j = 1; j <= p; ++j) {
             float *outp = (k == 1) ? T_at(j) : work[j % 3];
@@ -367,7 +384,11 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
             A.m = (j == 0) ? 1.0f : 2.0f;
             A.alpha = (float)coeffs[j];
             A.csd = (j == 1) ? 1.0f : 2.0f;
-            if ((st = adj_launch(sh.lpr, A, sh.grid, sh.block, s))) return st;
+            // CSR once, Gb_{j+1} gathered, Gb_{j+2}, G, Gb_j out, T_j rows, T_{j-1} gathered,
+            // edge and diagonal accumulators read and written
+            const double adj_b = csr_b + blk_b * ((A.B1 ? 1 : 0) + (A.B2 ? 1 : 0) + 3 + (A.Tm1 ? 1 : 0)) +
+                                 (A.Tm1 ? 8.0 * ((double)g->nnz + n) : 0.0);
+            if ((st = adj_launch(sh.lpr, A, sh.grid, sh.block, s, adj_b))) return st;
             pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 1, ga + j);
             if ((st = check_launch("pair_sum_kernel"))) return st;
         }
