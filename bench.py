@@ -410,7 +410,7 @@ def main():
     def roof_of(name, n_l, ms_, by_):
         gbs = by_ / (ms_ * 1e-3) / 1e9 if ms_ > 0 else 0.0
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": traffic_from_profile(args.workload, name), "kernel": f"cheb_step_kernel ({name})",
+                "traffic": traffic_from_profile(args.workload, name), "kernel": (f"sddmm_kernel ({name})" if name.startswith("adjoint") else f"cheb_step_kernel ({name})"),
                 "launches_timed": n_l, "avg_launch_ms": ms_ / max(n_l, 1), "bytes_per_launch": by_ / max(n_l, 1),
                 "share_of_sweep_time": ms_ / k_ms if k_ms > 0 else None, "peak_source": f"{peak_kind} hbm_gbs"}
 
@@ -495,7 +495,7 @@ def _roof_variants(variants, workload):
     for name, (n_l, ms, by) in variants.items():
         gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
         out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                     "traffic": traffic_from_profile(workload, name), "kernel": f"cheb_step_kernel ({name})",
+                     "traffic": traffic_from_profile(workload, name), "kernel": (f"sddmm_kernel ({name})" if name.startswith("adjoint") else f"cheb_step_kernel ({name})"),
                      "launches_timed": n_l, "avg_launch_ms": ms / max(n_l, 1), "share_of_sweep_time": ms / tot,
                      "peak_source": f"{kind} hbm_gbs"}
     dom = max(out.items(), key=lambda kv: kv[1]["share_of_sweep_time"])[0] if out else None

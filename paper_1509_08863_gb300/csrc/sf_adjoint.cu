@@ -8,157 +8,185 @@
 //     = Gb_1 T_0^T + sum_{j >= 2} 2 Gb_j T_{j-1}^T   (a sampled dense-dense
 //       product: only entries (u, v) with W_uv stored, plus (u, u));
 //   dl/dW_uv = (2/lam)(M_uu + M_vv - M_uv - M_vu) (L = S - W, §2.1).
-// One fused kernel per order computes Gb_j for a row (a Clenshaw step), then
-// reuses it from registers for that row's sampled products against the
-// gathered rows of T_{j-1}, and the row's part of <G, T_j>.
+// Per order: Gb_j is one Clenshaw sweep (the sweep kernel with G as the
+// addend block); the sampled products and <G, T_j> are a second kernel that
+// walks the same sliced-ELL tiles (TMA-staged) and gathers rows of T_{j-1}.
+// The edge accumulators are kept in sliced-ELL order and mapped back to CSR
+// order once at the end.
 #include <math.h>
 
 #include "sf_step.cuh"
 
 namespace sf {
 
-struct AdjParams {
+struct SddmmParams {
     int32_t n;
-    const int32_t *rowptr;
-    const int32_t *colidx;
-    const float *val;
-    const float *dtil;
-    float wscale_u;
+    int64_t sell_slices;
+    const int32_t *sell_ptr;
+    const int32_t *sell_perm;
+    const int32_t *sell_idx;
     int32_t ld;
-    const float *B1;     // Gb_{j+1} (gathered), nullptr when Gb_j is given
-    const float *B2;     // Gb_{j+2} or nullptr
-    const float *Gq;     // packed G slab
-    float *Bout;         // Gb_j (written) -- or read when `given`
-    float *Routf;        // final: dl/dR slab (fp32), when j == 0
-    const float *Tm1;    // T_{j-1} (gathered for the sampled products), nullptr for j == 0
-    const float *Tj;     // T_j (own rows) for <G, T_j>
-    float m;             // 2, or 1 for j == 0
-    float alpha;         // a_j
-    float csd;           // 1 for j == 1, 2 for j >= 2
-    int32_t given;       // Gb_j already in Bout (j == p)
-    float *Moff;         // [nnz] accumulated
-    float *Mdiag;        // [n] accumulated
-    double *part;        // [gridDim.x] partial <G, T_j>
+    const float *Gb;   // Gb_j, own rows
+    const float *Tm1;  // T_{j-1}: gathered for the sampled products, own row for the diagonal (nullptr: none)
+    const float *Gq;   // packed G, own rows
+    const float *Tj;   // T_j own rows, for <G, T_j>
+    float csd;         // 1 for j == 1, 2 for j >= 2
+    float *Msell;      // [entries] accumulated edge products, sliced-ELL order
+    float *Mdiag;      // [n] accumulated diagonal products
+    double *part;      // [gridDim.x] partial <G, T_j>
+    int32_t *status;
 };
 
+// sum of v over the LPR lanes of a group (all lanes get the sum); `mask` holds
+// the group's lanes only, so groups of one warp may diverge (padding rows,
+// slices of different lengths)
 template <int LPR>
-__global__ void __launch_bounds__(256) adj_step_kernel(const AdjParams P) {
-    using V = VT<float>;
+__device__ __forceinline__ float group_sum(unsigned mask, float v) {
+#pragma unroll
+    for (int off = 1; off < LPR; off <<= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
+    using C = TileCfg<LPR>;
     constexpr int VEC = 4;
-    constexpr int NG = 32 / LPR;
-    constexpr int U = (NG == 1) ? 8 : 4;
-    __shared__ double red[8];
-    const int lane = threadIdx.x & 31;
-    const int q = lane % LPR, grp = lane / LPR;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
+    unsigned char *s_buf0 = smem_raw + 64;
+    constexpr int buf_bytes = C::buf_bytes(false);
+    __shared__ double s_red[8];
+
+    const int tid = threadIdx.x;
+    const int q = tid % LPR, grp = tid / LPR;
+    const int ngrp = blockDim.x / LPR;
+    const int n_tiles = (P.n + C::rows - 1) / C::rows;
     const int32_t ld = P.ld;
-    const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
+    const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << ((tid & 31) & ~(LPR - 1)));
+    const float *__restrict__ Tm1q = P.Tm1 ? P.Tm1 + q * VEC : nullptr;
     double gdot = 0.0;
-    for (int64_t i = warp0; i < P.n; i += nwarps) {
-        const int32_t beg = __ldg(P.rowptr + i), end = __ldg(P.rowptr + i + 1);
-        const int64_t ro = i * ld + q * VEC;
-        float t[VEC];
-        if (!P.given) {
-            float acc[VEC] = {0.f, 0.f, 0.f, 0.f};
-            for (int32_t base = beg; base < end; base += U * NG) {
-                int32_t k[U];
-                float wv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int32_t e = base + u * NG + grp;
-                    const bool ok = e < end;
-                    k[u] = ok ? __ldg(P.colidx + e) : -1;
-                    wv[u] = ok ? (P.val ? __ldg(P.val + e) : 1.0f) : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    float xv[VEC] = {0.f, 0.f, 0.f, 0.f};
-                    if (k[u] >= 0) V::ld_gather(P.B1 + (int64_t)k[u] * ld + q * VEC, xv);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] = fmaf(wv[u], xv[v], acc[v]);
-                }
-            }
-#pragma unroll
-            for (int off = LPR; off < 32; off <<= 1)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
-            // every group holds the full sum: each computes the row's Gb_j chunk
-            float xi[VEC], gq[VEC];
-            V::ld_gather(P.B1 + ro, xi);
-            V::ld_gather(P.Gq + ro, gq);
-            const float d = __ldg(P.dtil + i);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) t[v] = fmaf(P.alpha, gq[v], P.m * fmaf(d, xi[v], -P.wscale_u * acc[v]));
-            if (P.B2) {
-                float z[VEC];
-                V::ld_gather(P.B2 + ro, z);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) t[v] -= z[v];
-            }
-            if (grp == 0) {
-                if (P.Routf) V::st(P.Routf + ro, t);
-                else V::st(P.Bout + ro, t);
-            }
-        } else {
-            V::ld_gather(P.Bout + ro, t);
+
+    auto issue = [&](int tile, int b) {
+        unsigned char *base = s_buf0 + b * buf_bytes;
+        int32_t *sp = reinterpret_cast<int32_t *>(base);
+        int32_t *pm = sp + C::sp_ints;
+        int32_t *ix = pm + C::rows;
+        const int32_t s0 = tile * C::slices;
+        const int32_t e0 = P.sell_ptr[s0], e1 = P.sell_ptr[s0 + C::slices];
+        const int32_t cnt = e1 - e0;
+        const bool fits = (P.Tm1 != nullptr) && cnt <= C::entries;
+        const uint32_t bytes = (C::sp_ints + C::rows) * 4 + (fits ? (uint32_t)cnt * 4u : 0u);
+        s_meta[2 * b] = e0;
+        s_meta[2 * b + 1] = fits ? 1 : 0;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&s_bar[b], bytes);
+        bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
+        bulk_g2s(pm, P.sell_perm + (int64_t)s0 * kSliceRows, C::rows * 4, &s_bar[b]);
+        if (fits && cnt > 0) bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+        if ((int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int tile = blockIdx.x + k * gridDim.x;
+        if (tile >= n_tiles) break;
+        const int b = k & 1;
+        if (tid == 0 && tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
+        const bool landed = mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicOr(P.status, 1);
+            mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
+            if (tile + (int)gridDim.x < n_tiles) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
+            return;
         }
-        // <G, T_j> on the row
-        if (grp == 0 && P.Tj) {
-            float gq[VEC], tj[VEC];
-            V::ld_gather(P.Gq + ro, gq);
-            V::ld_gather(P.Tj + ro, tj);
-            float s = 0.f;
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) s = fmaf(gq[v], tj[v], s);
-#pragma unroll
-            for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
-            if (q == 0) gdot += (double)s;
-        }
-        if (P.Tm1) {
-            // diagonal term by group 0, neighbours by all groups
-            if (grp == 0) {
-                float tp[VEC];
-                V::ld_gather(P.Tm1 + ro, tp);
-                float s = 0.f;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) s = fmaf(t[v], tp[v], s);
-#pragma unroll
-                for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
+        const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
+        const int32_t *s_pm = s_sp + C::sp_ints;
+        const int32_t *s_ix = s_pm + C::rows;
+        const int32_t e0 = s_meta[2 * b];
+        const bool fits = s_meta[2 * b + 1] != 0;
+
+        for (int tr = grp; tr < C::rows; tr += ngrp) {
+            const int32_t i = s_pm[tr];
+            if (i < 0) continue;
+            const int sl = tr / kSliceRows, pos = tr % kSliceRows;
+            const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
+            const int32_t eo = so - e0 + pos * ls;
+            const int64_t ro = (int64_t)i * ld + q * VEC;
+            if (P.Tj) {
+                const float4 gq = __ldg(reinterpret_cast<const float4 *>(P.Gq + ro));
+                const float4 tj = __ldg(reinterpret_cast<const float4 *>(P.Tj + ro));
+                const float s = group_sum<LPR>(gmask, dot4(gq, tj));
+                if (q == 0) gdot += (double)s;
+            }
+            if (!P.Tm1) continue;
+            const float4 gb = __ldg(reinterpret_cast<const float4 *>(P.Gb + ro));
+            {
+                const float4 tp = __ldg(reinterpret_cast<const float4 *>(P.Tm1 + ro));
+                const float s = group_sum<LPR>(gmask, dot4(gb, tp));
                 if (q == 0) P.Mdiag[i] += P.csd * s;
             }
-            for (int32_t base = beg; base < end; base += NG) {
-                const int32_t e = base + grp;
-                float s = 0.f;
-                if (e < end) {
-                    const int32_t v = __ldg(P.colidx + e);
-                    float tp[VEC];
-                    V::ld_gather(P.Tm1 + (int64_t)v * ld + q * VEC, tp);
+            const int32_t *ip = fits ? s_ix + eo : P.sell_idx + e0 + eo;
+            float *mp = P.Msell + (int64_t)e0 + eo;  // 16-byte aligned: rows start on multiples of 4
+            for (int32_t j = 0; j < ls; j += 4) {
+                const int4 a = fits ? lds_int4(ip + j) : __ldg(reinterpret_cast<const int4 *>(ip + j));
+                const int32_t kk[4] = {a.x, a.y, a.z, a.w};
+                float4 x[4];
 #pragma unroll
-                    for (int c = 0; c < VEC; ++c) s = fmaf(t[c], tp[c], s);
+                for (int u = 0; u < 4; ++u)
+                    x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
+                float d[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d[u] = group_sum<LPR>(gmask, dot4(gb, x[u]));
+                if (q == 0) {
+                    float4 m = *reinterpret_cast<float4 *>(mp + j);
+                    m.x = fmaf(P.csd, d[0], m.x);
+                    m.y = fmaf(P.csd, d[1], m.y);
+                    m.z = fmaf(P.csd, d[2], m.z);
+                    m.w = fmaf(P.csd, d[3], m.w);
+                    *reinterpret_cast<float4 *>(mp + j) = m;
                 }
-#pragma unroll
-                for (int off = 1; off < LPR; off <<= 1) s += __shfl_xor_sync(gmask, s, off);
-                if (e < end && q == 0) P.Moff[e] += P.csd * s;
             }
         }
+        __syncthreads();  // buffer b fully consumed before it is refilled
     }
-    const int w = threadIdx.x >> 5;
-    if (lane == 0) red[w] = gdot;
+    const int w = tid >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) gdot += __shfl_xor_sync(0xffffffffu, gdot, off);
+    if ((tid & 31) == 0) s_red[w] = gdot;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double a = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += red[k];
+        for (int k2 = 0; k2 < (int)(blockDim.x >> 5); ++k2) a += s_red[k2];
         P.part[blockIdx.x] = a;
     }
 }
 
-// grad[e] = (2/lam)(Md[u] + Md[v] - M[e] - M[rev(e)]), rev(e) = entry (v, u),
-// found by binary search in the sorted row v.
-__global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *Moff,
-                                 const float *Mdiag, float two_over_lam, float *grad) {
+// Position in the sliced-ELL accumulators of the jj-th entry of CSR row u.
+__device__ __forceinline__ int64_t sell_pos(const int32_t *sptr, const int32_t *iperm, int32_t u, int32_t jj) {
+    const int32_t t = iperm[u];
+    const int32_t sl = t / kSliceRows, pos = t % kSliceRows;
+    const int32_t so = sptr[sl], ls = (sptr[sl + 1] - so) / kSliceRows;
+    return (int64_t)so + (int64_t)pos * ls + jj;
+}
+
+// grad[e] = (2/lam)(Md[u] + Md[v] - M_uv - M_vu) for CSR entry e = (u, v); the
+// entry (v, u) is found by binary search in the sorted row v.
+__global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *sptr,
+                                 const int32_t *iperm, const float *Msell, const float *Mdiag, float two_over_lam,
+                                 float *grad) {
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        for (int32_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+        const int32_t beg = rowptr[u];
+        for (int32_t e = beg; e < rowptr[u + 1]; ++e) {
             const int32_t v = colidx[e];
             int32_t lo = rowptr[v], hi = rowptr[v + 1] - 1;
             float mvu = 0.f;
@@ -166,46 +194,45 @@ __global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t
                 const int32_t mid = (lo + hi) >> 1;
                 const int32_t c = colidx[mid];
                 if (c == u) {
-                    mvu = Moff[mid];
+                    mvu = Msell[sell_pos(sptr, iperm, v, mid - rowptr[v])];
                     break;
                 }
                 if (c < u) lo = mid + 1;
                 else hi = mid - 1;
             }
-            grad[e] = two_over_lam * ((Mdiag[u] + Mdiag[v]) - (Moff[e] + mvu));
+            const float muv = Msell[sell_pos(sptr, iperm, u, e - beg)];
+            grad[e] = two_over_lam * ((Mdiag[u] + Mdiag[v]) - (muv + mvu));
         }
     }
 }
 
-static sf_status adj_launch_raw(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s);
-
 template <int LPR>
-static void launch_adj(const AdjParams &P, int grid, int block, cudaStream_t s) {
-    adj_step_kernel<LPR><<<grid, block, 0, s>>>(P);
+static sf_status sddmm_launch_t(const SddmmParams &P, int grid, int block, cudaStream_t s) {
+    const int smem = TileCfg<LPR>::smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(sddmm_kernel<LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(sddmm_kernel)");
+    sddmm_kernel<LPR><<<grid, block, smem, s>>>(P);
+    return check_launch("sddmm_kernel");
 }
 
-static sf_status adj_launch(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s, double bytes) {
+static sf_status sddmm_launch(int lpr, const SddmmParams &P, int grid, int block, cudaStream_t s, double bytes) {
     cudaEvent_t ea = nullptr, eb = nullptr;
     const bool prof = profiling_on() && profile_events(&ea, &eb);
     if (prof) cudaEventRecord(ea, s);
-    sf_status st = adj_launch_raw(lpr, P, grid, block, s);
+    sf_status st;
+    switch (lpr) {
+        case 2: st = sddmm_launch_t<2>(P, grid, block, s); break;
+        case 4: st = sddmm_launch_t<4>(P, grid, block, s); break;
+        case 8: st = sddmm_launch_t<8>(P, grid, block, s); break;
+        case 16: st = sddmm_launch_t<16>(P, grid, block, s); break;
+        case 32: st = sddmm_launch_t<32>(P, grid, block, s); break;
+        default: set_error("bad lanes per row"); return SF_ERR_ARG;
+    }
     if (prof) {
         cudaEventRecord(eb, s);
         profile_record(ea, eb, bytes, kProfTagAdjoint);
     }
     return st;
-}
-
-static sf_status adj_launch_raw(int lpr, const AdjParams &P, int grid, int block, cudaStream_t s) {
-    switch (lpr) {
-        case 2: launch_adj<2>(P, grid, block, s); break;
-        case 4: launch_adj<4>(P, grid, block, s); break;
-        case 8: launch_adj<8>(P, grid, block, s); break;
-        case 16: launch_adj<16>(P, grid, block, s); break;
-        case 32: launch_adj<32>(P, grid, block, s); break;
-        default: set_error("bad lanes per row"); return SF_ERR_ARG;
-    }
-    return check_launch("adj_step_kernel");
 }
 
 }  // namespace sf
@@ -232,6 +259,10 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD,
                               !g->unit_weights, &sh, o.carveout_pct);
     if (st) return st;
+    SweepShape shc;  // the Clenshaw sweep kernel of the adjoint (its own attributes and occupancy)
+    if ((st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_CLEN, !g->unit_weights, &shc,
+                         o.carveout_pct)))
+        return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int ld = sh.ld;
@@ -254,7 +285,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     }
     Scratch sc(s);
     float *store = nullptr, *seg = nullptr, *work[3] = {nullptr, nullptr, nullptr}, *bb[3] = {nullptr, nullptr, nullptr};
-    float *gq = nullptr, *coef = nullptr, *dtil = nullptr, *moff = nullptr, *mdiag = nullptr, *gR = nullptr;
+    float *gq = nullptr, *coef = nullptr, *dtil = nullptr, *msell = nullptr, *mdiag = nullptr, *gR = nullptr;
     double *part = nullptr, *ga = nullptr;
     if ((st = sc.get(&store, (size_t)nslots * blk))) return st;
     if (k > 1 && (st = sc.get(&seg, (size_t)(k + 1) * blk))) return st;
@@ -263,10 +294,10 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         if ((st = sc.get(&bb[q], blk))) return st;
     }
     if ((st = sc.get(&gq, blk)) || (st = sc.get(&coef, (size_t)p + 1)) || (st = sc.get(&dtil, (size_t)n)) ||
-        (st = sc.get(&mdiag, (size_t)n)) || (st = sc.get(&part, (size_t)sh.grid + 1)) ||
+        (st = sc.get(&mdiag, (size_t)n)) || (st = sc.get(&part, (size_t)sm_count() * 4 + 1)) ||
         (st = sc.get(&ga, (size_t)p + 1)))
         return st;
-    if (g->nnz > 0 && (st = sc.get(&moff, (size_t)g->nnz))) return st;
+    if ((st = sc.get(&msell, (size_t)g->sell.entries + kCsrPad))) return st;
     if (grad_R && (st = sc.get(&gR, blk))) return st;
     SF_CHECK_CUDA(cudaMemsetAsync(store, 0, sizeof(float) * (size_t)nslots * blk, s));
     if (seg) SF_CHECK_CUDA(cudaMemsetAsync(seg, 0, sizeof(float) * (size_t)(k + 1) * blk, s));
@@ -279,7 +310,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         for (int j = 0; j <= p; ++j) cf[j] = (float)coeffs[j];
         SF_CHECK_CUDA(cudaMemcpyAsync(coef, cf.data(), sizeof(float) * (p + 1), cudaMemcpyHostToDevice, s));
     }
-    if (moff) SF_CHECK_CUDA(cudaMemsetAsync(moff, 0, sizeof(float) * g->nnz, s));
+    SF_CHECK_CUDA(cudaMemsetAsync(msell, 0, sizeof(float) * ((size_t)g->sell.entries + kCsrPad), s));
     SF_CHECK_CUDA(cudaMemsetAsync(mdiag, 0, sizeof(float) * n, s));
     SF_CHECK_CUDA(cudaMemsetAsync(ga, 0, sizeof(double) * (p + 1), s));
     if (n > 0) {
@@ -359,37 +390,47 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         pack_kernel<float><<<pack_grid, 256, 0, s>>>(G, SF_F32, (int32_t)n, n_sig, c0, w, ld, gq, nullptr, 0, 1, coef,
                                                      p + 1, p, nullptr, bb[p % 3], nullptr);
         if ((st = check_launch("pack_kernel"))) return st;
-        AdjParams A = {};
-        A.n = (int32_t)n;
-        A.rowptr = g->rowptr;
-        A.colidx = g->colidx;
-        A.val = val;
-        A.dtil = dtil;
-        A.wscale_u = (float)two_over_lam;
-        A.ld = ld;
-        A.Gq = gq;
-        A.Moff = moff;
-        A.Mdiag = mdiag;
-        A.part = part;
+        // the Clenshaw sweep on G: Gb_j = a_j G + m Lt Gb_{j+1} - Gb_{j+2}
+        StepParams C = P;
+        C.Q = gq;
+        C.coef = coef;
+        C.coef_ld = p + 1;
+        C.n_cut = 1;
+        SddmmParams D = {};
+        D.n = (int32_t)n;
+        D.sell_slices = g->sell.n_slices;
+        D.sell_ptr = g->sell.sptr;
+        D.sell_perm = g->sell.perm;
+        D.sell_idx = g->sell.idx;
+        D.ld = ld;
+        D.Gq = gq;
+        D.Msell = msell;
+        D.Mdiag = mdiag;
+        D.part = part;
+        D.status = device_status();
+        const int sddmm_grid = sm_count() * 4;
         for (int j = p; j >= 0; --j) {
             if (k > 1 && j >= 1 && (st = ensure_segment(j - 1))) return st;
-            A.given = (j == p);
-            A.B1 = (j < p) ? bb[(j + 1) % 3] : nullptr;
-            A.B2 = (j + 2 <= p) ? bb[(j + 2) % 3] : nullptr;
-            A.Bout = bb[j % 3];
-            A.Routf = (j == 0) ? gR : nullptr;
-            if (j == 0 && !gR) A.Routf = work[0];  // dl/dR not requested: scratch target
-            A.Tm1 = (j >= 1) ? T_get(j - 1) : nullptr;
-            A.Tj = (j >= 1) ? T_get(j) : T_at(0);
-            A.m = (j == 0) ? 1.0f : 2.0f;
-            A.alpha = (float)coeffs[j];
-            A.csd = (j == 1) ? 1.0f : 2.0f;
-            // CSR once, Gb_{j+1} gathered, Gb_{j+2}, G, Gb_j out, T_j rows, T_{j-1} gathered,
-            // edge and diagonal accumulators read and written
-            const double adj_b = csr_b + blk_b * ((A.B1 ? 1 : 0) + (A.B2 ? 1 : 0) + 3 + (A.Tm1 ? 1 : 0)) +
-                                 (A.Tm1 ? 8.0 * ((double)g->nnz + n) : 0.0);
-            if ((st = adj_launch(sh.lpr, A, sh.grid, sh.block, s, adj_b))) return st;
-            pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 1, ga + j);
+            if (j < p) {
+                C.X = bb[(j + 1) % 3];
+                C.Z = (j + 2 <= p) ? bb[(j + 2) % 3] : nullptr;
+                C.j = j;
+                C.m = (j == 0) ? 1.0f : 2.0f;
+                C.out = bb[j % 3];
+                C.outf = (j == 0) ? (gR ? gR : work[0]) : nullptr;  // dl/dR (scratch target when not requested)
+                const double cb = csr_b + blk_b * (C.Z ? 4 : 3);
+                if ((st = launch_step(shc, MODE_CLEN, C, s, cb))) return st;
+            }
+            D.Gb = bb[j % 3];
+            D.Tm1 = (j >= 1) ? T_get(j - 1) : nullptr;
+            D.Tj = (j >= 1) ? T_get(j) : T_at(0);
+            D.csd = (j == 1) ? 1.0f : 2.0f;
+            // index stream once, G and T_j rows, Gb_j rows and T_{j-1} gathered once (when products
+            // are taken), edge and diagonal accumulators read and written
+            const double db = (double)g->sell.entries * 4 + blk_b * 2 +
+                              (D.Tm1 ? blk_b * 2 + 8.0 * ((double)g->nnz + n) : 0.0);
+            if ((st = sddmm_launch(sh.lpr, D, sddmm_grid, 256, s, db))) return st;
+            pair_sum_kernel<<<1, 256, 0, s>>>(part, sddmm_grid, 1, ga + j);
             if ((st = check_launch("pair_sum_kernel"))) return st;
         }
         if (grad_R) {
@@ -398,8 +439,9 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         }
     }
     if (g->nnz > 0) {
-        edge_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, g->rowptr, g->colidx, moff, mdiag,
-                                                                     (float)two_over_lam, grad_val);
+        edge_grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int32_t)n, g->rowptr, g->colidx, g->sell.sptr,
+                                                                     g->sell.iperm, msell, mdiag, (float)two_over_lam,
+                                                                     grad_val);
         if ((st = check_launch("edge_grad_kernel"))) return st;
     }
     if (grad_coeffs) {

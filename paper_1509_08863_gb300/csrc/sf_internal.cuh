@@ -104,6 +104,7 @@ struct SellMatrix {
     int32_t *perm = nullptr;  // [n_slices * 8] original row of each slice row, -1 for none
     int32_t *idx = nullptr;   // [entries + pad] column index, n for padding
     float *val = nullptr;     // [entries + pad] weight, 0 for padding; nullptr for unit weights
+    int32_t *iperm = nullptr; // [n] slice row (slice * 8 + position) of each original row
     bool built = false;
 };
 

@@ -64,12 +64,19 @@ __global__ void sell_fill_kernel(int32_t n, int32_t n_slices, const int32_t *row
     }
 }
 
+// iperm[perm[t]] = t for every slice row t holding a row
+__global__ void sell_iperm_kernel(int64_t count, const int32_t *perm, int32_t *iperm) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count && perm[t] >= 0) iperm[perm[t]] = (int32_t)t;
+}
+
 __global__ void sell_fill_pad_kernel(int32_t *p, int count, int32_t v) {
     if ((int)threadIdx.x < count) p[threadIdx.x] = v;
 }
 
 void sell_release(SellMatrix *S) {
     cudaFree(S->sptr);
+    cudaFree(S->iperm);
     cudaFree(S->perm);
     cudaFree(S->idx);
     cudaFree(S->val);
@@ -117,6 +124,9 @@ sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int3
     sell_fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, n_slices, rowptr, colidx, val, S->perm,
                                                                        S->sptr, S->idx, S->val);
     if ((st = check_launch("sell_fill_kernel"))) return st;
+    if (cudaMalloc(&S->iperm, sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) return oom();
+    sell_iperm_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(threads, S->perm, S->iperm);
+    if ((st = check_launch("sell_iperm_kernel"))) return st;
     S->n = n;
     S->n_slices = n_slices;
     S->entries = total;
