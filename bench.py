@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--kernel-case", default=None,
-                    help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT (MODE moments|clenshaw|forward, "
-                         "STORAGE f32|bf16) runs two sweeps of --case-orders orders over one column slab of "
+                    help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward, "
+                         "STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
     ap.add_argument("--filter-algo", default="auto", choices=["auto", "clenshaw", "forward"],
@@ -82,7 +82,9 @@ def run_kernel_case(args, wl):
     from paper_1509_08863_gb300 import build as sfbuild
 
     sfbuild.build()
-    mode, stor, slab, warps, carve = args.kernel_case.split(":")
+    fields = args.kernel_case.split(":")
+    mode, stor, slab, warps, carve = fields[:5]
+    kind = {"tiled": sf.SWEEP_TILED, "direct": sf.SWEEP_DIRECT}[fields[5] if len(fields) > 5 else "tiled"]
     slab, warps, carve = int(slab), int(warps), int(carve)
     st = sf.BF16 if stor == "bf16" else sf.F32
     algo = {"moments": sf.ALGO_CLENSHAW, "clenshaw": sf.ALGO_CLENSHAW, "forward": sf.ALGO_FORWARD}[mode]
@@ -93,7 +95,7 @@ def run_kernel_case(args, wl):
     _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
     p = args.case_orders
     a = sf.cheb_coeffs(lh, 0.05 * lh, p, True)
-    o = sf.Opts(storage=st, algo=algo, slab_cols=slab, block_warps=warps, carveout_pct=carve)
+    o = sf.Opts(storage=st, algo=algo, slab_cols=slab, block_warps=warps, carveout_pct=carve, sweep_kernel=kind)
     for _ in range(2):
         if mode == "moments":
             sf.cheb_moments(g, lh, Rs, p, o)
@@ -302,7 +304,8 @@ def main():
     def opts_for(st, algo=sf.ALGO_CLENSHAW):
         t = tuned[st]
         return sf.Opts(storage=st, algo=algo, slab_cols=t.slab_cols, block_warps=t.block_warps,
-                       blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window)
+                       blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window,
+                       sweep_kernel=t.sweep_kernel)
 
     def step(src, dst, Rt, st, collect=None):
         """One pass of the path; `st` is the block storage of both sweeps (FP16
@@ -435,7 +438,8 @@ def main():
                    "mean_degree": wl["deg"], "c_out_over_c_in": wl["eps"],
                    "block_storage": wl["storage"], "filter_algo": args.filter_algo,
                    "tiles": {("f32", "bf16", "f16")[k]: {"slab_cols": v.slab_cols, "block_warps": v.block_warps,
-                                                                  "carveout_pct": v.carveout_pct, "l2_window": v.l2_window}
+                                                                  "carveout_pct": v.carveout_pct, "l2_window": v.l2_window,
+                                                                  "sweep_kernel": ("auto", "tiled", "direct")[v.sweep_kernel]}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": (f"column shards x{world}: each rank filters its own {wl['R']} signals of one "
@@ -609,7 +613,7 @@ def run_batch(args, wl):
         coeffs[i] = sf.cheb_coeffs(lams[i], lk, p, True)[0]
     tuned = sf.autotune(gs[int(np.argmax(np.diff(offs)))], eta, st, 1)
     opts = sf.Opts(storage=st, slab_cols=tuned.slab_cols, block_warps=tuned.block_warps,
-                   carveout_pct=tuned.carveout_pct, l2_window=tuned.l2_window)
+                   carveout_pct=tuned.carveout_pct, l2_window=tuned.l2_window, sweep_kernel=tuned.sweep_kernel)
     Y = torch.empty((n_tot, eta), dtype=torch.float32, device=dev)
     Rs = [R[int(offs[i]):int(offs[i + 1])].contiguous() for i in range(ng)]
     Ys = [torch.empty_like(x) for x in Rs]

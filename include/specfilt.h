@@ -66,6 +66,13 @@ enum {
     SF_ALGO_CLENSHAW = 2  /* backward Clenshaw sum, one cutoff at a time */
 };
 
+/* Sweep kernel variants (sf_opts.sweep_kernel). */
+enum {
+    SF_SWEEP_AUTO = 0,   /* the staged tiles (SF_SWEEP_TILED) unless sf_autotune chose otherwise */
+    SF_SWEEP_TILED = 1,  /* CTA tiles whose indices are staged in shared memory by TMA bulk copies */
+    SF_SWEEP_DIRECT = 2  /* no staging: each warp reads its rows' indices from global memory */
+};
+
 /*
  * Tuning and precision options; a NULL sf_opts* means all zero (defaults).
  *   storage         SF_F32 / SF_BF16 / SF_F16: element type of the T_j (or
@@ -91,8 +98,18 @@ enum {
  *                   the sweep down.
  *   l2_window       1: mark each order's gathered block as persisting in L2
  *                   (access-policy window, up to the device's persisting
- *                   carve-out, which the first such call raises to its maximum
- *                   for this process); 0: no window.
+ *                   set-aside, which the call raises to its maximum); 0: no
+ *                   window. At the end of such a call the stream is
+ *                   synchronised, the persisting lines are turned back to
+ *                   normal and the set-aside is put back to its previous size
+ *                   (not while the stream is being captured). Measured slower
+ *                   than no window on the 1M-node workload; sf_autotune does
+ *                   not select it.
+ *   sweep_kernel    SF_SWEEP_*: which sweep kernel runs the orders. Both sum
+ *                   each row in the same order, so blocks and filter outputs
+ *                   are bit-identical; the FP64 moment sums may differ in the
+ *                   last bits (rows reach the block partial sums in another
+ *                   order).
  */
 typedef struct sf_opts {
     int32_t storage;
@@ -104,6 +121,7 @@ typedef struct sf_opts {
     int64_t mem_cap_mb;
     int32_t carveout_pct;
     int32_t l2_window;
+    int32_t sweep_kernel;
 } sf_opts;
 
 typedef struct sf_graph sf_graph; /* device-resident CSR of W, owned by the library */

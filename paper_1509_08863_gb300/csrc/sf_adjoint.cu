@@ -257,11 +257,11 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     if (o.slab_cols <= 0) o.slab_cols = auto_slab_cols(g->n, n_sig, SF_F32, 32ll << 20);
     SweepShape sh;
     sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD,
-                              !g->unit_weights, &sh, o.carveout_pct);
+                              !g->unit_weights, &sh, o.carveout_pct, o.sweep_kernel);
     if (st) return st;
     SweepShape shc;  // the Clenshaw sweep kernel of the adjoint (its own attributes and occupancy)
     if ((st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_CLEN, !g->unit_weights, &shc,
-                         o.carveout_pct)))
+                         o.carveout_pct, o.sweep_kernel)))
         return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;

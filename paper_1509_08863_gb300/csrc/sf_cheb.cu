@@ -27,16 +27,16 @@ int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t budget) {
 }
 
 template <typename TS, int LPR, bool W>
-static const void *step_fn(int mode) {
+static StepFn step_fn(int mode) {
     switch (mode) {
-        case MODE_FWD: return (const void *)cheb_step_kernel<TS, LPR, MODE_FWD, W>;
-        case MODE_MOM: return (const void *)cheb_step_kernel<TS, LPR, MODE_MOM, W>;
-        default: return (const void *)cheb_step_kernel<TS, LPR, MODE_CLEN, W>;
+        case MODE_FWD: return cheb_step_kernel<TS, LPR, MODE_FWD, W>;
+        case MODE_MOM: return cheb_step_kernel<TS, LPR, MODE_MOM, W>;
+        default: return cheb_step_kernel<TS, LPR, MODE_CLEN, W>;
     }
 }
 
 template <typename TS, bool W>
-static const void *step_fn_lpr(int lpr, int mode) {
+static StepFn step_fn_lpr(int lpr, int mode) {
     switch (lpr) {
         case 2: return step_fn<TS, 2, W>(mode);
         case 4: return step_fn<TS, 4, W>(mode);
@@ -47,7 +47,8 @@ static const void *step_fn_lpr(int lpr, int mode) {
     }
 }
 
-static const void *kernel_for(int storage, int lpr, int mode, bool weighted) {
+static StepFn kernel_for(int storage, int lpr, int mode, bool weighted, bool direct) {
+    if (direct) return direct_step_fn(storage, lpr, mode, weighted);
     if (storage == SF_F32) return weighted ? step_fn_lpr<float, true>(lpr, mode) : step_fn_lpr<float, false>(lpr, mode);
     if (storage == SF_BF16)
         return weighted ? step_fn_lpr<__nv_bfloat16, true>(lpr, mode) : step_fn_lpr<__nv_bfloat16, false>(lpr, mode);
@@ -82,9 +83,10 @@ int32_t *device_status() {
 }
 
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
-                     SweepShape *sh, int carveout_pct) {
+                     SweepShape *sh, int carveout_pct, int sweep_kernel) {
     SF_ARG(storage == SF_F32 || storage == SF_BF16 || storage == SF_F16, "storage type %d is not supported",
            storage);
+    SF_ARG(sweep_kernel >= SF_SWEEP_AUTO && sweep_kernel <= SF_SWEEP_DIRECT, "sweep_kernel must be SF_SWEEP_*");
     const int vec = vec_of(storage);
     SF_ARG(slab_cols % vec == 0, "slab_cols %d is not a multiple of %d", slab_cols, vec);
     const int lpr = slab_cols / vec;
@@ -92,10 +94,11 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
            "slab_cols %d gives %d lanes per row (need 2..32, power of two)", slab_cols, lpr);
     if (block_warps <= 0) block_warps = 8;
     SF_ARG(block_warps >= 1 && block_warps <= 8, "block_warps must be in 1..8");
-    const void *fn = kernel_for(storage, lpr, mode, weighted);
+    const bool direct = sweep_kernel == SF_SWEEP_DIRECT;
+    const void *fn = (const void *)kernel_for(storage, lpr, mode, weighted, direct);
     SF_ARG(fn, "no kernel for this shape");
-    const int smem = step_smem(lpr, weighted);
-    SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = direct ? 0 : step_smem(lpr, weighted);
+    if (!direct) SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // The L1 part of the unified L1/shared array tracks the gathers in flight:
     // by default ask for no more shared memory than the resident blocks need.
     SF_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -111,66 +114,36 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
     sh->grid = occ * sm_count();
     sh->smem = smem;
     sh->weighted = weighted;
+    sh->direct = direct;
     return SF_OK;
 }
 
 // Launches one sweep; with a window, the gathered block is marked persisting
 // in L2 for this launch only (the stream's own attributes are left alone).
-template <typename TS, int LPR, bool W>
-static void launch_mode(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
-    void (*fn)(const StepParams);
-    switch (mode) {
-        case MODE_FWD: fn = cheb_step_kernel<TS, LPR, MODE_FWD, W>; break;
-        case MODE_MOM: fn = cheb_step_kernel<TS, LPR, MODE_MOM, W>; break;
-        default: fn = cheb_step_kernel<TS, LPR, MODE_CLEN, W>; break;
-    }
-    if (sh.l2_window_bytes == 0) {
-        fn<<<sh.grid, sh.block, sh.smem, s>>>(P);
-        return;
-    }
+sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes) {
+    const StepFn fn = kernel_for(sh.storage, sh.lpr, mode, sh.weighted, sh.direct);
+    SF_ARG(fn, "no kernel for this shape");
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    const bool prof = profiling_on() && profile_events(&ea, &eb);
+    if (prof) cudaEventRecord(ea, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sh.grid);
     cfg.blockDim = dim3(sh.block);
     cfg.dynamicSmemBytes = sh.smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    at[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(P.X);
-    at[0].val.accessPolicyWindow.num_bytes = sh.l2_window_bytes;
-    at[0].val.accessPolicyWindow.hitRatio = sh.l2_hit_ratio;
-    at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    if (sh.l2_window_bytes > 0) {
+        at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(P.X);
+        at[0].val.accessPolicyWindow.num_bytes = sh.l2_window_bytes;
+        at[0].val.accessPolicyWindow.hitRatio = sh.l2_hit_ratio;
+        at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
     cudaLaunchKernelEx(&cfg, fn, P);
-}
-
-template <typename TS, bool W>
-static void launch_lpr(int mode, const SweepShape &sh, const StepParams &P, cudaStream_t s) {
-    switch (sh.lpr) {
-        case 2: launch_mode<TS, 2, W>(mode, sh, P, s); break;
-        case 4: launch_mode<TS, 4, W>(mode, sh, P, s); break;
-        case 8: launch_mode<TS, 8, W>(mode, sh, P, s); break;
-        case 16: launch_mode<TS, 16, W>(mode, sh, P, s); break;
-        default: launch_mode<TS, 32, W>(mode, sh, P, s); break;
-    }
-}
-
-sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes) {
-    cudaEvent_t ea = nullptr, eb = nullptr;
-    const bool prof = profiling_on() && profile_events(&ea, &eb);
-    if (prof) cudaEventRecord(ea, s);
-    if (sh.storage == SF_F32) {
-        if (sh.weighted) launch_lpr<float, true>(mode, sh, P, s);
-        else launch_lpr<float, false>(mode, sh, P, s);
-    } else if (sh.storage == SF_BF16) {
-        if (sh.weighted) launch_lpr<__nv_bfloat16, true>(mode, sh, P, s);
-        else launch_lpr<__nv_bfloat16, false>(mode, sh, P, s);
-    } else {
-        if (sh.weighted) launch_lpr<__half, true>(mode, sh, P, s);
-        else launch_lpr<__half, false>(mode, sh, P, s);
-    }
-    sf_status st = check_launch("cheb_step_kernel");
+    sf_status st = check_launch(sh.direct ? "cheb_step_direct_kernel" : "cheb_step_kernel");
     if (prof) {
         cudaEventRecord(eb, s);
         profile_record(ea, eb, bytes, mode * 3 + sh.storage);
@@ -233,20 +206,38 @@ static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r
 // Persisting-L2 window over the gathered block: the context's persisting
 // carve-out is raised once (a per-process limit, gone with the context) and
 // each launch marks its gathered block (up to the carve-out) as persisting.
+// The persisting set-aside is raised for the call and put back afterwards:
+// while it is up, the L2 share left to ordinary accesses is smaller even when
+// no line is marked persisting (measured: the 1M-node BF16 sweep takes 40%
+// longer), so it must not outlive the call.
+static size_t g_prev_persist[64];
+
 static sf_status setup_l2_window(SweepShape *sh, size_t block_bytes) {
-    static size_t carve[64] = {0};
     const int d = current_device();
+    SF_ARG(d >= 0 && d < 64, "device index %d out of range", d);
     int max_persist = 0, max_window = 0;
     SF_CHECK_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, d));
     SF_CHECK_CUDA(cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, d));
     if (max_persist <= 0 || max_window <= 0) return SF_OK;
-    if (d < 64 && carve[d] == 0) {
-        SF_CHECK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist));
-        carve[d] = (size_t)max_persist;
-    }
+    SF_CHECK_CUDA(cudaDeviceGetLimit(&g_prev_persist[d], cudaLimitPersistingL2CacheSize));
+    SF_CHECK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist));
     const size_t win = block_bytes < (size_t)max_window ? block_bytes : (size_t)max_window;
     sh->l2_window_bytes = win;
     sh->l2_hit_ratio = win <= (size_t)max_persist ? 1.0f : (float)max_persist / (float)win;
+    return SF_OK;
+}
+
+// Lines marked persisting keep their status after the launch: once the
+// window's sweeps have run, turn them back to normal and put the set-aside
+// back (skipped while the stream is being captured into a graph, where the
+// host cannot wait for the work).
+static sf_status release_l2_window(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SF_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SF_OK;
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    SF_CHECK_CUDA(cudaCtxResetPersistingL2Cache());
+    SF_CHECK_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_prev_persist[current_device()]));
     return SF_OK;
 }
 
@@ -278,7 +269,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                             const double *tol_dev = nullptr) {
     SweepShape sh;
     sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh,
-                              o.carveout_pct);
+                              o.carveout_pct, o.sweep_kernel);
     if (st) return st;
     int32_t *status = device_status();
     SF_ARG(status, "device status word unavailable");
@@ -427,6 +418,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
             if ((st = check_launch("unpack_kernel"))) return st;
         }
     }
+    if (sh.l2_window_bytes > 0) return release_l2_window(s);
     return SF_OK;
 }
 
@@ -679,13 +671,17 @@ SF_API sf_status sf_autotune(const sf_graph *g, int32_t n_sig, int32_t storage, 
     const double lam = 2.0 * g->max_strength + 1.0;
     for (int w = full; w >= vec * 2; w /= 2) {
         for (int wi = 0; wi < 2; ++wi) {
-            for (int ci = 0; ci < 6; ++ci) {
+            // staged tiles at three carve-outs, and the direct kernel (no shared memory). The
+            // persisting-L2 window is not searched: it never won once the set-aside it needs
+            // was put back after each call, and raising it slows every other kernel meanwhile.
+            for (int ci = 0; ci < 4; ++ci) {
                 sf_opts t = b0;  // algorithm as the caller will run it (AUTO resolves per storage)
                 t.slab_cols = w;
                 t.block_warps = warps_opts[wi];
                 t.blocks_per_sm = 0;
-                t.carveout_pct = carve_opts[ci % 3];
-                t.l2_window = ci / 3;
+                t.l2_window = 0;
+                t.sweep_kernel = ci < 3 ? SF_SWEEP_TILED : SF_SWEEP_DIRECT;
+                t.carveout_pct = ci < 3 ? carve_opts[ci] : 0;
                 st = sf_cheb_filter(g, lam, cf.data(), n_cut, p_try, R, SF_F32, n_sig, Y, &t, stream);  // warm-up
                 if (st) continue;
                 sf_profile_begin();

@@ -87,7 +87,7 @@ __global__ void radix_scatter_kernel(const uint64_t *keys_in, const float *vals_
         int64_t idx = base + r * 32 + lane;
         bool ok = idx < count;
         key[r] = ok ? keys_in[idx] : 0ull;
-        val[r] = ok ? vals_in[idx] : 0.f;
+        val[r] = (ok && vals_in) ? vals_in[idx] : 0.f;
         int d = ok ? (int)((key[r] >> shift) & 0xFF) : 256 + lane;  // out-of-range items never match
         dig[r] = ok ? d : -1;
         unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -116,7 +116,7 @@ __global__ void radix_scatter_kernel(const uint64_t *keys_in, const float *vals_
         int d = dig[r];
         int64_t pos = (int64_t)offs[(int64_t)d * tiles + blockIdx.x] + wcnt[w][d] + rank[r];
         keys_out[pos] = key[r];
-        vals_out[pos] = val[r];
+        if (vals_out) vals_out[pos] = val[r];
     }
 }
 
@@ -184,15 +184,15 @@ sf_status compute_strength(sf_graph *g, cudaStream_t s) {
     return SF_OK;
 }
 
-static sf_status radix_sort(uint64_t *&keys, float *&vals, uint64_t *&keys_alt, float *&vals_alt,
-                            int64_t count, int bits, cudaStream_t s) {
+sf_status radix_sort(uint64_t *&keys, float *&vals, uint64_t *&keys_alt, float *&vals_alt, int64_t count,
+                     int shift0, int bits, cudaStream_t s) {
     if (count <= 1) return SF_OK;
     int32_t tiles = (int32_t)((count + kSortTile - 1) / kSortTile);
     Scratch sc(s);
     int32_t *hist = nullptr;
     sf_status st = sc.get(&hist, (size_t)tiles * 256);
     if (st) return st;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = shift0; shift < bits; shift += 8) {
         radix_hist_kernel<<<tiles, kSortThreads, 0, s>>>(keys, count, shift, hist, tiles);
         if ((st = check_launch("radix_hist_kernel"))) return st;
         if ((st = exclusive_scan_i32(hist, hist, (int64_t)tiles * 256, s))) return st;
@@ -284,7 +284,7 @@ SF_API sf_status sf_csr_build(int32_t n_nodes, int64_t n_edges, const int32_t *s
                 return fail(SF_ERR_ARG);
             }
             valid = cnt - 2 * (int64_t)hf[2];
-            if ((st = radix_sort(k0, v0, k1, v1, cnt, bits, s))) return fail(st);
+            if ((st = radix_sort(k0, v0, k1, v1, cnt, 0, bits, s))) return fail(st);
             if (valid > 0) {
                 run_heads_kernel<<<(unsigned)((valid + 255) / 256), 256, 0, s>>>(k0, valid, head);
                 if ((st = check_launch("run_heads_kernel"))) return fail(st);

@@ -112,6 +112,11 @@ namespace sf {
 sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val,
                      cudaStream_t s);
 void sell_release(SellMatrix *S);
+// Stable LSD radix sort of 64-bit keys on bits [shift0, bits) (8 bits per
+// pass), carrying `vals` when non-null; keys/vals end up in the returned
+// pointers (the _alt buffers are the ping-pong partners).
+sf_status radix_sort(uint64_t *&keys, float *&vals, uint64_t *&keys_alt, float *&vals_alt, int64_t count,
+                     int shift0, int bits, cudaStream_t s);
 }  // namespace sf
 
 struct sf_graph {

@@ -1,35 +1,37 @@
 // Sliced-ELL copy of a CSR for the sweep kernels.
 //
 // Rows are sorted by decreasing length (ties by index) inside windows of
-// kSellWindow consecutive rows, then cut into slices of kSliceRows rows. A
-// slice is padded to the length of its longest row rounded up to a multiple
-// of 4 and stored row after row; padding entries carry index n (a zero row
-// appended to every gathered block) and weight 0. Slice offsets are
+// 2^kSellWindowLog2 consecutive rows, then cut into slices of kSliceRows
+// rows. A slice is padded to the length of its longest row rounded up to a
+// multiple of 4 and stored row after row; padding entries carry index n (a
+// zero row appended to every gathered block) and weight 0. Slice offsets are
 // therefore multiples of 32 entries (128 bytes) and every row starts on a
 // 16-byte boundary. The slice count is padded to a multiple of
 // kSellSliceAlign with empty slices so that whole tiles can be bulk-copied.
-// Every step is deterministic (rank sort, max, prefix sum, copy).
+// The window is about as many rows as the sweep kernels process at once, so
+// the sort keeps whatever locality the row order has at that scale while the
+// slices of one tile (64 or 128 consecutive sorted rows) have nearly equal
+// lengths: the warps of a tile finish together and padding stays small.
+// Every step is deterministic (stable radix sort, max, prefix sum, copy).
 #include "sf_step.cuh"
 
 namespace sf {
 
-constexpr int kSellWindow = 256;
+constexpr int kSellWindowLog2 = 15;
 constexpr int kSellSliceAlign = 16;
 
-// perm[w * 256 + rank] = row, ranking rows of window w by (length desc, index asc).
-__global__ void sell_rank_kernel(int32_t n, const int32_t *rowptr, int32_t *perm) {
-    __shared__ int32_t len[kSellWindow];
-    const int32_t base = blockIdx.x * kSellWindow;
-    const int32_t i = base + threadIdx.x;
-    len[threadIdx.x] = (i < n) ? (rowptr[i + 1] - rowptr[i]) : -1;
-    __syncthreads();
-    const int32_t li = len[threadIdx.x];
-    int32_t rank = 0;
-    for (int j = 0; j < kSellWindow; ++j) {
-        const int32_t lj = len[j];
-        rank += (lj > li) || (lj == li && j < (int)threadIdx.x);
-    }
-    perm[base + rank] = (i < n) ? i : -1;
+// key = window (bits 48..63) | 0xffff - min(length, 0xffff) (bits 32..47) | row (bits 0..31);
+// a stable sort on bits 32..63 orders rows by window, then length descending, then index.
+__global__ void sell_key_kernel(int32_t n, const int32_t *rowptr, uint64_t *keys) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t len = (uint32_t)min(rowptr[i + 1] - rowptr[i], 0xffff);
+    keys[i] = ((uint64_t)((uint32_t)i >> kSellWindowLog2) << 48) | ((uint64_t)(0xffffu - len) << 32) | (uint32_t)i;
+}
+
+__global__ void sell_perm_kernel(int32_t n, const uint64_t *keys, int32_t *perm) {
+    const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) perm[t] = (int32_t)(uint32_t)(keys[t] & 0xffffffffull);
 }
 
 // entries of slice s = 8 * (longest row length rounded up to 4)
@@ -87,10 +89,9 @@ sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int3
                      cudaStream_t s) {
     if (S->built) return SF_OK;
     sell_release(S);
-    const int32_t n_windows = (n + kSellWindow - 1) / kSellWindow;
     int32_t n_slices = (n + kSliceRows - 1) / kSliceRows;
     n_slices = (n_slices + kSellSliceAlign - 1) / kSellSliceAlign * kSellSliceAlign;
-    const int64_t perm_len = std::max<int64_t>((int64_t)n_slices * kSliceRows, (int64_t)n_windows * kSellWindow);
+    const int64_t perm_len = (int64_t)n_slices * kSliceRows;
     sf_status st;
     auto oom = [&]() {
         cudaGetLastError();
@@ -102,8 +103,17 @@ sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int3
         cudaMalloc(&S->sptr, sizeof(int32_t) * (size_t)(n_slices + 1 + kCsrPad)) != cudaSuccess)
         return oom();
     SF_CHECK_CUDA(cudaMemsetAsync(S->perm, 0xff, sizeof(int32_t) * (size_t)perm_len, s));  // -1
-    sell_rank_kernel<<<n_windows, kSellWindow, 0, s>>>(n, rowptr, S->perm);
-    if ((st = check_launch("sell_rank_kernel"))) return st;
+    if (n > 0) {
+        Scratch sc(s);
+        uint64_t *keys = nullptr, *keys_alt = nullptr;
+        float *no_vals = nullptr, *no_vals_alt = nullptr;
+        if ((st = sc.get(&keys, (size_t)n)) || (st = sc.get(&keys_alt, (size_t)n))) return st;
+        sell_key_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, rowptr, keys);
+        if ((st = check_launch("sell_key_kernel"))) return st;
+        if ((st = radix_sort(keys, no_vals, keys_alt, no_vals_alt, n, 32, 64, s))) return st;
+        sell_perm_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, keys, S->perm);
+        if ((st = check_launch("sell_perm_kernel"))) return st;
+    }
     {
         Scratch sc(s);
         int32_t *slen = nullptr;

@@ -279,7 +279,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // ------------------------------------------------------------ the sweep
 // The sweep reads the graph in a sliced-ELL layout (built from the CSR by
 // the library, see sell_build): rows are sorted by length inside windows of
-// 256 rows and grouped into slices of 8 rows padded to a common length (a
+// 32768 rows and grouped into slices of 8 rows padded to a common length (a
 // multiple of 4); padding entries point at the zero row n appended to every
 // gathered block. Each slice is stored row after row, so a row's indices
 // are 16-byte aligned and read four at a time.
@@ -372,29 +372,124 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
     }
 }
 
-template <typename TS, int LPR, int MODE, bool W>
-__global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
+// One row of one order: acc = sum_e w_e X[idx_e] over the row's ls entries,
+// then t = m (d_i X_i - (2/lam) acc) - Z_i [+ a_j Q_i], stored; the forward
+// mode adds a_cj t to each accumulator, the moment mode sums t.t and t.X_i.
+template <typename TS, int MODE, bool W, bool SMEM>
+__device__ __forceinline__ void sweep_row(const StepParams &P, int32_t i, int q, const int32_t *ip, const float *wp,
+                                          int32_t ls, double &mtt, double &mtx) {
     using V = VT<TS>;
-    using C = TileCfg<LPR>;
     constexpr int VEC = V::V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
-    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
-    unsigned char *s_buf0 = smem_raw + 64;
-    constexpr int buf_bytes = C::buf_bytes(W);
-    __shared__ double s_red[8][2];
-
-    const int tid = threadIdx.x;
-    const int q = tid % LPR, grp = tid / LPR;
-    const int ngrp = blockDim.x / LPR;
-    const int n_tiles = (P.n + C::rows - 1) / C::rows;
     const TS *__restrict__ X = static_cast<const TS *>(P.X);
     const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
     TS *__restrict__ out = static_cast<TS *>(P.out);
     const int32_t ld = P.ld;
-    const float m = P.m;
-    const TS *__restrict__ Xq = X + q * VEC;
+    const int64_t ro = (int64_t)i * ld + q * VEC;
+    // epilogue operands first (kept packed): their latency overlaps the gathers
+    const typename V::raw_t xi_r = V::ld_raw(X + ro);
+    const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
+    typename V::raw_t q_r = V::zero_raw();
+    if (MODE == MODE_CLEN) q_r = V::ld_raw_stream(Qb + ro);
+    const float d = __ldcs(P.dtil + i);
+    const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
+    const int g = P.gid ? __ldcs(P.gid + i) : 0;
+
+    float acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+    gather_row<TS, W, SMEM>(X + q * VEC, ld, ip, wp, ls, acc);
+
+    float t[VEC], xi[VEC];
+    {
+        float z[VEC];
+        V::to_float(xi_r, xi);
+        V::to_float(z_r, z);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) t[v] = P.m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
+    }
+    if (MODE == MODE_CLEN) {
+        const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
+        float qv[VEC];
+        V::to_float(q_r, qv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
+    }
+    if (MODE == MODE_CLEN && P.outf) {
+        float *o = P.outf + ro;
+#pragma unroll
+        for (int v = 0; v < VEC; v += 4)
+            __stcs(reinterpret_cast<float4 *>(o + v), make_float4(t[v], t[v + 1], t[v + 2], t[v + 3]));
+    } else {
+        V::st(out + ro, t);
+    }
+    if (MODE == MODE_FWD) {
+        for (int c = 0; c < P.n_cut; ++c) {
+            const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + P.j);
+            float *y = P.Y + c * P.ystride + ro;
+#pragma unroll
+            for (int v = 0; v < VEC; v += 4) {
+                float4 yy = __ldcs(reinterpret_cast<const float4 *>(y + v));
+                yy.x = fmaf(a, t[v], yy.x);
+                yy.y = fmaf(a, t[v + 1], yy.y);
+                yy.z = fmaf(a, t[v + 2], yy.z);
+                yy.w = fmaf(a, t[v + 3], yy.w);
+                __stcs(reinterpret_cast<float4 *>(y + v), yy);
+            }
+        }
+    }
+    if (MODE == MODE_MOM) {
+        float tt = 0.f, tx = 0.f;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            const float ts = V::rt(t[v]);  // the value the next order reads
+            tt = fmaf(ts, ts, tt);
+            tx = fmaf(ts, xi[v], tx);
+        }
+        mtt += (double)tt;
+        mtx += (double)tx;
+    }
+}
+
+// Moment sums of the block in a fixed order (lanes of a warp, then warps)
+// into part[2 * blockIdx.x + {0, 1}]. Every thread of the block calls it.
+__device__ __forceinline__ void block_moments(const StepParams &P, double mtt, double mtx) {
+    __shared__ double s_red[32][2];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        mtt += __shfl_xor_sync(0xffffffffu, mtt, off);
+        mtx += __shfl_xor_sync(0xffffffffu, mtx, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_red[w][0] = mtt;
+        s_red[w][1] = mtx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a += s_red[k][0];
+            b += s_red[k][1];
+        }
+        P.part[2 * blockIdx.x] = a;
+        P.part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+template <typename TS, int LPR, int MODE, bool W>
+__global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
+    using C = TileCfg<LPR>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
+    unsigned char *s_buf0 = smem_raw + 64;
+    constexpr int buf_bytes = C::buf_bytes(W);
+
+    const int tid = threadIdx.x;
+    const int q = tid % LPR, grp = tid / LPR;
+    const int ngrp = blockDim.x / LPR;
+    const int n_tiles = (P.n + C::rows - 1) / C::rows;
     double mtt = 0.0, mtx = 0.0;
 
     // thread 0: stage tile `tile` into buffer `b`
@@ -455,98 +550,40 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
             const int sl = tr / kSliceRows, pos = tr % kSliceRows;
             const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
             const int32_t eo = so - e0 + pos * ls;  // offset of the row's first entry in the tile
-            const int64_t ro = (int64_t)i * ld + q * VEC;
-            // epilogue operands first (kept packed): their latency overlaps the gathers
-            const typename V::raw_t xi_r = V::ld_raw(X + ro);
-            const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
-            typename V::raw_t q_r = V::zero_raw();
-            if (MODE == MODE_CLEN) q_r = V::ld_raw_stream(Qb + ro);
-            const float d = __ldcs(P.dtil + i);
-            const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
-            const int g = P.gid ? __ldcs(P.gid + i) : 0;
-
-            float acc[VEC];
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-            if (fits) gather_row<TS, W, true>(Xq, ld, s_ix + eo, s_wv + eo, ls, acc);
-            else gather_row<TS, W, false>(Xq, ld, P.sell_idx + e0 + eo, P.sell_val + e0 + eo, ls, acc);
-
-
-            float t[VEC], xi[VEC];
-            {
-                float z[VEC];
-                V::to_float(xi_r, xi);
-                V::to_float(z_r, z);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) t[v] = m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
-            }
-            if (MODE == MODE_CLEN) {
-                const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
-                float qv[VEC];
-                V::to_float(q_r, qv);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
-            }
-            if (MODE == MODE_CLEN && P.outf) {
-                float *o = P.outf + ro;
-#pragma unroll
-                for (int v = 0; v < VEC; v += 4)
-                    __stcs(reinterpret_cast<float4 *>(o + v), make_float4(t[v], t[v + 1], t[v + 2], t[v + 3]));
-            } else {
-                V::st(out + ro, t);
-            }
-            if (MODE == MODE_FWD) {
-                for (int c = 0; c < P.n_cut; ++c) {
-                    const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + P.j);
-                    float *y = P.Y + c * P.ystride + ro;
-#pragma unroll
-                    for (int v = 0; v < VEC; v += 4) {
-                        float4 yy = __ldcs(reinterpret_cast<const float4 *>(y + v));
-                        yy.x = fmaf(a, t[v], yy.x);
-                        yy.y = fmaf(a, t[v + 1], yy.y);
-                        yy.z = fmaf(a, t[v + 2], yy.z);
-                        yy.w = fmaf(a, t[v + 3], yy.w);
-                        __stcs(reinterpret_cast<float4 *>(y + v), yy);
-                    }
-                }
-            }
-            if (MODE == MODE_MOM) {
-                float tt = 0.f, tx = 0.f;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    const float ts = V::rt(t[v]);  // the value the next order reads
-                    tt = fmaf(ts, ts, tt);
-                    tx = fmaf(ts, xi[v], tx);
-                }
-                mtt += (double)tt;
-                mtx += (double)tx;
-            }
+            if (fits) sweep_row<TS, MODE, W, true>(P, i, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
+            else sweep_row<TS, MODE, W, false>(P, i, q, P.sell_idx + e0 + eo, W ? P.sell_val + e0 + eo : nullptr,
+                                               ls, mtt, mtx);
         }
         __syncthreads();  // buffer b fully consumed before it is refilled
     }
-    if (MODE == MODE_MOM) {
-        // fixed-order reduction: lanes of a warp, then warps of the block
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            mtt += __shfl_xor_sync(0xffffffffu, mtt, off);
-            mtx += __shfl_xor_sync(0xffffffffu, mtx, off);
-        }
-        const int w = tid >> 5;
-        if ((tid & 31) == 0) {
-            s_red[w][0] = mtt;
-            s_red[w][1] = mtx;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                a += s_red[k][0];
-                b += s_red[k][1];
-            }
-            P.part[2 * blockIdx.x] = a;
-            P.part[2 * blockIdx.x + 1] = b;
-        }
+    if (MODE == MODE_MOM) block_moments(P, mtt, mtx);
+}
+
+// Direct variant: no staging and no block barriers. Warp c of the grid walks
+// chunks of 32 / LPR consecutive slice rows (chunk c, c + W, ... for W warps
+// in the grid); each lane group reads its row's slice offsets, original row
+// and indices straight from global memory (16-byte vector loads, broadcast
+// within the group). With no shared memory the whole L1 holds gathers in
+// flight.
+template <typename TS, int LPR, int MODE, bool W>
+__global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepParams P) {
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31, q = lane % LPR, g = lane / LPR;
+    const int64_t n_chunks = ((int64_t)P.n + RPW - 1) / RPW;
+    const int wpb = blockDim.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * wpb;
+    double mtt = 0.0, mtx = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+        const int64_t t = c * RPW + g;
+        const int32_t i = (t < P.n) ? __ldg(P.sell_perm + t) : -1;
+        if (i < 0) continue;
+        const int32_t sl = (int32_t)(t / kSliceRows), pos = (int32_t)(t % kSliceRows);
+        const int32_t so = __ldg(P.sell_ptr + sl);
+        const int32_t ls = (__ldg(P.sell_ptr + sl + 1) - so) / kSliceRows;
+        const int64_t eo = (int64_t)so + (int64_t)pos * ls;
+        sweep_row<TS, MODE, W, false>(P, i, q, P.sell_idx + eo, W ? P.sell_val + eo : nullptr, ls, mtt, mtx);
     }
+    if (MODE == MODE_MOM) block_moments(P, mtt, mtx);
 }
 
 // ------------------------------------------------------------ pack / unpack
@@ -658,6 +695,7 @@ struct SweepShape {
     int grid;         // blocks
     int smem;         // dynamic shared memory per block
     bool weighted;    // kernel reads weights
+    bool direct = false;  // cheb_step_direct_kernel instead of the staged tiles
     size_t l2_window_bytes = 0;  // persisting-L2 window over the gathered block (0: none)
     float l2_hit_ratio = 0.f;
 };
@@ -665,7 +703,10 @@ struct SweepShape {
 // Picks the slab width (columns) for n rows and n_sig signals.
 int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t l2_budget_bytes);
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
-                     SweepShape *sh, int carveout_pct = 0);
+                     SweepShape *sh, int carveout_pct = 0, int sweep_kernel = 0);
+using StepFn = void (*)(const StepParams);
+// cheb_step_direct_kernel instances (defined in their own translation unit).
+StepFn direct_step_fn(int storage, int lpr, int mode, bool weighted);
 // Device error word written by the sweep kernels (bounded waits).
 int32_t *device_status();
 sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes);

@@ -47,7 +47,7 @@ def test_sbm1m_filter_and_moments_column_sample(sf, oracle_mod):
     Rt = torch.as_tensor(R, dtype=torch.float32, device=dev)
     tuned = sf.autotune(g, wl["R"], sf.BF16, 1)
     opts = sf.Opts(storage=sf.BF16, slab_cols=tuned.slab_cols, block_warps=tuned.block_warps,
-                   carveout_pct=tuned.carveout_pct, l2_window=tuned.l2_window)
+                   carveout_pct=tuned.carveout_pct, l2_window=tuned.l2_window, sweep_kernel=tuned.sweep_kernel)
     mu = sf.cheb_moments(g, lh, Rt, p, opts)
     lk = sf.dichotomy(mu, p, lh, wl["k"] - 0.5)
     a = sf.cheb_coeffs(lh, lk, p, True)

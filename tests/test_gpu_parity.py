@@ -253,6 +253,49 @@ def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo):
         assert err <= 2.0 ** -11 * p, (scale, err)
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_direct_kernel_matches_tiled_and_oracle(sf, oracle_mod, weighted):
+    """The unstaged sweep kernel sums every row in the same order as the staged
+    tiles: filter (both algorithms, several cutoffs) and the adjoint agree bit
+    for bit across lane-group widths and storages, moments to FP64 reduction
+    order, and the FP32 filter meets the oracle bound. Ragged sizes: N = 3001 (not a multiple of
+    the 8-row slices or the tiles), 37 signals (partial last slab)."""
+    n, n_sig, p = 3001, 37, 23
+    src, dst, w = random_graph(n, 20000, 31)
+    g, go = build_both(sf, oracle_mod, n, src, dst, w if weighted else None)
+    _, lh = sf.lambda_max_estimate(g, 40, None, seed=2)
+    R = np.random.default_rng(5).standard_normal((n, n_sig)) / math.sqrt(n_sig)
+    a = oracle_mod.cheb_coeffs(lh, [0.05 * lh, 0.3 * lh], p, True)
+    Yo = oracle_mod.cheb_filter(go, lh, a, R)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    cases = [(sf.F32, s) for s in (8, 16, 32, 64, 128)] + [(sf.BF16, s) for s in (16, 32, 64)] + [(sf.F16, 32)]
+    for st, slab in cases:
+        for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+            out = []
+            for kind in (sf.SWEEP_TILED, sf.SWEEP_DIRECT):
+                o = sf.Opts(storage=st, algo=algo, slab_cols=slab, sweep_kernel=kind)
+                out.append(sf.cheb_filter(g, lh, a, Rt, o).cpu().numpy())
+            assert np.array_equal(out[0], out[1]), (st, slab, algo)
+            if st == sf.F32:
+                for c in range(2):
+                    assert rel(out[1][c], Yo[c]) <= 1e-5
+        if st != sf.F16:
+            mus = [sf.cheb_moments(g, lh, Rt, p, sf.Opts(storage=st, slab_cols=slab, sweep_kernel=kind))
+                   for kind in (sf.SWEEP_TILED, sf.SWEEP_DIRECT)]
+            # same blocks; the FP64 moment sums differ only in the order rows reach them
+            assert np.all(np.abs(mus[0] - mus[1]) <= 1e-12 * mus[0][0]), (st, slab)
+    # the persisting-L2 window changes cache hints only
+    yw = [sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.BF16, slab_cols=32, l2_window=w)).cpu().numpy()
+          for w in (0, 1)]
+    assert np.array_equal(yw[0], yw[1])
+    G = torch.as_tensor(np.random.default_rng(6).standard_normal((n, n_sig)), dtype=torch.float32, device="cuda")
+    grads = [sf.cheb_filter_backward(g, lh, a[0], Rt, G, True, sf.Opts(slab_cols=32, sweep_kernel=kind))
+             for kind in (sf.SWEEP_TILED, sf.SWEEP_DIRECT)]
+    assert torch.equal(grads[0][0], grads[1][0])
+    assert np.array_equal(grads[0][1], grads[1][1])
+    assert torch.equal(grads[0][2], grads[1][2])
+
+
 # ------------------------------------------------------------------ moments / count
 def test_moments_and_counts_match_oracle(sf, oracle_mod):
     from paper_1509_08863_gb300 import synth
