@@ -96,6 +96,9 @@ constexpr int kCsrPad = 4;
 
 // ---------------------------------------------------------------- objects
 // Sliced-ELL copy of a CSR used by the sweep kernels (see sf_sell.cu).
+namespace sf {
+constexpr int kSliceRows = 8;  // rows per slice
+}  // namespace sf
 struct SellMatrix {
     int32_t n = 0;
     int32_t n_slices = 0;

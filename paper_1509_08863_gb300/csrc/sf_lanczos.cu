@@ -35,25 +35,41 @@ __device__ void block_dot_store(double acc, double *part) {
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// w = L v (warp per row, lanes over the row's entries); partial <w, v>.
-__global__ void __launch_bounds__(256) lap_spmv_f64_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx,
-                                                           const float *val, const double *strength, const double *v,
-                                                           double *w, double *part) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// w = L v over the sliced-ELL copy: one thread per row, indices read four at a
+// time and four gathers in flight; partial <w, v>. Padding entries gather
+// v[n] = 0. The row sum runs in entry order (the CSR column order).
+__global__ void __launch_bounds__(256) lap_spmv_sell_kernel(int32_t n, const int32_t *sptr, const int32_t *perm,
+                                                            const int32_t *idx, const float *sval,
+                                                            const double *strength, const double *v, double *w,
+                                                            double *part) {
     double dot = 0.0;
-    for (int64_t i = warp0; i < n; i += nw) {
-        const int32_t beg = rowptr[i], end = rowptr[i + 1];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = perm[t];
+        if (i < 0) continue;
+        const int32_t sl = (int32_t)(t / kSliceRows), pos = (int32_t)(t % kSliceRows);
+        const int32_t so = sptr[sl], ls = (sptr[sl + 1] - so) / kSliceRows;
+        const int64_t eo = (int64_t)so + (int64_t)pos * ls;
         double acc = 0.0;
-        for (int32_t e = beg + lane; e < end; e += 32) acc += (double)(val ? val[e] : 1.0f) * v[colidx[e]];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) {
-            const double wi = strength[i] * v[i] - acc;
-            w[i] = wi;
-            dot += wi * v[i];
+        for (int32_t e = 0; e < ls; e += 4) {
+            const int4 k = __ldg(reinterpret_cast<const int4 *>(idx + eo + e));
+            const double x0 = __ldg(v + k.x), x1 = __ldg(v + k.y), x2 = __ldg(v + k.z), x3 = __ldg(v + k.w);
+            if (sval) {
+                const float4 c = __ldg(reinterpret_cast<const float4 *>(sval + eo + e));
+                acc += (double)c.x * x0;
+                acc += (double)c.y * x1;
+                acc += (double)c.z * x2;
+                acc += (double)c.w * x3;
+            } else {
+                acc += x0;
+                acc += x1;
+                acc += x2;
+                acc += x3;
+            }
         }
+        const double vi = v[i];
+        const double wi = strength[i] * vi - acc;
+        w[i] = wi;
+        dot += wi * vi;
     }
     block_dot_store<256>(dot, part);
 }
@@ -196,10 +212,19 @@ SF_API sf_status sf_lambda_max_estimate(const sf_graph *g, int32_t iters, const 
            *nrm = nullptr;
     sf_status st;
     const int grid = 4 * sm_count();
-    if ((st = sc.get(&v, n)) || (st = sc.get(&vp, n)) || (st = sc.get(&w, n)) || (st = sc.get(&part, grid)) ||
-        (st = sc.get(&alpha, iters)) || (st = sc.get(&beta, iters)) || (st = sc.get(&nrm, 1)))
+    // one extra element, kept 0: the padding entries of the sliced-ELL copy gather v[n]
+    if ((st = sc.get(&v, (size_t)n + 1)) || (st = sc.get(&vp, (size_t)n + 1)) || (st = sc.get(&w, (size_t)n + 1)) ||
+        (st = sc.get(&part, grid)) || (st = sc.get(&alpha, iters)) || (st = sc.get(&beta, iters)) ||
+        (st = sc.get(&nrm, 1)))
         return st;
-    const float *val = g->unit_weights ? nullptr : g->val;
+    SF_CHECK_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * ((size_t)n + 1), s));
+    SF_CHECK_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * ((size_t)n + 1), s));
+    SF_CHECK_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * ((size_t)n + 1), s));
+    {
+        std::lock_guard<std::mutex> lk(g->sell_mu);
+        if ((st = sell_build(&g->sell, g->n, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, s))) return st;
+    }
+    const SellMatrix &S = g->sell;
     lanczos_init_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, v0, seed, n);
     if ((st = check_launch("lanczos_init_kernel"))) return st;
     sumsq_kernel<<<grid, 256, 0, s>>>(n, w, part);
@@ -209,8 +234,8 @@ SF_API sf_status sf_lambda_max_estimate(const sf_graph *g, int32_t iters, const 
     lanczos_scale_kernel<<<grid, 256, 0, s>>>(n, w, nrm, 0, v);
     if ((st = check_launch("lanczos_scale_kernel"))) return st;
     for (int k = 0; k < iters; ++k) {
-        lap_spmv_f64_kernel<<<grid, 256, 0, s>>>(n, g->rowptr, g->colidx, val, g->strength, v, w, part);
-        if ((st = check_launch("lap_spmv_f64_kernel"))) return st;
+        lap_spmv_sell_kernel<<<grid, 256, 0, s>>>(n, S.sptr, S.perm, S.idx, S.val, g->strength, v, w, part);
+        if ((st = check_launch("lap_spmv_sell_kernel"))) return st;
         lanczos_scalar_kernel<<<1, 256, 0, s>>>(part, grid, alpha, k, 0);
         if ((st = check_launch("lanczos_scalar_kernel"))) return st;
         if (k + 1 == iters) break;

@@ -291,7 +291,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // processed. Tiles whose entries do not fit read the indices from global
 // memory. Lane group g (LPR lanes, 16 bytes each) owns tile rows g, g + G,
 // ...; the groups of one warp share a slice, so their trip counts match.
-constexpr int kSliceRows = 8;
 
 template <int LPR>
 struct TileCfg {
