@@ -120,6 +120,16 @@ def make_inputs(wl, rank=0):
     return gr, R
 
 
+def make_count_signals(wl, rank=0):
+    """The eigenvalue count's own probe block (§4.1 draws the filtered signals
+    R in step 4, after lambda_k is estimated in step 2): same law, other seed."""
+    from paper_1509_08863_gb300 import synth
+
+    Rc = synth.standard_normal_block(wl["n"], wl["R"], seed=wl["r_seed"] + 1 + 7919 * rank)
+    Rc /= np.sqrt(wl["R"])
+    return Rc
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -291,7 +301,8 @@ def main():
     src_h = torch.from_numpy(gr.src).pin_memory()
     dst_h = torch.from_numpy(gr.dst).pin_memory()
     R_h = torch.from_numpy(R.astype(np.float32)).pin_memory()
-    src_d, dst_d, R_d = src_h.to(dev), dst_h.to(dev), R_h.to(dev)
+    Rc_h = torch.from_numpy(make_count_signals(wl, rank).astype(np.float32)).pin_memory()
+    src_d, dst_d, R_d, Rc_d = src_h.to(dev), dst_h.to(dev), R_h.to(dev), Rc_h.to(dev)
     stream = torch.cuda.current_stream()
 
     # tile shapes from the autotuner (untimed; cached per graph size)
@@ -307,15 +318,16 @@ def main():
                        blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window,
                        sweep_kernel=t.sweep_kernel)
 
-    def step(src, dst, Rt, st, collect=None):
-        """One pass of the path; `st` is the block storage of both sweeps (FP16
-        applies to the filter, whose moments then use BF16 blocks)."""
+    def step(src, dst, Rc, Rt, st, collect=None):
+        """One pass of the path: the count's moments on the probe block Rc, the
+        filter on R. `st` is the block storage of both sweeps (FP16 applies to
+        the filter, whose moments then use BF16 blocks)."""
         g = sf.csr_build(n, src, dst, None)
         _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
         mst = sf.BF16 if st == sf.F16 else st
         if mst not in tuned:
             tuned[mst] = sf.autotune(g, eta, mst, 1)
-        mu = sf.cheb_moments(g, lh, Rt, p, opts_for(mst))
+        mu = sf.cheb_moments(g, lh, Rc, p, opts_for(mst))
         if dist:  # columns are sharded over ranks: moments add up
             mu = sharded.combine_moments(mu, device=dev)
         lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
@@ -333,7 +345,7 @@ def main():
         return F
 
     info = {}
-    F = step(src_d, dst_d, R_d, storage, info)
+    F = step(src_d, dst_d, Rc_d, R_d, storage, info)
     torch.cuda.synchronize()
     nnz = info["nnz"]
     updates = 2.0 * (nnz + n) * eta * p
@@ -342,10 +354,10 @@ def main():
         for _ in range(warmup):
             if e2e:
                 out = step(src_h.to(dev, non_blocking=True), dst_h.to(dev, non_blocking=True),
-                           R_h.to(dev, non_blocking=True), st)
+                           Rc_h.to(dev, non_blocking=True), R_h.to(dev, non_blocking=True), st)
                 out.cpu()
             else:
-                step(src_d, dst_d, R_d, st)
+                step(src_d, dst_d, Rc_d, R_d, st)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -359,10 +371,10 @@ def main():
         for _ in range(steps):
             if e2e:
                 out = step(src_h.to(dev, non_blocking=True), dst_h.to(dev, non_blocking=True),
-                           R_h.to(dev, non_blocking=True), st)
+                           Rc_h.to(dev, non_blocking=True), R_h.to(dev, non_blocking=True), st)
                 host_out.copy_(out, non_blocking=True)
             else:
-                step(src_d, dst_d, R_d, st)
+                step(src_d, dst_d, Rc_d, R_d, st)
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -377,7 +389,7 @@ def main():
     # main timed region (device-resident inputs) with kernel timing and clocks
     clk = ClockSampler(local if world == 1 else int(os.environ.get("LOCAL_RANK", "0")))
     for _ in range(args.warmup):
-        step(src_d, dst_d, R_d, storage)
+        step(src_d, dst_d, Rc_d, R_d, storage)
     torch.cuda.synchronize()
     clk.start()
     sf.profile_begin()
@@ -404,7 +416,8 @@ def main():
     if not args.no_e2e:
         mse, _ = timed(storage, max(3, args.steps // 2), 1, e2e=True)
         e2e = {"value": updates * world / (mse * 1e-3), "unit": "updates/s",
-               "h2d_bytes_per_step": int(src_h.numel() * 4 + dst_h.numel() * 4 + R_h.numel() * 4),
+               "h2d_bytes_per_step": int(src_h.numel() * 4 + dst_h.numel() * 4 + R_h.numel() * 4 +
+                                         Rc_h.numel() * 4),
                "d2h_bytes_per_step": int(n * eta * 4)}
 
     # accuracy of this step's features/filter against the FP64 oracle on one column
@@ -420,6 +433,21 @@ def main():
     by_variant = {name: roof_of(name, *v) for name, v in variants.items()}
     dominant = max(variants.items(), key=lambda kv: kv[1][1])[0] if variants else None
     roof = by_variant.get(dominant) if dominant else None
+
+    # the gather pattern's own ceiling: random rows of the slab width from a block
+    # of N rows, timed alone (untimed by the step clock)
+    gather = None
+    st_b = 2 if storage != sf.F32 else 4
+    t_main = tuned.get(storage)
+    if t_main is not None and t_main.slab_cols * st_b in (32, 64, 128, 256):
+        rb = t_main.slab_cols * st_b
+        deg = max(4, int(round(nnz / n / 4.0)) * 4)
+        rps = sf.gather_ceiling(n, rb, deg, 10)
+        at_ceiling = nnz / rps * 1e3
+        gather = {"rows_per_s": rps, "row_bytes": rb, "table_rows": n, "deg": deg,
+                  "launch_ms_at_ceiling": at_ceiling,
+                  "frac_of_ceiling": {name: at_ceiling / v["avg_launch_ms"] for name, v in by_variant.items()},
+                  "note": "sf_gather_ceiling: the sweep's random-row gathers alone (nnz_off rows per launch)"}
 
     result = {
         "metric": "filtered nnz*R*p updates/s",
@@ -442,11 +470,13 @@ def main():
                                                                   "sweep_kernel": ("auto", "tiled", "direct")[v.sweep_kernel]}
                              for k, v in tuned.items()},
                    "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
+                   "signals": "the count's probe block and the filtered block R are drawn independently (N(0, 1/R) each)",
                    "parallelism": (f"column shards x{world}: each rank filters its own {wl['R']} signals of one "
                                    f"{wl['R'] * world}-signal block; moments and row norms all-reduced")
                    if world > 1 else "single GPU"},
         "gpu_launches": launches,
         "roofline": roof,
+        "gather_ceiling": gather,
         "roofline_by_variant": by_variant,
         "clocks": clocks,
         "e2e": e2e,

@@ -431,6 +431,27 @@ SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
  */
 SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes);
 
+/*
+ * Measured ceiling of the sweep's gather pattern. A diagnostic with no
+ * counterpart in the paper: it times a kernel that does nothing but the
+ * sweep's data movement without its arithmetic -- for every output row, sum
+ * (in FP32) `deg` uniformly random rows of a synthetic BF16 table of
+ * n_rows + 1 rows of row_bytes bytes, with lane groups of row_bytes / 16
+ * lanes, eight 16-byte gathers in flight per lane, indices read from memory,
+ * FP32 sums written out -- so a sweep launch's duration can be set against
+ * what the memory system delivers for the same random-row pattern.
+ *   n_rows      table rows and output rows (1 .. 2^31 - 2)
+ *   row_bytes   32, 64, 128 or 256
+ *   deg         entries per output row: a multiple of 4 in [4, 256]
+ *   reps        timed launches (>= 1) after two untimed ones
+ *   rows_per_s  out: gathered rows per second (mean over the timed launches)
+ * Allocates and frees its own buffers: (n_rows + 1) * row_bytes (table),
+ * n_rows * deg * 4 (indices), n_rows * row_bytes * 2 (sums). Synchronises
+ * `stream`.
+ */
+SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps, void *stream,
+                                   double *rows_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -154,6 +154,7 @@ def lib():
         "sf_cheb_moments_noalloc": (_i32, [_vp, _f64, _vp, _i32, _i32, _dp, _vp]),
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
         "sf_profile_variant": (_i32, [_i32, C.POINTER(_i64), _dp, _dp]),
+        "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -510,6 +511,15 @@ def profile_end():
     n, ms, by = _i64(), _f64(), _f64()
     _check(lib().sf_profile_end(C.byref(n), C.byref(ms), C.byref(by)), "sf_profile_end")
     return n.value, ms.value, by.value
+
+
+def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> float:
+    """Rows per second of the sweep's random-row gather pattern alone (synthetic
+    BF16 table of n_rows + 1 rows of row_bytes bytes, deg entries per row)."""
+    r = _f64()
+    _check(lib().sf_gather_ceiling(int(n_rows), int(row_bytes), int(deg), int(reps), _stream(), C.byref(r)),
+           "sf_gather_ceiling")
+    return r.value
 
 
 def device_check():

@@ -303,7 +303,11 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         if (tol_dev) tol = const_cast<double *>(tol_dev);
         else if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
     }
-    if (mode == MODE_MOM && (st = sc.get(&part, (size_t)2 * sh.grid + 2))) return st;
+    uint32_t *done = nullptr;
+    if (mode == MODE_MOM) {
+        if ((st = sc.get(&part, (size_t)2 * sh.grid + 2)) || (st = sc.get(&done, 1))) return st;
+        SF_CHECK_CUDA(cudaMemsetAsync(done, 0, sizeof(uint32_t), s));
+    }
     // FP16 blocks: each slab is scaled by a power of two so that its largest
     // magnitude lies in (1/2, 1]; the filter is linear, so the output is
     // unscaled exactly at unpack time
@@ -376,11 +380,11 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 P.m = (j == 1) ? 1.0f : 2.0f;
                 P.j = j;
                 double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false);
-                if ((st = launch_step(sh, mode, P, s, by))) return st;
-                if (mode == MODE_MOM) {
-                    pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 2, mom + 2 * j);
-                    if ((st = check_launch("pair_sum_kernel"))) return st;
+                if (mode == MODE_MOM) {  // the kernel's last block adds <T_j,T_j>, <T_j,T_{j-1}> into mom
+                    P.dots = mom + 2 * j;
+                    P.done = done;
                 }
+                if ((st = launch_step(sh, mode, P, s, by))) return st;
             }
         } else {
             // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};

@@ -1,0 +1,143 @@
+// Gather ceiling (sf_gather_ceiling): the sweep kernel's random-row data
+// movement alone, timed on synthetic data, as the practical ceiling its
+// launches are compared with.
+#include <math.h>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+__device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
+    // SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014)
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// table: hashed BF16 values in [-0.5, 0.5), last row zero
+__global__ void probe_fill_table(uint16_t *T, int64_t rows, int32_t cols) {
+    const int64_t total = rows * cols;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (t / cols == rows - 1) ? 0.0f : (float)(probe_mix((uint64_t)t) & 0xffff) / 65536.0f - 0.5f;
+        T[t] = (uint16_t)(__float_as_uint(v) >> 16);
+    }
+}
+
+__global__ void probe_fill_idx(int32_t *idx, int64_t count, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        idx[t] = (int32_t)(probe_mix((uint64_t)t + 0x5851F42D4C957F2Dull) % (uint64_t)n);
+}
+
+__device__ __forceinline__ void probe_add(float (&acc)[8], const uint4 v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        acc[2 * i] += __uint_as_float(w[i] << 16);
+        acc[2 * i + 1] += __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(256, 4) probe_gather_kernel(const uint16_t *T, const int32_t *idx, int64_t n_out,
+                                                              int32_t deg, float *out) {
+    constexpr int COLS = LPR * 8;  // BF16 columns per row
+    constexpr int RPB = 256 / LPR;
+    const int q = threadIdx.x % LPR, grp = threadIdx.x / LPR;
+    for (int64_t row = (int64_t)blockIdx.x * RPB + grp; row < n_out; row += (int64_t)gridDim.x * RPB) {
+        const int32_t *ip = idx + row * deg;
+        float acc[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] = 0.f;
+        int32_t j = 0;
+        for (; j + 8 <= deg; j += 8) {
+            const int4 a = __ldg(reinterpret_cast<const int4 *>(ip + j));
+            const int4 b = __ldg(reinterpret_cast<const int4 *>(ip + j + 4));
+            const int32_t k[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            uint4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = __ldg(reinterpret_cast<const uint4 *>(T + (int64_t)k[u] * COLS + q * 8));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) probe_add(acc, x[u]);
+        }
+        if (j < deg) {  // deg is a multiple of 4
+            const int4 a = __ldg(reinterpret_cast<const int4 *>(ip + j));
+            const int32_t k[4] = {a.x, a.y, a.z, a.w};
+            uint4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                x[u] = __ldg(reinterpret_cast<const uint4 *>(T + (int64_t)k[u] * COLS + q * 8));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) probe_add(acc, x[u]);
+        }
+        float4 *o = reinterpret_cast<float4 *>(out + row * COLS + q * 8);
+        __stcs(o, make_float4(acc[0], acc[1], acc[2], acc[3]));
+        __stcs(o + 1, make_float4(acc[4], acc[5], acc[6], acc[7]));
+    }
+}
+
+template <int LPR>
+static void probe_launch(int grid, cudaStream_t s, const uint16_t *T, const int32_t *idx, int64_t n, int32_t deg,
+                         float *out) {
+    probe_gather_kernel<LPR><<<grid, 256, 0, s>>>(T, idx, n, deg, out);
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps,
+                                              void *stream, double *rows_per_s) {
+    SF_ARG(rows_per_s, "rows_per_s is NULL");
+    SF_ARG(n_rows >= 1 && n_rows <= (1ll << 31) - 2, "n_rows must be in [1, 2^31 - 2]");
+    SF_ARG(row_bytes == 32 || row_bytes == 64 || row_bytes == 128 || row_bytes == 256,
+           "row_bytes must be 32, 64, 128 or 256");
+    SF_ARG(deg >= 4 && deg <= 256 && deg % 4 == 0, "deg must be a multiple of 4 in [4, 256]");
+    SF_ARG(reps >= 1, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cols = row_bytes / 2;
+    Scratch sc(s);
+    uint16_t *T = nullptr;
+    int32_t *idx = nullptr;
+    float *out = nullptr;
+    sf_status st;
+    if ((st = sc.get(&T, (size_t)(n_rows + 1) * cols)) || (st = sc.get(&idx, (size_t)n_rows * deg)) ||
+        (st = sc.get(&out, (size_t)n_rows * cols)))
+        return st;
+    const int fill_grid = 8 * sm_count();
+    probe_fill_table<<<fill_grid, 256, 0, s>>>(T, n_rows + 1, cols);
+    if ((st = check_launch("probe_fill_table"))) return st;
+    probe_fill_idx<<<fill_grid, 256, 0, s>>>(idx, n_rows * deg, n_rows);
+    if ((st = check_launch("probe_fill_idx"))) return st;
+    const int grid = 4 * sm_count();
+    auto launch = [&]() {
+        switch (row_bytes) {
+            case 32: probe_launch<2>(grid, s, T, idx, n_rows, deg, out); break;
+            case 64: probe_launch<4>(grid, s, T, idx, n_rows, deg, out); break;
+            case 128: probe_launch<8>(grid, s, T, idx, n_rows, deg, out); break;
+            default: probe_launch<16>(grid, s, T, idx, n_rows, deg, out); break;
+        }
+        return check_launch("probe_gather_kernel");
+    };
+    for (int i = 0; i < 2; ++i)
+        if ((st = launch())) return st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    SF_CHECK_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    cudaEventRecord(a, s);
+    for (int i = 0; i < reps && st == SF_OK; ++i) st = launch();
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "timing the gather ceiling");
+    *rows_per_s = (double)n_rows * deg * reps / ((double)ms * 1e-3);
+    return SF_OK;
+}

@@ -234,6 +234,8 @@ struct StepParams {
     int32_t j;              // coefficient index used by this order
     // moments
     double *part;           // [gridDim.x][2]: sum t.t, sum t.x
+    double *dots;           // when set: the last block adds the block partials into dots[0..1]
+    uint32_t *done;         // blocks finished (zero before the launch; the last block resets it)
     int32_t *status;        // device error word (bit 0: a bounded wait gave up)
 };
 
@@ -450,29 +452,61 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t i, int q,
     }
 }
 
-// Moment sums of the block in a fixed order (lanes of a warp, then warps)
-// into part[2 * blockIdx.x + {0, 1}]. Every thread of the block calls it.
-__device__ __forceinline__ void block_moments(const StepParams &P, double mtt, double mtx) {
-    __shared__ double s_red[32][2];
+// Sum over the block of (a, b) in a fixed order (lanes of a warp, then warps);
+// the result is valid in thread 0. Every thread of the block calls it.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*s_red)[2]) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        mtt += __shfl_xor_sync(0xffffffffu, mtt, off);
-        mtx += __shfl_xor_sync(0xffffffffu, mtx, off);
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
     }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        s_red[w][0] = mtt;
-        s_red[w][1] = mtx;
+        s_red[w][0] = a;
+        s_red[w][1] = b;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        a = 0.0;
+        b = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
             a += s_red[k][0];
             b += s_red[k][1];
         }
-        P.part[2 * blockIdx.x] = a;
-        P.part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Moment sums of the block into part[2 * blockIdx.x + {0, 1}]. With P.dots
+// set, the block that finishes last adds all block partials, in block order
+// (deterministic whichever block is last), into dots[0] and dots[1] and
+// resets the counter: no separate reduction launch per order.
+__device__ __forceinline__ void block_moments(const StepParams &P, double mtt, double mtx) {
+    __shared__ double s_red[32][2];
+    __shared__ int s_last;
+    block_sum2(mtt, mtx, s_red);
+    if (threadIdx.x == 0) {
+        P.part[2 * blockIdx.x] = mtt;
+        P.part[2 * blockIdx.x + 1] = mtx;
+        if (P.dots) {
+            __threadfence();  // the partial is visible before the block counts as done
+            s_last = (atomicAdd(P.done, 1u) == gridDim.x - 1) ? 1 : 0;
+        }
+    }
+    if (!P.dots) return;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        a += __ldcg(P.part + 2 * k);
+        b += __ldcg(P.part + 2 * k + 1);
+    }
+    __syncthreads();  // s_red is reused
+    block_sum2(a, b, s_red);
+    if (threadIdx.x == 0) {
+        P.dots[0] += a;
+        P.dots[1] += b;
+        *P.done = 0u;
     }
 }
 

@@ -537,3 +537,11 @@ def test_autotune_and_profile(sf, oracle_mod):
     n_l, ms, by = sf.profile_end()
     assert n_l == 10 and ms > 0 and by > 0
     assert sf.launch_count() - n0 >= 12
+
+
+def test_gather_ceiling_diagnostic(sf):
+    r = sf.gather_ceiling(100_000, 64, 32, 2)
+    assert np.isfinite(r) and r > 1e9  # rows per second
+    for bad in ((0, 64, 32), (1000, 48, 32), (1000, 64, 30), (1000, 64, 0)):
+        with pytest.raises(sf.SpecFiltError):
+            sf.gather_ceiling(*bad, 1)
