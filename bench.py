@@ -350,6 +350,10 @@ def main():
     nnz = info["nnz"]
     updates = 2.0 * (nnz + n) * eta * p
 
+    # inputs smaller than L2: overwrite a buffer larger than L2 between timed steps
+    in_bytes = 4 * (src_h.numel() + dst_h.numel() + R_h.numel() + Rc_h.numel())
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device=dev) if in_bytes < (256 << 20) else None
+
     def timed(st, steps, warmup, e2e=False):
         for _ in range(warmup):
             if e2e:
@@ -363,23 +367,24 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         host_out = torch.empty((n, eta), dtype=torch.float32).pin_memory() if e2e else None
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         l0 = sf.launch_count()
         torch.cuda.nvtx.range_push("timed")
-        e0.record(stream)
-        for _ in range(steps):
+        for i in range(steps):
+            ev[i][0].record(stream)
             if e2e:
                 out = step(src_h.to(dev, non_blocking=True), dst_h.to(dev, non_blocking=True),
                            Rc_h.to(dev, non_blocking=True), R_h.to(dev, non_blocking=True), st)
                 host_out.copy_(out, non_blocking=True)
             else:
                 step(src_d, dst_d, Rc_d, R_d, st)
-        e1.record(stream)
+            ev[i][1].record(stream)
+            if flush is not None:  # between steps, outside the timed spans
+                flush.add_(1)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         launches = sf.launch_count() - l0
-        ms = e0.elapsed_time(e1) / steps
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
         if dist:
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -469,7 +474,9 @@ def main():
                                                                   "carveout_pct": v.carveout_pct, "l2_window": v.l2_window,
                                                                   "sweep_kernel": ("auto", "tiled", "direct")[v.sweep_kernel]}
                              for k, v in tuned.items()},
-                   "sweeps_per_step": 2, "l2": "inputs larger than L2 (no flush)",
+                   "sweeps_per_step": 2,
+                   "l2": ("inputs larger than L2 (no flush)" if flush is None else
+                          "inputs smaller than L2: a 256 MB buffer is overwritten between timed steps"),
                    "signals": "the count's probe block and the filtered block R are drawn independently (N(0, 1/R) each)",
                    "parallelism": (f"column shards x{world}: each rank filters its own {wl['R']} signals of one "
                                    f"{wl['R'] * world}-signal block; moments and row norms all-reduced")
@@ -495,23 +502,29 @@ def main():
     return 0
 
 
-def _clock_timed(fn, steps, warmup, sf):
+def _clock_timed(fn, steps, warmup, sf, flush_l2=False):
+    """Mean device time of fn over `steps` calls (CUDA events around each call);
+    with flush_l2, a 256 MB buffer is overwritten between calls, outside the
+    timed spans (for inputs smaller than L2)."""
     import torch
 
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device="cuda") if flush_l2 else None
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
     sf.profile_begin()
     l0 = sf.launch_count()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.nvtx.range_push("timed")
-    e0.record(stream)
-    for _ in range(steps):
+    for i in range(steps):
+        ev[i][0].record(stream)
         fn()
-    e1.record(stream)
+        ev[i][1].record(stream)
+        if flush is not None:
+            flush.add_(1)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = sf.launch_count() - l0
@@ -519,7 +532,7 @@ def _clock_timed(fn, steps, warmup, sf):
     variants = sf.profile_variants()
     clocks = clk.stop()
     sf.device_check()
-    return e0.elapsed_time(e1) / steps, launches, variants, clocks
+    return sum(a.elapsed_time(b) for a, b in ev) / steps, launches, variants, clocks
 
 
 def _roof_variants(variants, workload):
@@ -566,7 +579,7 @@ def run_knn_grad(args, wl):
         sf.cheb_filter(g, lh, a[None, :], R, opts)
         sf.cheb_filter_backward(g, lh, a, R, G, False, opts)
 
-    ms, launches, variants, clocks = _clock_timed(step, args.steps, args.warmup, sf)
+    ms, launches, variants, clocks = _clock_timed(step, args.steps, args.warmup, sf, flush_l2=True)
     updates = 3.0 * (nnz + n) * eta * p
     roof, by_variant = _roof_variants(variants, args.workload)
     # directional finite difference at full size: l(W + h D) - l(W - h D) vs <grad, D>
@@ -600,7 +613,8 @@ def run_knn_grad(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "knn200k", "N": n, "nnz_off": nnz, "R": eta, "p": p, "k_nn": wl["knn"],
                    "sigma": wl["sigma"], "step": "filter + backward (edge weights, coefficients)",
-                   "sweeps_per_step": 3},
+                   "sweeps_per_step": 3,
+                   "l2": "inputs smaller than L2: a 256 MB buffer is overwritten between timed steps"},
         "gpu_launches": launches, "roofline": roof, "roofline_by_variant": by_variant, "clocks": clocks,
         "e2e": None,
         "gradient_check": {"directional_fd": fd, "adjoint": an, "rel_diff": abs(fd - an) / max(abs(fd), 1e-300),
@@ -683,7 +697,10 @@ def run_batch(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch256", "graphs": ng, "N_total": n_tot, "nnz_off_total": nnz_sum, "R": eta,
                    "p": p, "block_storage": wl["storage"], "tiles": {"slab_cols": tuned.slab_cols,
-                                                                     "block_warps": tuned.block_warps}},
+                                                                     "block_warps": tuned.block_warps,
+                                                                     "sweep_kernel": ("auto", "tiled", "direct")[
+                                                                         tuned.sweep_kernel]},
+                   "l2": "inputs larger than L2 (no flush)"},
         "gpu_launches": launches_b, "roofline": roof, "roofline_by_variant": by_variant, "clocks": clocks,
         "e2e": None,
         "sequential": {"value": updates / (ms_s * 1e-3), "ms_per_step": ms_s, "gpu_launches": launches_s,
