@@ -318,27 +318,41 @@ def main():
                        blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window,
                        sweep_kernel=t.sweep_kernel)
 
-    def step(src, dst, Rc, Rt, st, collect=None):
+    def step(src, dst, Rc, Rt, st, collect=None, marks=None):
         """One pass of the path: the count's moments on the probe block Rc, the
         filter on R. `st` is the block storage of both sweeps (FP16 applies to
-        the filter, whose moments then use BF16 blocks)."""
+        the filter, whose moments then use BF16 blocks). `marks`, when given,
+        collects (stage, CUDA event) pairs after each stage."""
+        def mark(name):
+            if marks is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append((name, e))
+
+        mark("start")
         g = sf.csr_build(n, src, dst, None)
+        mark("csr_build")
         _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
+        mark("lambda_max_estimate")
         mst = sf.BF16 if st == sf.F16 else st
         if mst not in tuned:
             tuned[mst] = sf.autotune(g, eta, mst, 1)
         mu = sf.cheb_moments(g, lh, Rc, p, opts_for(mst))
         if dist:  # columns are sharded over ranks: moments add up
             mu = sharded.combine_moments(mu, device=dev)
+        mark("cheb_moments")
         lk = sf.dichotomy(mu, p, lh, k - 0.5, True, 40, 1e-9)
         a = sf.cheb_coeffs(lh, lk, p, True)
+        mark("dichotomy_and_coeffs")
         if st not in tuned:
             tuned[st] = sf.autotune(g, eta, st, 1)
         Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st, filter_algo))[0]
+        mark("cheb_filter")
         if dist:  # row norms run over every rank's columns
             F = sharded.normalize_rows_sharded(Y, sf.row_sumsq, lambda y, tot: sf.features_scaled(y, tot, out=y))
         else:
             F = sf.features(Y, True, out=Y)
+        mark("features")
         if collect is not None:
             collect.update(lam_hat=lh, lam_k=lk, nnz=g.nnz, Y=Y)
         g.free()
@@ -404,6 +418,12 @@ def main():
     clocks = clk.stop()
     sf.device_check()
     value = updates * world / (ms * 1e-3)
+
+    # where one step's device time goes (one extra, untimed step with events between stages)
+    marks = []
+    step(src_d, dst_d, Rc_d, R_d, storage, marks=marks)
+    torch.cuda.synchronize()
+    stages = {name: marks[i - 1][1].elapsed_time(e) for i, (name, e) in enumerate(marks) if i > 0}
 
     # the same run with FP32 blocks in both sweeps
     fp32 = None
@@ -484,6 +504,7 @@ def main():
         "gpu_launches": launches,
         "roofline": roof,
         "gather_ceiling": gather,
+        "stages_ms": stages,
         "roofline_by_variant": by_variant,
         "clocks": clocks,
         "e2e": e2e,

@@ -124,7 +124,7 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     const StepFn fn = kernel_for(sh.storage, sh.lpr, mode, sh.weighted, sh.direct);
     SF_ARG(fn, "no kernel for this shape");
     cudaEvent_t ea = nullptr, eb = nullptr;
-    const bool prof = profiling_on() && profile_events(&ea, &eb);
+    const bool prof = profiling_on() && !profile_span_active() && profile_events(&ea, &eb);
     if (prof) cudaEventRecord(ea, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sh.grid);
@@ -373,6 +373,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 if ((st = check_launch("pair_sum_kernel"))) return st;
             }
             // orders 1..p: buffer of T_j is j % 3
+            ProfSpan span(s, mode * 3 + o.storage);
             for (int j = 1; j <= p; ++j) {
                 P.X = buf[(j - 1) % 3];
                 P.Z = (j >= 2) ? buf[(j - 2) % 3] : nullptr;
@@ -385,6 +386,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                     P.done = done;
                 }
                 if ((st = launch_step(sh, mode, P, s, by))) return st;
+                span.add(by);
             }
         } else {
             // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};
@@ -393,6 +395,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                                   0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr, maxbits)))
                 return st;
             P.Q = qbuf;
+            ProfSpan span(s, MODE_CLEN * 3 + o.storage);
             for (int j = p - 1; j >= 0; --j) {
                 // b_j lives in buffer j % 3; b_{j+1}, b_{j+2} in the other two
                 P.X = buf[(j + 1) % 3];
@@ -409,6 +412,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 }
                 double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, MODE_CLEN, j + 2 <= p, 1, j == 0);
                 if ((st = launch_step(sh, MODE_CLEN, P, s, by))) return st;
+                span.add(by);
             }
             if (p == 0) {
                 // Y = a_0 R: b_0 computed by the pack as a_p R with p = 0, widen to fp32

@@ -236,9 +236,10 @@ double tridiag_max_eig_host(int k, const double *a, const double *b) {
 
 // ---------------------------------------------------------------- profiling
 struct ProfRec {
-    int ev;        // index of the first event of the pair
-    double bytes;  // algorithmic bytes of the launch
-    int tag;       // kernel variant
+    int ev;            // index of the first event of the pair
+    double bytes;      // algorithmic bytes of the launches
+    int tag;           // kernel variant
+    int64_t launches;  // launches between the two events
 };
 struct ProfTotals {
     int64_t launches = 0;
@@ -273,14 +274,18 @@ bool profile_events(cudaEvent_t *a, cudaEvent_t *b) {
     return true;
 }
 
-void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag) {
+void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag, int64_t launches) {
     ProfState &P = prof();
     std::lock_guard<std::mutex> lk(P.mu);
     (void)a;
     (void)b;
-    P.recs.push_back({(int)P.used, bytes, (tag >= 0 && tag < kProfTags) ? tag : 0});
+    P.recs.push_back({(int)P.used, bytes, (tag >= 0 && tag < kProfTags) ? tag : 0, launches});
     P.used += 2;
 }
+
+static thread_local bool t_span = false;
+bool profile_span_active() { return t_span; }
+void profile_span_set(bool on) { t_span = on; }
 
 }  // namespace sf
 
@@ -368,6 +373,7 @@ SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes) {
     std::lock_guard<std::mutex> lk(P.mu);
     P.on = false;
     double tot = 0.0, by = 0.0;
+    int64_t n_launch = 0;
     for (auto &t : P.last) t = ProfTotals();
     for (auto &r : P.recs) {
         cudaEvent_t a = P.pool[r.ev], b = P.pool[r.ev + 1];
@@ -378,11 +384,12 @@ SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
         tot += t;
         by += r.bytes;
-        P.last[r.tag].launches += 1;
+        n_launch += r.launches;
+        P.last[r.tag].launches += r.launches;
         P.last[r.tag].ms += t;
         P.last[r.tag].bytes += r.bytes;
     }
-    if (launches) *launches = (int64_t)P.recs.size();
+    if (launches) *launches = n_launch;
     if (ms) *ms = tot;
     if (bytes) *bytes = by;
     P.recs.clear();

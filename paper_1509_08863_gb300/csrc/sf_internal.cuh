@@ -79,8 +79,38 @@ sf_status reduce_sum_f64(const double *in, int64_t count, double *out, cudaStrea
 constexpr int kProfTags = 10;
 constexpr int kProfTagAdjoint = 9;  // the adjoint's fused Clenshaw + sampled-product kernel
 bool profiling_on();
-void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag);
+void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag, int64_t launches = 1);
 bool profile_events(cudaEvent_t *a, cudaEvent_t *b);
+// A span times a run of consecutive launches of one kernel variant with one
+// pair of events (per-launch events would add a bubble between launches);
+// launches made while a span is open on this thread record no events.
+bool profile_span_active();
+void profile_span_set(bool on);
+struct ProfSpan {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s = nullptr;
+    bool on = false;
+    int tag = 0;
+    int64_t launches = 0;
+    double bytes = 0.0;
+    ProfSpan(cudaStream_t st, int t) : s(st), tag(t) {
+        on = profiling_on() && !profile_span_active() && profile_events(&a, &b);
+        if (on) {
+            cudaEventRecord(a, s);
+            profile_span_set(true);
+        }
+    }
+    void add(double by) {
+        ++launches;
+        bytes += by;
+    }
+    ~ProfSpan() {
+        if (!on) return;
+        profile_span_set(false);
+        cudaEventRecord(b, s);
+        profile_record(a, b, bytes, tag, launches);
+    }
+};
 
 // ---------------------------------------------------------------- host math
 void cheb_coeffs_host(double lam_max, double lc, int p, int jackson, double *a);
