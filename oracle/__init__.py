@@ -13,6 +13,8 @@ follows. Parity status:
   moments, eigencount, features, cheb_filter_backward: pinned (CPU tests).
 * dichotomy: parity unpinned beyond self-consistency (the paper prints no
   estimate of lambda_k to compare with).
+* kmeans: pinned (brute-force argmin, numpy means, separated clusters,
+  monotone inertia, ties).
 """
 from __future__ import annotations
 
@@ -31,6 +33,7 @@ _lock = threading.Lock()
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +80,9 @@ def _load():
                                          C.c_int64, _f64p, C.c_double, C.c_int32, C.c_double]
         lib.oracle_features.restype = None
         lib.oracle_features.argtypes = [C.c_int32, C.c_int64, _f64p, C.c_int32, _f64p]
+        lib.oracle_kmeans.restype = C.c_double
+        lib.oracle_kmeans.argtypes = [C.c_int32, C.c_int32, C.c_int32, _f32p, _f32p, C.c_int32, _i32p,
+                                      C.POINTER(C.c_int32)]
         lib.oracle_cheb_filter_backward.restype = None
         lib.oracle_cheb_filter_backward.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32,
                                                     _f64p, C.c_int64, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
@@ -256,3 +262,22 @@ def count_from_moments(mu, coeffs) -> np.ndarray:
                 s += a[q, j] * a[q, jj] * 0.5 * (mu[j + jj] + mu[abs(j - jj)])
         out[q] = s
     return out
+
+
+def kmeans(F, C0, max_iter: int):
+    """Lloyd's k-means (§4.1 step 6, Euclidean distance between feature rows)
+    from the initial centroids C0 (k x d): returns (labels int32[n], centroids
+    float32[k x d], assignments performed, inertia of the last assignment).
+    Distances are FP32 sums of fused multiply-adds in index order (the
+    precision in which the GPU takes the same decision), ties to the lowest
+    centroid; centroid means are FP64 sums in row order, rounded to FP32."""
+    lib = _load()
+    F = np.ascontiguousarray(F, dtype=np.float32)
+    cent = np.array(C0, dtype=np.float32, copy=True, order="C")
+    n, d = F.shape
+    k = cent.shape[0]
+    assert cent.shape[1] == d
+    labels = np.full(n, -1, np.int32)
+    iters = C.c_int32(0)
+    inertia = lib.oracle_kmeans(n, d, k, F, cent, int(max_iter), labels, C.byref(iters))
+    return labels, cent, iters.value, inertia

@@ -488,3 +488,74 @@ void oracle_cheb_filter_backward(int32_t n, const int32_t *rowptr, const int32_t
     if (grad_R) for (int64_t t = 0; t < sz; ++t) grad_R[t] = Gb[t];
     free(T); free(Gb); free(tmp); free(Mdiag); free(Moff);
 }
+
+/* ------------------------------------------------------------------------ */
+/* k-means on the feature rows (§4.1 step 6: k-means with the Euclidean      */
+/* distance between rows f~_i).                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Squared Euclidean distance in FP32, accumulated in index order with fused
+ * multiply-adds. The label is an integer decided by floating point, so the
+ * oracle takes that decision in the precision and order the GPU path states
+ * for it (IEEE FP32, fmaf correctly rounded). */
+static float sqdist_f32(const float *f, const float *c, int32_t d) {
+    float acc = 0.0f;
+    for (int32_t j = 0; j < d; ++j) {
+        const float t = f[j] - c[j];
+        acc = fmaf(t, t, acc);
+    }
+    return acc;
+}
+
+/* Lloyd's algorithm from the given centroids C (k x d, row-major, updated in
+ * place), rows F (n x d). Each iteration:
+ *   assignment: label_i = argmin_c sqdist_f32(f_i, c_c), ties to the lowest c;
+ *   stop if no label changed (from the second iteration on);
+ *   update: c_c = (sum of the rows labelled c, in row order, in FP64) / count,
+ *   rounded to FP32; an empty cluster keeps its centroid;
+ * at most max_iter assignments. Returns the inertia of the last assignment
+ * (sum over rows, in row order, in FP64, of the FP32 distances it used) and
+ * the number of assignments in *iters. Parity: pinned (CPU tests: brute-force
+ * argmin, numpy means, separated clusters, monotone inertia, ties). */
+double oracle_kmeans(int32_t n, int32_t d, int32_t k, const float *F, float *C, int32_t max_iter,
+                     int32_t *labels, int32_t *iters) {
+    double *sum = (double *)malloc(sizeof(double) * (size_t)k * (size_t)(d > 0 ? d : 1));
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    double inertia = 0.0;
+    int32_t it = 0;
+    while (it < max_iter) {
+        int changed = (it == 0);
+        inertia = 0.0;
+        for (int32_t i = 0; i < n; ++i) {
+            const float *f = F + (int64_t)i * d;
+            int32_t best = 0;
+            float bd = sqdist_f32(f, C, d);
+            for (int32_t c = 1; c < k; ++c) {
+                const float dc = sqdist_f32(f, C + (int64_t)c * d, d);
+                if (dc < bd) {
+                    bd = dc;
+                    best = c;
+                }
+            }
+            if (labels[i] != best) changed = 1;
+            labels[i] = best;
+            inertia += (double)bd;
+        }
+        ++it;
+        if (!changed) break;
+        for (int64_t t = 0; t < (int64_t)k * d; ++t) sum[t] = 0.0;
+        for (int32_t c = 0; c < k; ++c) cnt[c] = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t c = labels[i];
+            cnt[c] += 1;
+            for (int32_t j = 0; j < d; ++j) sum[(int64_t)c * d + j] += (double)F[(int64_t)i * d + j];
+        }
+        for (int32_t c = 0; c < k; ++c)
+            if (cnt[c] > 0)
+                for (int32_t j = 0; j < d; ++j) C[(int64_t)c * d + j] = (float)(sum[(int64_t)c * d + j] / (double)cnt[c]);
+    }
+    *iters = it;
+    free(sum);
+    free(cnt);
+    return inertia;
+}

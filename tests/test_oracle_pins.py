@@ -445,3 +445,72 @@ def test_backward_matches_finite_differences(oracle_mod):
         Rp[i, r] += h; Rm[i, r] -= h
         fd = (loss(R_=Rp) - loss(R_=Rm)) / (2 * h)
         assert abs(fd - gR[i, r]) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------------ k-means (§4.1 step 6)
+def test_kmeans_assignment_is_bruteforce_argmin_and_update_is_mean(oracle_mod):
+    """One Lloyd iteration: labels equal numpy's FP64 argmin of squared
+    distances wherever the best two candidates are not within FP32 rounding,
+    and the new centroids are the numpy means of the labelled rows."""
+    rng = np.random.default_rng(3)
+    n, d, k = 2000, 24, 9
+    F = rng.standard_normal((n, d)).astype(np.float32)
+    C0 = rng.standard_normal((k, d)).astype(np.float32)
+    labels, C1, iters, inertia = oracle_mod.kmeans(F, C0, 1)
+    assert iters == 1
+    D = ((F.astype(np.float64)[:, None, :] - C0.astype(np.float64)[None, :, :]) ** 2).sum(-1)
+    srt = np.sort(D, axis=1)
+    clear = (srt[:, 1] - srt[:, 0]) > 1e-4 * srt[:, 1]
+    assert clear.mean() > 0.99
+    np.testing.assert_array_equal(labels[clear], np.argmin(D, axis=1)[clear])
+    assert inertia == pytest.approx(D[np.arange(n), labels].sum(), rel=1e-5)
+    for c in range(k):
+        rows = F[labels == c].astype(np.float64)
+        if len(rows):
+            np.testing.assert_allclose(C1[c], rows.mean(axis=0), rtol=1e-6, atol=1e-7)
+        else:
+            np.testing.assert_array_equal(C1[c], C0[c])
+
+
+def test_kmeans_recovers_separated_clusters(oracle_mod):
+    """Points scattered tightly around k far-apart centres, started from one
+    point of each cluster: labels equal the generating clusters and centroids
+    their means after two assignments (the second changes nothing)."""
+    rng = np.random.default_rng(4)
+    k, d, per = 6, 5, 150
+    centres = rng.standard_normal((k, d)) * 50.0
+    truth = np.repeat(np.arange(k), per)
+    F = (centres[truth] + rng.standard_normal((k * per, d)) * 0.5).astype(np.float32)
+    C0 = F[np.arange(k) * per].copy()
+    labels, C, iters, _ = oracle_mod.kmeans(F, C0, 20)
+    np.testing.assert_array_equal(labels, truth)
+    assert iters == 2
+    for c in range(k):
+        np.testing.assert_allclose(C[c], F[truth == c].astype(np.float64).mean(axis=0), rtol=1e-6, atol=1e-6)
+
+
+def test_kmeans_inertia_never_increases(oracle_mod):
+    """Lloyd's iterations never increase the inertia (each step minimises it
+    over labels, then over centroids)."""
+    rng = np.random.default_rng(5)
+    F = rng.standard_normal((1500, 8)).astype(np.float32)
+    C0 = F[rng.choice(1500, 12, replace=False)].copy()
+    prev = math.inf
+    for t in range(1, 12):
+        _, _, iters, inertia = oracle_mod.kmeans(F, C0, t)
+        assert inertia <= prev * (1 + 1e-9)
+        prev = inertia
+        if iters < t:
+            break
+
+
+def test_kmeans_ties_and_empty_clusters(oracle_mod):
+    """Equal centroids: every row takes the lower index. A centroid no row is
+    nearest to keeps its coordinates."""
+    rng = np.random.default_rng(6)
+    F = rng.standard_normal((300, 4)).astype(np.float32)
+    C0 = np.stack([np.zeros(4), np.zeros(4), np.full(4, 1e6)]).astype(np.float32)
+    labels, C, iters, _ = oracle_mod.kmeans(F, C0, 1)
+    assert np.all(labels == 0)
+    np.testing.assert_array_equal(C[1], C0[1])
+    np.testing.assert_array_equal(C[2], C0[2])
