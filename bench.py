@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-kmeans", action="store_true")
     ap.add_argument("--kernel-case", default=None,
                     help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward, "
                          "STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
@@ -445,6 +446,11 @@ def main():
                                          Rc_h.numel() * 4),
                "d2h_bytes_per_step": int(n * eta * 4)}
 
+    # k-means on the step's features (§4.1 step 6; measured apart from the step)
+    kmeans = None
+    if not args.no_kmeans and world == 1:
+        kmeans = run_kmeans_leg(sf, info["Y"], k, wl["r_seed"] + 5, 20)
+
     # accuracy of this step's features/filter against the FP64 oracle on one column
     hbm, peak_kind = peaks()
 
@@ -505,6 +511,7 @@ def main():
         "roofline": roof,
         "gather_ceiling": gather,
         "stages_ms": stages,
+        "kmeans": kmeans,
         "roofline_by_variant": by_variant,
         "clocks": clocks,
         "e2e": e2e,
@@ -521,6 +528,62 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 burst peak times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16_tflops x 1.1/2.25"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback 1.9 PFLOP/s bf16 x 1.1/2.25"
+
+
+def run_kmeans_leg(sf, Fk, k, seed, max_iter):
+    """Lloyd's k-means on feature rows Fk (N x d, FP32, on the device) from k
+    seeded random rows: tensor cores (when the shape allows) vs CUDA cores,
+    the same labels; the distance kernel's roofline."""
+    import torch
+
+    n, d = Fk.shape
+    rng = np.random.default_rng(seed)
+    C0 = Fk[torch.as_tensor(rng.choice(n, k, replace=False), device=Fk.device)].contiguous().clone()
+    tc_ok = d % 32 == 0 and 32 <= d <= 128 and k <= 128
+    out = {"rows": n, "d": d, "k": k, "max_iter": max_iter, "init": "k seeded random rows"}
+    res = {}
+    for name, mode in (("tensor_cores", sf.KMEANS_TENSOR if tc_ok else None), ("cuda_cores", sf.KMEANS_CUDA_CORES)):
+        if mode is None:
+            continue
+        sf.kmeans(Fk, C0, 2, mode)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sf.profile_begin()
+        e0.record()
+        lab, C, it, inertia = sf.kmeans(Fk, C0, max_iter, mode)
+        e1.record()
+        torch.cuda.synchronize()
+        sf.profile_end()
+        v = sf.profile_variants()
+        ms = e0.elapsed_time(e1)
+        res[name] = lab
+        ent = {"ms": ms, "assignments": it, "ms_per_assignment": ms / it, "inertia": inertia}
+        if "kmeans_tc_f32" in v:
+            nl, kms, by = v["kmeans_tc_f32"]
+            t = kms / nl * 1e-3
+            hbm, kind = peaks()
+            tfp, tkind = tf32_peak()
+            ent["distance_kernel"] = {
+                "avg_launch_ms": kms / nl, "launches": nl,
+                "hbm": {"achieved": by / nl / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": by / nl / t / 1e9 / hbm,
+                        "peak_source": f"{kind} hbm_gbs"},
+                "tensor": {"achieved": 2.0 * n * k * d / t / 1e12, "peak": tfp, "unit": "TFLOP/s",
+                           "frac": 2.0 * n * k * d / t / 1e12 / tfp, "peak_source": tkind},
+                "bound": "hbm"}
+        out[name] = ent
+    if len(res) == 2:
+        out["labels_equal"] = bool(torch.equal(res["tensor_cores"], res["cuda_cores"]))
+    return out
 
 
 def _clock_timed(fn, steps, warmup, sf, flush_l2=False):

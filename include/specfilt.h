@@ -427,9 +427,47 @@ SF_API sf_status sf_profile_end(int64_t *launches, double *ms, double *bytes);
 /*
  * Per-variant totals of the last sf_profile_end: tag = 3 * mode + storage,
  * with mode 0 forward, 1 moments, 2 Clenshaw and storage SF_F32 / SF_BF16 /
- * SF_F16; tag 9 is the adjoint kernel of sf_cheb_filter_backward.
+ * SF_F16; tag 9 is the adjoint kernel of sf_cheb_filter_backward, tag 10
+ * the tensor-core distance kernel of sf_kmeans.
  */
 SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, double *bytes);
+
+/* ---------------------------------------------------------------------- */
+/* k-means on the feature rows (§4.1 step 6)                               */
+/* ---------------------------------------------------------------------- */
+
+enum {
+    SF_KMEANS_AUTO = 0,       /* tensor cores when the shape allows (below), else CUDA cores */
+    SF_KMEANS_TENSOR = 1,     /* tensor cores (SF_ERR_ARG when the shape does not allow them) */
+    SF_KMEANS_CUDA_CORES = 2  /* CUDA cores only */
+};
+
+/*
+ * Lloyd's k-means with the Euclidean distance between feature rows (§4.1
+ * step 6), from given initial centroids.
+ *   F         device float[n][d], row-major, rows f~_i (e.g. sf_features output)
+ *   n, d, k   rows (>= 1), columns (1..4096), clusters (1..1023)
+ *   C         device float[k][d]: initial centroids in, final centroids out
+ *   max_iter  maximum number of assignments (>= 1)
+ *   mode      SF_KMEANS_*
+ *   labels    device int32[n] out: cluster of each row
+ *   iters     host out: assignments performed
+ *   inertia   host out or NULL: sum over rows (FP64) of the squared distance
+ *             to the centroid of the last assignment
+ * Iteration: assignment label_i = argmin_c d(f_i, c_c), ties to the lowest c,
+ * with d the FP32 fused-multiply-add sum of (f_ij - c_cj)^2 in index order;
+ * stop when no label changed (from the second assignment on); otherwise
+ * c_c = (FP64 sum of its rows / count) rounded to FP32, empty clusters
+ * keeping their centroid. With tensor cores (d a multiple of 32 in [32, 128],
+ * k <= 128, F and C 16-byte aligned) the products f_i.c_c come from tcgen05
+ * TF32 MMAs and every row whose two best candidates lie within the products'
+ * error bound is decided again with the exact FP32 sum on CUDA cores, so both
+ * modes return the same labels. Deterministic. SF_ERR_NUMERIC when a row or
+ * a centroid is not finite. Synchronises `stream` once per assignment (to
+ * read whether labels changed).
+ */
+SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int32_t k, float *C, int32_t max_iter,
+                           int32_t mode, int32_t *labels, int32_t *iters, double *inertia, void *stream);
 
 /*
  * Measured ceiling of the sweep's gather pattern. A diagnostic with no

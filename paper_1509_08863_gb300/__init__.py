@@ -154,6 +154,7 @@ def lib():
         "sf_cheb_moments_noalloc": (_i32, [_vp, _f64, _vp, _i32, _i32, _dp, _vp]),
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
         "sf_profile_variant": (_i32, [_i32, C.POINTER(_i64), _dp, _dp]),
+        "sf_kmeans": (_i32, [_vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_i32), _dp, _vp]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -513,6 +514,26 @@ def profile_end():
     return n.value, ms.value, by.value
 
 
+KMEANS_AUTO, KMEANS_TENSOR, KMEANS_CUDA_CORES = 0, 1, 2
+
+
+def kmeans(F, C0, max_iter: int = 50, mode: int = KMEANS_AUTO):
+    """Lloyd's k-means on the rows of F (§4.1 step 6) from centroids C0 (k x d):
+    returns (labels int32 tensor [n], centroids float32 tensor [k x d],
+    assignments performed, inertia of the last assignment)."""
+    torch = _torch()
+    n, d = F.shape
+    k = C0.shape[0]
+    Fd = F.contiguous()
+    Cw = C0.to(device=F.device, dtype=torch.float32).contiguous().clone()
+    labels = torch.empty(n, dtype=torch.int32, device=F.device)
+    it = _i32()
+    inertia = _f64()
+    _check(lib().sf_kmeans(_dev_ptr(Fd, torch.float32, "F"), int(n), int(d), int(k), Cw.data_ptr(), int(max_iter),
+                           int(mode), labels.data_ptr(), C.byref(it), C.byref(inertia), _stream()), "sf_kmeans")
+    return labels, Cw, it.value, inertia.value
+
+
 def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> float:
     """Rows per second of the sweep's random-row gather pattern alone (synthetic
     BF16 table of n_rows + 1 rows of row_bytes bytes, deg entries per row)."""
@@ -530,6 +551,7 @@ def device_check():
 PROFILE_TAGS = {3 * m + s: f"{mn}_{sn}" for m, mn in enumerate(("forward", "moments", "clenshaw"))
                 for s, sn in enumerate(("f32", "bf16", "f16"))}
 PROFILE_TAGS[9] = "adjoint_f32"
+PROFILE_TAGS[10] = "kmeans_tc_f32"
 
 
 def profile_variants():

@@ -76,8 +76,9 @@ sf_status reduce_sum_f64(const double *in, int64_t count, double *out, cudaStrea
 // ---------------------------------------------------------------- profiling
 // Kernel variants are tagged mode * 3 + storage (SF_F32 0, SF_BF16 1,
 // SF_F16 2) with mode 0 forward, 1 moments, 2 Clenshaw.
-constexpr int kProfTags = 10;
-constexpr int kProfTagAdjoint = 9;  // the adjoint's fused Clenshaw + sampled-product kernel
+constexpr int kProfTags = 11;
+constexpr int kProfTagAdjoint = 9;   // the adjoint's sampled-product kernel
+constexpr int kProfTagKmeansTc = 10; // the k-means tensor-core distance kernel
 bool profiling_on();
 void profile_record(cudaEvent_t a, cudaEvent_t b, double bytes, int tag, int64_t launches = 1);
 bool profile_events(cudaEvent_t *a, cudaEvent_t *b);

@@ -1,0 +1,751 @@
+// k-means on the feature rows (§4.1 step 6: k-means with the Euclidean
+// distance between rows f~_i), Lloyd's iterations from given centroids.
+//
+// Assignment. The label of row i is argmin_c d(f_i, c_c), ties to the lowest
+// c, where d is the FP32 sum of fused multiply-adds (f_j - c_j)^2 in index
+// order: a floating-point decision, so it is stated in one precision and
+// order. Two ways to take it:
+//  * CUDA cores (kmeans_assign_kernel): a warp per row, a lane per centroid,
+//    exactly that sum;
+//  * tensor cores (kmeans_tc_kernel): G = F C^T for a 128-row tile on tcgen05
+//    (TF32 operands staged by TMA in 128-byte swizzled shared memory, FP32
+//    accumulators in TMEM), e_c = |c_c|^2 - 2 G_ic; the row takes the tensor
+//    argmin when its two best candidates are further apart than twice the
+//    bound on |e_c + |f_i|^2 - d(f_i, c_c)|, and is otherwise queued for the
+//    CUDA-core decision. Both give the same labels.
+// Bound: TF32 keeps 10 mantissa bits (truncation error < 2^-10 per operand),
+// so |G_ic - f_i.c_c| <= (2^-9 + 2^-16) |f_i| |c_c| with FP32 accumulation
+// of 128 products; |c|^2 and the FP32 sum d carry <= 2^-16 (|f| + |c|)^2.
+// With the factor 2 on G and a safety margin: E_i = 2^-7 |f_i| c_max +
+// 2^-16 (|f_i| + c_max)^2, and a row is decided by the tensor cores when the
+// gap between its two best e exceeds 2 E_i.
+//
+// Update. Rows are sorted by (label, row) (stable radix sort), cut into
+// chunks of at most kChunkRows rows within each cluster; each chunk's column
+// sums are FP64 in row order, and each cluster adds its chunks in order:
+// c_c = (float)(sum / count); an empty cluster keeps its centroid. Every
+// step is deterministic.
+#include <cuda.h>
+#include <math.h>
+
+#include "sf_step.cuh"
+
+namespace sf {
+
+constexpr int kChunkRows = 256;
+constexpr int kTcRows = 128;  // rows of F per tensor-core tile (MMA M)
+
+// ------------------------------------------------------------ small kernels
+// |f_i| (FP32, rounded up by 2^-20 relative), one warp per row
+__global__ void km_row_norm_kernel(const float *F, int32_t n, int32_t d, float *fn, int32_t *bad) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        float s = 0.f;
+        for (int j = lane; j < d; j += 32) s = fmaf(F[i * d + j], F[i * d + j], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            fn[i] = sqrtf(s) * (1.0f + 1.0f / 1048576.0f);
+            if (!isfinite(s)) *bad = 1;
+        }
+    }
+}
+
+// cn2[c] = |c_c|^2 (FP32 fused multiply-adds in index order); cmax = max |c| rounded up. One block.
+__global__ void km_centroid_norm_kernel(const float *C, int32_t k, int32_t d, float *cn2, float *cmax,
+                                        int32_t *bad) {
+    __shared__ float s_max[32];
+    float mx = 0.f;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        float s = 0.f;
+        for (int j = 0; j < d; ++j) s = fmaf(C[(int64_t)c * d + j], C[(int64_t)c * d + j], s);
+        cn2[c] = s;
+        mx = fmaxf(mx, s);
+        if (!isfinite(s)) *bad = 1;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_max[w]);
+        *cmax = sqrtf(m) * (1.0f + 1.0f / 1048576.0f);
+    }
+}
+
+// The exact decision for one row: lane l scores centroids l, l + 32, ...
+// (each an FP32 fused-multiply-add chain in index order), then the warp keeps
+// the smallest score, ties to the lowest centroid. sC: centroids with row
+// stride ldc (a shared-memory copy, or C itself).
+__device__ __forceinline__ int32_t km_decide_row(const float *__restrict__ f, const float *sC, int32_t ldc, int32_t k,
+                                                 int32_t d, float *best_d) {
+    const int lane = threadIdx.x & 31;
+    float bd = INFINITY;
+    int32_t bc = 0x7fffffff;
+    for (int c = lane; c < k; c += 32) {
+        const float *cc = sC + (int64_t)c * ldc;
+        float acc = 0.f;
+        for (int j = 0; j < d; ++j) {
+            const float t = __fsub_rn(__ldg(f + j), cc[j]);
+            acc = __fmaf_rn(t, t, acc);
+        }
+        if (acc < bd) {  // c increases along the loop: ties keep the lower index
+            bd = acc;
+            bc = c;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, bd, off);
+        const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        if (od < bd || (od == bd && oc < bc)) {
+            bd = od;
+            bc = oc;
+        }
+    }
+    *best_d = bd;
+    return bc;
+}
+
+// CUDA-core assignment of rows list[0..*count) (list == nullptr: all rows,
+// count == nullptr: n). Centroids staged in shared memory with row stride
+// d + 1 (bank-conflict free) when smem_c is set.
+__global__ void km_assign_kernel(const float *F, int32_t n, int32_t d, const float *C, int32_t k,
+                                 const int32_t *list, const int32_t *count, int32_t *labels, int32_t *changed,
+                                 int smem_c) {
+    extern __shared__ float s_c[];
+    const float *cs = C;
+    int32_t ldc = d;
+    if (smem_c) {
+        for (int64_t t = threadIdx.x; t < (int64_t)k * d; t += blockDim.x) s_c[(t / d) * (d + 1) + t % d] = C[t];
+        __syncthreads();
+        cs = s_c;
+        ldc = d + 1;
+    }
+    const int64_t total = list ? (int64_t)*count : (int64_t)n;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t i = list ? list[w] : (int32_t)w;
+        float bd;
+        const int32_t c = km_decide_row(F + (int64_t)i * d, cs, ldc, k, d, &bd);
+        if (lane == 0) {
+            if (labels[i] != c) *changed = 1;
+            labels[i] = c;
+        }
+    }
+}
+
+// The same exact decision, register-blocked for k <= 128 and d <= 256: a block
+// of 128 threads takes 32 rows at a time; thread (g, h) = (t / 16, t % 16)
+// scores rows 4g .. 4g + 3 against centroids h, h + 16, ..., h + 112, each
+// pair an FP32 fused-multiply-add chain in index order (the same arithmetic
+// as km_decide_row), with rows and centroids staged in shared memory (row
+// stride d + 1: no bank conflicts). The 16 lanes of a row group then keep the
+// smallest score, ties to the lowest centroid.
+constexpr int kExRows = 32;
+__global__ void __launch_bounds__(128) km_assign_blocked_kernel(const float *F, int32_t n, int32_t d, const float *C,
+                                                                int32_t k, const int32_t *list, const int32_t *count,
+                                                                int32_t *labels, int32_t *changed) {
+    extern __shared__ float s_ex[];
+    const int ld = d + 1;
+    float *sC = s_ex;                // [128][d + 1], rows >= k zero
+    float *sF = s_ex + 128 * ld;     // [32][d + 1]
+    for (int t = threadIdx.x; t < 128 * d; t += blockDim.x) {
+        const int c = t / d, j = t % d;
+        sC[c * ld + j] = (c < k) ? C[(int64_t)c * d + j] : 0.0f;
+    }
+    const int64_t total = list ? (int64_t)*count : (int64_t)n;
+    const int g = threadIdx.x >> 4, h = threadIdx.x & 15;
+    for (int64_t r0 = (int64_t)blockIdx.x * kExRows; r0 < total; r0 += (int64_t)gridDim.x * kExRows) {
+        __syncthreads();  // sC ready (first pass) / sF free
+        for (int t = threadIdx.x; t < kExRows * d; t += blockDim.x) {
+            const int r = t / d, j = t % d;
+            float v = 0.0f;
+            if (r0 + r < total) {
+                const int64_t i = list ? list[r0 + r] : r0 + r;
+                v = F[i * d + j];
+            }
+            sF[r * ld + j] = v;
+        }
+        __syncthreads();
+        float acc[4][8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[r][m] = 0.0f;
+        const float *fr = sF + (4 * g) * ld;
+        const float *cr = sC + h * ld;
+        for (int j = 0; j < d; ++j) {
+            float fv[4], cv[8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) fv[r] = fr[r * ld + j];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) cv[m] = cr[(16 * m) * ld + j];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const float t = __fsub_rn(fv[r], cv[m]);
+                    acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float bd = INFINITY;
+            int32_t bc = 0x7fffffff;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int c = h + 16 * m;
+                if (c < k && acc[r][m] < bd) {
+                    bd = acc[r][m];
+                    bc = c;
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {  // the 16 lanes of this row group
+                const float od = __shfl_xor_sync(0xffffffffu, bd, off);
+                const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                if (od < bd || (od == bd && oc < bc)) {
+                    bd = od;
+                    bc = oc;
+                }
+            }
+            const int64_t w = r0 + 4 * g + r;
+            if (h == 0 && w < total) {
+                const int64_t i = list ? list[w] : w;
+                if (labels[i] != bc) *changed = 1;
+                labels[i] = bc;
+            }
+        }
+    }
+}
+
+// inertia partials: part[b] = sum over this block's rows (block order) of d(f_i, c_label_i)
+__global__ void km_inertia_kernel(const float *F, int32_t n, int32_t d, const float *C, const int32_t *labels,
+                                  double *part) {
+    __shared__ double s_red[32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float *f = F + i * d;
+        const float *c = C + (int64_t)labels[i] * d;
+        float s = 0.f;
+        for (int j = 0; j < d; ++j) {
+            const float t = __fsub_rn(f[j], c[j]);
+            s = __fmaf_rn(t, t, s);
+        }
+        acc += (double)s;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[w];
+        part[blockIdx.x] = a;
+    }
+}
+
+// key = label << 32 | row
+__global__ void km_keys_kernel(const int32_t *labels, int32_t n, uint64_t *keys) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = ((uint64_t)(uint32_t)labels[i] << 32) | (uint32_t)i;
+}
+
+// offs[c] = first sorted position with label >= c (c = 0..k); coffs = prefix of
+// ceil(count / kChunkRows) chunks per cluster. One block of 1024 threads, k <= 1023.
+__global__ void km_offsets_kernel(const uint64_t *keys, int32_t n, int32_t k, int32_t *offs, int32_t *coffs) {
+    __shared__ int32_t s_scan[1024];
+    const int c = threadIdx.x;
+    auto lower = [&](int32_t lab) {
+        int32_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if ((int32_t)(keys[mid] >> 32) < lab) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    int32_t nch = 0;
+    if (c <= k) {
+        const int32_t o = lower(c);
+        offs[c] = o;
+        if (c < k) {
+            const int32_t cnt = lower(c + 1) - o;
+            nch = (cnt + kChunkRows - 1) / kChunkRows;
+        }
+    }
+    s_scan[c] = nch;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan (Hillis-Steele)
+        const int32_t v = (c >= off) ? s_scan[c - off] : 0;
+        __syncthreads();
+        s_scan[c] += v;
+        __syncthreads();
+    }
+    if (c <= k) coffs[c] = (c == 0) ? 0 : s_scan[c - 1];
+}
+
+// FP64 column sums of one chunk of one cluster, rows in sorted (row) order
+__global__ void km_chunk_sum_kernel(const float *F, int32_t d, int32_t k, const uint64_t *keys, const int32_t *offs,
+                                    const int32_t *coffs, double *part) {
+    const int32_t b = blockIdx.x;
+    if (b >= coffs[k]) return;
+    int32_t lo = 0, hi = k - 1;  // the cluster c with coffs[c] <= b < coffs[c + 1]
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (coffs[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int32_t c = lo;
+    const int32_t q = b - coffs[c];
+    const int32_t r0 = offs[c] + q * kChunkRows;
+    const int32_t r1 = min(offs[c + 1], r0 + kChunkRows);
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int32_t r = r0; r < r1; ++r) s += (double)F[(int64_t)(uint32_t)(keys[r] & 0xffffffffu) * d + j];
+        part[(int64_t)b * d + j] = s;
+    }
+}
+
+// c_c = (sum of its chunks in order) / count, rounded to FP32; empty clusters keep c_c
+__global__ void km_centroid_kernel(int32_t d, const int32_t *offs, const int32_t *coffs, const double *part,
+                                   float *C) {
+    const int32_t c = blockIdx.x;
+    const int32_t cnt = offs[c + 1] - offs[c];
+    if (cnt == 0) return;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int32_t q = coffs[c]; q < coffs[c + 1]; ++q) s += part[(int64_t)q * d + j];
+        C[(int64_t)c * d + j] = (float)(s / (double)cnt);
+    }
+}
+
+// ------------------------------------------------------------ tensor cores
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 2-D tiled TMA load of box {32 FP32 columns, rows} at (x, y) into shared memory
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte
+// swizzle, 8-row groups 1024 bytes apart, start address `addr` (16-byte units).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+    uint64_t desc = 0;
+    desc |= (uint64_t)((addr >> 4) & 0x3FFFu);         // start address
+    desc |= (uint64_t)1u << 16;                         // leading byte offset (unused for this layout)
+    desc |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+    desc |= (uint64_t)1u << 46;                         // descriptor version
+    desc |= (uint64_t)2u << 61;                         // 128-byte swizzle
+    return desc;
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, M = 128, N = nmma.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int nmma) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+struct TcParams {
+    int32_t n, d, k, nmma, ncols;  // ncols: TMEM columns per accumulator (power of two >= 32)
+    const float *cn2;              // [k]
+    const float *cmax;             // [1]
+    const float *fn;               // [n]
+    int32_t *labels;
+    int32_t *changed;
+    int32_t *list;                 // rows left to the exact decision
+    int32_t *count;
+    int32_t *status;               // bit 0: a bounded wait gave up
+};
+
+constexpr uint32_t kTcPolls = 1u << 24;
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    for (uint32_t it = 0; it < kTcPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 1023u) == 1023u && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// Warp roles: 0 = TMA producer, 1 = TMEM owner and MMA issuer, 2..5 = epilogue
+// (128 threads, one tile row each). A: two stages of 128 x d FP32; B: the
+// centroids (nmma x d, rows >= k zero-filled by the copy); two TMEM
+// accumulators of ncols columns so that tile t + 1 multiplies while tile t is
+// read.
+__global__ void __launch_bounds__(192, 1)
+    kmeans_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapC,
+                     const TcParams P) {
+    extern __shared__ __align__(16) unsigned char km_smem[];
+    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tfull[2], s_tempty[2], s_bfull;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // 1024-byte aligned base for the swizzled tiles
+    unsigned char *base = km_smem + ((1024u - (smem_u32(km_smem) & 1023u)) & 1023u);
+    const int atoms = P.d / 32;                     // 128-byte K-chunks
+    const uint32_t a_bytes = (uint32_t)kTcRows * P.d * 4;
+    const uint32_t b_atom = (uint32_t)P.nmma * 128;
+    unsigned char *sB = base;
+    unsigned char *sA[2] = {base + (uint32_t)atoms * b_atom, base + (uint32_t)atoms * b_atom + a_bytes};
+    const int n_tiles = (P.n + kTcRows - 1) / kTcRows;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&s_full[s], 1);
+            mbar_init(&s_empty[s], 1);
+            mbar_init(&s_tfull[s], 1);
+            mbar_init(&s_tempty[s], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&s_bfull, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(2 * P.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    volatile int *abort = &s_abort;
+
+    if (warp == 0 && lane == 0) {
+        // producer: the centroids once, then the A tiles through two stages
+        mbar_arrive_expect_tx(&s_bfull, (uint32_t)atoms * b_atom);
+        for (int a = 0; a < atoms; ++a) tma_load_2d(sB + a * b_atom, &mapC, 32 * a, 0, &s_bfull);
+        int t = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+            const int s = t & 1;
+            if (t >= 2 && !tc_wait(&s_empty[s], (uint32_t)((t >> 1) - 1) & 1u, abort)) break;
+            mbar_arrive_expect_tx(&s_full[s], a_bytes);
+            for (int a = 0; a < atoms; ++a)
+                tma_load_2d(sA[s] + (uint32_t)a * kTcRows * 128, &mapF, 32 * a, tile * kTcRows, &s_full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = umma_idesc_tf32(P.nmma);
+        bool ok = tc_wait(&s_bfull, 0, abort);
+        int t = 0;
+        for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++t) {
+            const int s = t & 1;
+            if (!tc_wait(&s_full[s], (uint32_t)(t >> 1) & 1u, abort)) break;
+            if (t >= 2 && !tc_wait(&s_tempty[s], (uint32_t)((t >> 1) - 1) & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dcol = tmem + (uint32_t)s * P.ncols;
+            for (int kk = 0; kk < P.d / 8; ++kk) {  // K = 8 TF32 per instruction: 32 bytes of a 128-byte row
+                const int a = kk >> 2;
+                const uint32_t off = (uint32_t)(kk & 3) * 32;
+                const uint64_t adesc = umma_desc_sw128(smem_u32(sA[s] + (uint32_t)a * kTcRows * 128) + off);
+                const uint64_t bdesc = umma_desc_sw128(smem_u32(sB + (uint32_t)a * b_atom) + off);
+                const uint32_t acc = kk > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            // the stage is free and the accumulator ready once these MMAs complete
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&s_empty[s]))
+                         : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&s_tfull[s]))
+                         : "memory");
+        }
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int q = warp & 3;
+        const float cmax = *P.cmax;
+        int t = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+            const int s = t & 1;
+            if (!tc_wait(&s_tfull[s], (uint32_t)(t >> 1) & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int64_t row = (int64_t)tile * kTcRows + q * 32 + lane;
+            float b1 = INFINITY, b2 = INFINITY;
+            int32_t c1 = 0;
+            for (int c0 = 0; c0 < P.nmma; c0 += 32) {
+                // two 16-column loads in flight, one wait
+                uint32_t r[32];
+                const uint32_t taddr = tmem + (uint32_t)s * P.ncols + (uint32_t)c0 + ((uint32_t)(q * 32) << 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr));
+                const bool two = c0 + 16 < P.nmma;
+                if (two)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                          "=r"(r[30]), "=r"(r[31])
+                        : "r"(taddr + 16u));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const int c = c0 + u;
+                    if (c < P.k && (u < 16 || two)) {
+                        const float e = fmaf(-2.0f, __uint_as_float(r[u]), __ldg(P.cn2 + c));
+                        if (e < b1) {
+                            b2 = b1;
+                            b1 = e;
+                            c1 = c;
+                        } else if (e < b2) {
+                            b2 = e;
+                        }
+                    }
+                }
+            }
+            // the accumulator may be overwritten once every epilogue warp has read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_tempty[s]);
+            bool queue = false;
+            if (row < P.n) {
+                const float fi = __ldg(P.fn + row);
+                const float e_bound = 0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax);
+                queue = P.k > 1 && !(b2 - b1 > 2.0f * e_bound);
+                if (!queue) {
+                    if (P.labels[row] != c1) *P.changed = 1;
+                    P.labels[row] = c1;
+                }
+            }
+            // one queue slot reservation per warp
+            const unsigned qm = __ballot_sync(0xffffffffu, queue);
+            if (qm) {
+                int32_t slot0 = 0;
+                if (lane == 0) slot0 = atomicAdd(P.count, __popc(qm));
+                slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+                if (queue) P.list[slot0 + __popc(qm & ((1u << lane) - 1u))] = (int32_t)row;
+            }
+        }
+    }
+    // teardown: every role has left its loop
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && s_abort) atomicOr(P.status, 1);
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * P.ncols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------ host
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static sf_status encode_fn(EncodeTiledFn *out) {
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+            cudaGetLastError();
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return SF_ERR_CUDA;
+        }
+        fn = (EncodeTiledFn)p;
+    }
+    *out = fn;
+    return SF_OK;
+}
+
+// FP32 row-major [rows][d] with 128-byte swizzled boxes of {32, box_rows}
+static sf_status encode_rows(CUtensorMap *map, const float *ptr, int64_t rows, int32_t d, int32_t box_rows) {
+    EncodeTiledFn fn;
+    sf_status st = encode_fn(&fn);
+    if (st) return st;
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return SF_ERR_CUDA;
+    }
+    return SF_OK;
+}
+
+static bool tc_shape_ok(int32_t d, int32_t k) { return d % 32 == 0 && d >= 32 && d <= 128 && k >= 1 && k <= 128; }
+
+static int tc_smem_bytes(int32_t d, int32_t nmma) {
+    return 1024 /* alignment slack */ + (d / 32) * nmma * 128 + 2 * kTcRows * d * 4;
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int32_t k, float *C, int32_t max_iter,
+                                      int32_t mode, int32_t *labels, int32_t *iters, double *inertia,
+                                      void *stream) {
+    SF_ARG(F && C && labels && iters, "F/C/labels/iters is NULL");
+    SF_ARG(n >= 1 && d >= 1 && d <= 4096, "need n >= 1 and 1 <= d <= 4096");
+    SF_ARG(k >= 1 && k <= 1023, "k must be in [1, 1023]");
+    SF_ARG(max_iter >= 1, "max_iter must be >= 1");
+    SF_ARG(mode == SF_KMEANS_AUTO || mode == SF_KMEANS_TENSOR || mode == SF_KMEANS_CUDA_CORES,
+           "mode must be SF_KMEANS_*");
+    const bool aligned = ((uintptr_t)F % 16 == 0) && ((uintptr_t)C % 16 == 0);
+    const bool tc = mode != SF_KMEANS_CUDA_CORES && tc_shape_ok(d, k) && aligned;
+    SF_ARG(mode != SF_KMEANS_TENSOR || tc,
+           "the tensor-core assignment needs d a multiple of 32 in [32, 128], k <= 128 and 16-byte aligned F and C");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    float *fn = nullptr, *cn2 = nullptr, *cmax = nullptr;
+    int32_t *changed = nullptr, *bad = nullptr, *list = nullptr, *count = nullptr, *offs = nullptr, *coffs = nullptr;
+    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    double *part = nullptr, *ipart = nullptr, *isum = nullptr;
+    const int64_t max_chunks = (int64_t)(n + kChunkRows - 1) / kChunkRows + k;
+    const int ig = 2 * sm_count();
+    sf_status st;
+    if ((st = sc.get(&fn, (size_t)n)) || (st = sc.get(&cn2, (size_t)k)) || (st = sc.get(&cmax, 1)) ||
+        (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) || (st = sc.get(&count, 2)) ||
+        (st = sc.get(&offs, (size_t)k + 1)) || (st = sc.get(&coffs, (size_t)k + 1)) ||
+        (st = sc.get(&keys, (size_t)n)) || (st = sc.get(&keys_alt, (size_t)n)) ||
+        (st = sc.get(&part, (size_t)max_chunks * d)) || (st = sc.get(&ipart, (size_t)ig)) ||
+        (st = sc.get(&isum, 1)))
+        return st;
+    SF_CHECK_CUDA(cudaMemsetAsync(labels, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1: no label yet
+    SF_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
+    km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad);
+    if ((st = check_launch("km_row_norm_kernel"))) return st;
+
+    // tensor-core setup
+    CUtensorMap mapF, mapC;
+    TcParams T = {};
+    int tc_grid = 0, tc_smem = 0;
+    if (tc) {
+        const int nmma = (k + 15) / 16 * 16;
+        int ncols = 32;
+        while (ncols < nmma) ncols *= 2;
+        if ((st = encode_rows(&mapF, F, n, d, kTcRows)) || (st = encode_rows(&mapC, C, k, d, nmma))) return st;
+        tc_smem = tc_smem_bytes(d, nmma);
+        SF_CHECK_CUDA(cudaFuncSetAttribute(kmeans_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+        const int n_tiles = (n + kTcRows - 1) / kTcRows;
+        tc_grid = n_tiles < sm_count() ? n_tiles : sm_count();
+        T.n = n;
+        T.d = d;
+        T.k = k;
+        T.nmma = nmma;
+        T.ncols = ncols;
+        T.cn2 = cn2;
+        T.cmax = cmax;
+        T.fn = fn;
+        T.labels = labels;
+        T.changed = changed;
+        T.list = list;
+        T.count = count;
+        T.status = device_status();
+        SF_ARG(T.status, "device status word unavailable");
+    }
+    // exact-decision kernel: register-blocked for k <= 128 and d <= 256, else a warp per row with the
+    // centroids in shared memory when they fit
+    const bool blocked = k <= 128 && d <= 256;
+    const size_t ex_smem = (size_t)(128 + kExRows) * (d + 1) * sizeof(float);
+    const size_t c_smem = (size_t)k * (d + 1) * sizeof(float);
+    const int smem_c = c_smem <= 160 * 1024 ? 1 : 0;
+    if (blocked)
+        SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ex_smem));
+    else if (smem_c)
+        SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)c_smem));
+    int ex_occ = 1;
+    if (blocked) SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ex_occ, km_assign_blocked_kernel, 128,
+                                                                             ex_smem));
+    const int assign_grid = blocked ? (ex_occ > 0 ? ex_occ : 1) * sm_count() : (smem_c ? sm_count() : 4 * sm_count());
+    auto exact = [&](const int32_t *lst, const int32_t *cnt) -> sf_status {
+        if (blocked)
+            km_assign_blocked_kernel<<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
+        else
+            km_assign_kernel<<<assign_grid, 256, smem_c ? c_smem : 0, s>>>(F, n, d, C, k, lst, cnt, labels, changed,
+                                                                           smem_c);
+        return check_launch("km_assign_kernel");
+    };
+
+    int it = 0;
+    while (it < max_iter) {
+        SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+        km_centroid_norm_kernel<<<1, 1024, 0, s>>>(C, k, d, cn2, cmax, bad);
+        if ((st = check_launch("km_centroid_norm_kernel"))) return st;
+        if (tc) {
+            SF_CHECK_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
+            cudaEvent_t ea = nullptr, eb = nullptr;
+            const bool prof = profiling_on() && profile_events(&ea, &eb);
+            if (prof) cudaEventRecord(ea, s);
+            kmeans_tc_kernel<<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, T);
+            if ((st = check_launch("kmeans_tc_kernel"))) return st;
+            if (prof) {
+                cudaEventRecord(eb, s);
+                // compulsory bytes: the rows once, the centroids per CTA, labels read and written
+                profile_record(ea, eb, (double)n * d * 4 + (double)tc_grid * k * d * 4 + (double)n * 8,
+                               kProfTagKmeansTc);
+            }
+            if ((st = exact(list, count))) return st;
+        } else {
+            if ((st = exact(nullptr, nullptr))) return st;
+        }
+        int32_t h_changed = 0, h_bad = 0;
+        SF_CHECK_CUDA(cudaMemcpyAsync(&h_changed, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaStreamSynchronize(s));
+        if ((st = sf_device_check(stream))) return st;
+        if (h_bad) {
+            set_error("non-finite feature row or centroid");
+            return SF_ERR_NUMERIC;
+        }
+        ++it;
+        const bool last = (it > 1 && !h_changed) || it == max_iter;
+        if (last && inertia) {
+            km_inertia_kernel<<<ig, 256, 0, s>>>(F, n, d, C, labels, ipart);
+            if ((st = check_launch("km_inertia_kernel"))) return st;
+            if ((st = reduce_sum_f64(ipart, ig, isum, s))) return st;
+            SF_CHECK_CUDA(cudaMemcpyAsync(inertia, isum, sizeof(double), cudaMemcpyDeviceToHost, s));
+            SF_CHECK_CUDA(cudaStreamSynchronize(s));
+        }
+        if (it > 1 && !h_changed) break;
+        // update: rows sorted by (label, row), FP64 chunk sums, clusters add their chunks in order
+        km_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels, n, keys);
+        if ((st = check_launch("km_keys_kernel"))) return st;
+        int bits = 8;
+        while (bits < 32 && (1ll << bits) < k) bits += 8;
+        uint64_t *ka = keys, *kb = keys_alt;
+        float *nv = nullptr, *nv2 = nullptr;
+        if ((st = radix_sort(ka, nv, kb, nv2, n, 32, 32 + bits, s))) return st;
+        km_offsets_kernel<<<1, 1024, 0, s>>>(ka, n, k, offs, coffs);
+        if ((st = check_launch("km_offsets_kernel"))) return st;
+        km_chunk_sum_kernel<<<(unsigned)max_chunks, 128, 0, s>>>(F, d, k, ka, offs, coffs, part);
+        if ((st = check_launch("km_chunk_sum_kernel"))) return st;
+        km_centroid_kernel<<<k, 128, 0, s>>>(d, offs, coffs, part, C);
+        if ((st = check_launch("km_centroid_kernel"))) return st;
+    }
+    *iters = it;
+    return SF_OK;
+}

@@ -36,7 +36,7 @@ __device__ void block_dot_store(double acc, double *part) {
 }
 
 // w = L v over the sliced-ELL copy: one thread per row, indices read four at a
-// time and four gathers in flight; partial <w, v>. Padding entries gather
+// time and eight gathers in flight; partial <w, v>. Padding entries gather
 // v[n] = 0. The row sum runs in entry order (the CSR column order).
 __global__ void __launch_bounds__(256) lap_spmv_sell_kernel(int32_t n, const int32_t *sptr, const int32_t *perm,
                                                             const int32_t *idx, const float *sval,
@@ -50,7 +50,26 @@ __global__ void __launch_bounds__(256) lap_spmv_sell_kernel(int32_t n, const int
         const int32_t so = sptr[sl], ls = (sptr[sl + 1] - so) / kSliceRows;
         const int64_t eo = (int64_t)so + (int64_t)pos * ls;
         double acc = 0.0;
-        for (int32_t e = 0; e < ls; e += 4) {
+        int32_t e = 0;
+        for (; e + 8 <= ls; e += 8) {  // eight gathers in flight
+            const int4 ka = __ldg(reinterpret_cast<const int4 *>(idx + eo + e));
+            const int4 kb = __ldg(reinterpret_cast<const int4 *>(idx + eo + e + 4));
+            const int32_t k[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(v + k[u]);
+            if (sval) {
+                const float4 ca = __ldg(reinterpret_cast<const float4 *>(sval + eo + e));
+                const float4 cb = __ldg(reinterpret_cast<const float4 *>(sval + eo + e + 4));
+                const float c[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += (double)c[u] * x[u];
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += x[u];
+            }
+        }
+        if (e < ls) {  // ls is a multiple of 4
             const int4 k = __ldg(reinterpret_cast<const int4 *>(idx + eo + e));
             const double x0 = __ldg(v + k.x), x1 = __ldg(v + k.y), x2 = __ldg(v + k.z), x3 = __ldg(v + k.w);
             if (sval) {

@@ -1,0 +1,124 @@
+"""GPU k-means (§4.1 step 6) against the oracle's Lloyd iterations on the same
+FP32 rows and initial centroids.
+
+Labels are integers decided by floating point; both sides decide them with
+the FP32 fused-multiply-add sum in index order (ties to the lowest index), so
+labels and the number of assignments must be equal. Centroids are FP64 means
+rounded to FP32 on both sides, summed in different orders (chunks vs one
+pass): equal up to one FP32 ulp. Inertia: FP64 sums in different orders,
+1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_08863_gb300 import build
+
+    build.build()
+    import paper_1509_08863_gb300 as m
+
+    return m
+
+
+def mixture(n, d, k, seed, spread=1.0):
+    rng = np.random.default_rng(seed)
+    centres = rng.standard_normal((k, d)) * 2.0
+    lab = rng.integers(0, k, n)
+    F = (centres[lab] + spread * rng.standard_normal((n, d))).astype(np.float32)
+    F /= np.linalg.norm(F, axis=1, keepdims=True)  # unit rows, like the features
+    C0 = F[rng.choice(n, k, replace=False)].copy()
+    return F, C0
+
+
+def farthest_point_init(F, k, seed):
+    """k rows: a random first one, then repeatedly the row farthest from those
+    chosen (a deterministic k-means++ variant)."""
+    rng = np.random.default_rng(seed)
+    idx = [int(rng.integers(len(F)))]
+    dmin = ((F - F[idx[0]]) ** 2).sum(1)
+    for _ in range(k - 1):
+        idx.append(int(np.argmax(dmin)))
+        dmin = np.minimum(dmin, ((F - F[idx[-1]]) ** 2).sum(1))
+    return F[idx].copy()
+
+
+def check_same(sf, oracle_mod, F, C0, max_iter, mode):
+    lo, Co, it_o, in_o = oracle_mod.kmeans(F, C0, max_iter)
+    lab, C, it, inertia = sf.kmeans(torch.as_tensor(F, device="cuda"), torch.as_tensor(C0, device="cuda"),
+                                    max_iter, mode)
+    np.testing.assert_array_equal(lab.cpu().numpy(), lo)
+    assert it == it_o
+    Cg = C.cpu().numpy()
+    ulp = np.abs(Cg.view(np.int32).astype(np.int64) - Co.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 1, ulp.max()
+    assert inertia == pytest.approx(in_o, rel=1e-12)
+    return lo, it_o
+
+
+@pytest.mark.parametrize("d,k", [(32, 1), (32, 7), (64, 16), (128, 100), (128, 128), (96, 33)])
+def test_kmeans_tensor_cores_match_oracle(sf, oracle_mod, d, k):
+    # ragged row count: not a multiple of the 128-row tiles
+    F, C0 = mixture(3001, d, k, seed=d + k)
+    for mode in (sf.KMEANS_TENSOR, sf.KMEANS_CUDA_CORES):
+        check_same(sf, oracle_mod, F, C0, 12, mode)
+
+
+def test_kmeans_other_shapes_use_cuda_cores(sf, oracle_mod):
+    F, C0 = mixture(1500, 48, 200, seed=5)  # d not a multiple of 32, k > 128
+    check_same(sf, oracle_mod, F, C0, 6, sf.KMEANS_AUTO)
+    with pytest.raises(sf.SpecFiltError):
+        sf.kmeans(torch.as_tensor(F, device="cuda"), torch.as_tensor(C0, device="cuda"), 3, sf.KMEANS_TENSOR)
+
+
+def test_kmeans_ties_go_to_lowest_index(sf, oracle_mod):
+    """Duplicated centroids tie exactly; the tensor-core gap is zero, so the
+    rows go to the exact decision, which keeps the lower index."""
+    F, C0 = mixture(2000, 64, 8, seed=7)
+    C0 = np.concatenate([C0, C0[:3]], axis=0)  # centroids 8..10 duplicate 0..2
+    lab, _ = check_same(sf, oracle_mod, F, C0, 1, sf.KMEANS_TENSOR)
+    assert not np.isin(lab, [8, 9, 10]).any()
+
+
+def test_kmeans_small_and_degenerate(sf, oracle_mod):
+    F, C0 = mixture(5, 32, 3, seed=8)  # fewer rows than a tile
+    check_same(sf, oracle_mod, F, C0, 5, sf.KMEANS_TENSOR)
+    F, C0 = mixture(700, 32, 4, seed=9)
+    C0[3] = 100.0  # far away: stays empty and keeps its coordinates
+    check_same(sf, oracle_mod, F, C0, 4, sf.KMEANS_AUTO)
+    F[17, 3] = np.nan
+    with pytest.raises(sf.SpecFiltError):
+        sf.kmeans(torch.as_tensor(F, device="cuda"), torch.as_tensor(C0, device="cuda"), 3)
+
+
+def test_kmeans_on_filtered_features(sf, oracle_mod):
+    """The path end to end on a small SBM: filter at the k-th eigenvalue,
+    row-normalised features, k-means: labels equal the oracle's on the GPU's
+    own features, and the communities are recovered."""
+    from paper_1509_08863_gb300 import synth
+
+    n, k, eta, p = 1200, 6, 24, 60
+    sizes = synth.community_sizes_equal(n, k)
+    gr = synth.sbm_edges(n, sizes, 18.0, 0.02, seed=11)
+    dev = torch.device("cuda")
+    g = sf.csr_build(n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+    _, lh = sf.lambda_max_estimate(g, 60, None, seed=3)
+    R = torch.as_tensor(synth.gaussian_block(n, eta, 21), dtype=torch.float32, device=dev)
+    mu = sf.cheb_moments(g, lh, R, p)
+    lk = sf.dichotomy(mu, p, lh, k - 0.5)
+    a = sf.cheb_coeffs(lh, lk, p, True)
+    Y = sf.cheb_filter(g, lh, a, R)[0]
+    Fe = sf.features(Y, True).cpu().numpy()
+    C0 = farthest_point_init(Fe, k, seed=2)
+    lab, _ = check_same(sf, oracle_mod, Fe, C0, 30, sf.KMEANS_AUTO)
+    # purity of the recovered communities (labels up to permutation)
+    truth = gr.labels
+    purity = sum(np.bincount(truth[lab == c]).max() for c in range(k) if (lab == c).any()) / n
+    assert purity > 0.9, purity
