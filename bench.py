@@ -703,9 +703,56 @@ def run_knn_grad(args, wl):
         "e2e": None,
         "gradient_check": {"directional_fd": fd, "adjoint": an, "rel_diff": abs(fd - an) / max(abs(fd), 1e-300),
                            "h": h},
+        "clustering": cluster_recovery(sf, g, lh, R, wl["k"], p, labels, seed=wl["r_seed"]),
     }
     print(json.dumps(out))
     return 0
+
+
+def adjusted_rand_index(a, b):
+    """Adjusted Rand index of two labelings (Hubert and Arabie, 1985)."""
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    _, ai = np.unique(a, return_inverse=True)
+    _, bi = np.unique(b, return_inverse=True)
+    table = np.zeros((ai.max() + 1, bi.max() + 1), np.int64)
+    np.add.at(table, (ai, bi), 1)
+    comb = lambda x: x * (x - 1) / 2.0  # noqa: E731
+    s_ij = comb(table).sum()
+    s_a = comb(table.sum(1)).sum()
+    s_b = comb(table.sum(0)).sum()
+    expected = s_a * s_b / comb(len(a))
+    top = 0.5 * (s_a + s_b)
+    return float((s_ij - expected) / (top - expected)) if top != expected else 1.0
+
+
+def cluster_recovery(sf, g, lh, R, k, p, truth, seed, restarts=10):
+    """§4.1 end to end on the graph: eigencount for lambda_k (count k - 1/2),
+    filter R at it, row-normalised features, k-means with several seeded
+    restarts (the lowest inertia kept); the adjusted Rand index against the
+    generating labels."""
+    import torch
+
+    n = R.shape[0]
+    mu = sf.cheb_moments(g, lh, R, p)
+    lk = sf.dichotomy(mu, p, lh, k - 0.5)
+    a = sf.cheb_coeffs(lh, lk, p, True)
+    F = sf.features(sf.cheb_filter(g, lh, a, R)[0], True)
+    rng = np.random.default_rng(seed)
+    best = None
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(restarts):
+        C0 = F[torch.as_tensor(rng.choice(n, k, replace=False), device=F.device)].contiguous()
+        lab, _, it, inertia = sf.kmeans(F, C0, 100)
+        if best is None or inertia < best[1]:
+            best = (lab, inertia, it)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"k": k, "lam_k_estimate": lk, "restarts": restarts, "kmeans_ms_total": e0.elapsed_time(e1),
+            "best_inertia": best[1], "assignments_of_best": best[2],
+            "ari_vs_generating_labels": adjusted_rand_index(best[0].cpu().numpy(), truth)}
 
 
 def run_batch(args, wl):
