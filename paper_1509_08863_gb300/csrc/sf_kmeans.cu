@@ -303,10 +303,21 @@ __global__ void km_chunk_sum_kernel(const float *F, int32_t d, int32_t k, const 
     const int32_t c = lo;
     const int32_t q = b - coffs[c];
     const int32_t r0 = offs[c] + q * kChunkRows;
-    const int32_t r1 = min(offs[c + 1], r0 + kChunkRows);
+    const int32_t cnt = min(offs[c + 1], r0 + kChunkRows) - r0;
+    __shared__ int32_t s_rows[kChunkRows];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) s_rows[t] = (int32_t)(uint32_t)(keys[r0 + t] & 0xffffffffu);
+    __syncthreads();
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         double s = 0.0;
-        for (int32_t r = r0; r < r1; ++r) s += (double)F[(int64_t)(uint32_t)(keys[r] & 0xffffffffu) * d + j];
+        int32_t r = 0;
+        for (; r + 8 <= cnt; r += 8) {  // eight loads in flight, added in row order
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = F[(int64_t)s_rows[r + u] * d + j];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += (double)v[u];
+        }
+        for (; r < cnt; ++r) s += (double)F[(int64_t)s_rows[r] * d + j];
         part[(int64_t)b * d + j] = s;
     }
 }
@@ -390,6 +401,7 @@ __global__ void __launch_bounds__(192, 1)
     __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tfull[2], s_tempty[2], s_bfull;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
+    __shared__ float s_cn2[128];  // |c|^2, +inf for the padding columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // 1024-byte aligned base for the swizzled tiles
     unsigned char *base = km_smem + ((1024u - (smem_u32(km_smem) & 1023u)) & 1023u);
@@ -411,6 +423,7 @@ __global__ void __launch_bounds__(192, 1)
         s_abort = 0;
         fence_mbar_init();
     }
+    for (int c = threadIdx.x; c < 128; c += blockDim.x) s_cn2[c] = (c < P.k) ? P.cn2[c] : INFINITY;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(2 * P.ncols)
@@ -476,8 +489,15 @@ __global__ void __launch_bounds__(192, 1)
             if (!tc_wait(&s_tfull[s], (uint32_t)(t >> 1) & 1u, abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int64_t row = (int64_t)tile * kTcRows + q * 32 + lane;
-            float b1 = INFINITY, b2 = INFINITY;
-            int32_t c1 = 0;
+            // four interleaved best / second-best trackers (columns u % 4), branch-free
+            float t1[4], t2[4];
+            int32_t tc[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                t1[v] = INFINITY;
+                t2[v] = INFINITY;
+                tc[v] = 0x7fffffff;
+            }
             for (int c0 = 0; c0 < P.nmma; c0 += 32) {
                 // two 16-column loads in flight, one wait
                 uint32_t r[32];
@@ -501,19 +521,27 @@ __global__ void __launch_bounds__(192, 1)
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
-                    const int c = c0 + u;
-                    if (c < P.k && (u < 16 || two)) {
-                        const float e = fmaf(-2.0f, __uint_as_float(r[u]), __ldg(P.cn2 + c));
-                        if (e < b1) {
-                            b2 = b1;
-                            b1 = e;
-                            c1 = c;
-                        } else if (e < b2) {
-                            b2 = e;
-                        }
+                    if (u < 16 || two) {
+                        const int v = u & 3;
+                        const float e = fmaf(-2.0f, __uint_as_float(r[u]), s_cn2[c0 + u]);  // +inf past k
+                        const bool lt = e < t1[v];  // strict: the earlier (lower) column keeps ties
+                        t2[v] = fminf(t2[v], fmaxf(t1[v], e));
+                        tc[v] = lt ? c0 + u : tc[v];
+                        t1[v] = fminf(t1[v], e);
                     }
                 }
             }
+            // merge: smallest value, ties to the lowest column; second = the others' best or the winner's second
+            int w = 0;
+#pragma unroll
+            for (int v = 1; v < 4; ++v)
+                if (t1[v] < t1[w] || (t1[v] == t1[w] && tc[v] < tc[w])) w = v;
+            const float b1 = t1[w];
+            const int32_t c1 = tc[w];
+            float b2 = t2[w];
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (v != w) b2 = fminf(b2, t1[v]);
             // the accumulator may be overwritten once every epilogue warp has read it
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
