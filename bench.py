@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-kmeans", action="store_true")
     ap.add_argument("--kernel-case", default=None,
-                    help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward, "
-                         "STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
+                    help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward|adjoint|"
+                         "kmeans, STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
     ap.add_argument("--filter-algo", default="auto", choices=["auto", "clenshaw", "forward"],
@@ -88,13 +88,43 @@ def run_kernel_case(args, wl):
     kind = {"tiled": sf.SWEEP_TILED, "direct": sf.SWEEP_DIRECT}[fields[5] if len(fields) > 5 else "tiled"]
     slab, warps, carve = int(slab), int(warps), int(carve)
     st = sf.BF16 if stor == "bf16" else sf.F32
+    dev = torch.device("cuda")
+    p = args.case_orders
+    if mode == "kmeans":
+        # Lloyd assignments on N unit rows of R columns (the workload's feature shape), k centroids
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        F = torch.randn(wl["n"], wl["R"], device=dev, generator=gen)
+        F /= F.norm(dim=1, keepdim=True)
+        for _ in range(2):
+            sf.kmeans(F, F[:wl["k"]].clone(), 2, sf.KMEANS_TENSOR)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": args.kernel_case, "status": "ok"}))
+        return 0
+    if mode == "adjoint":
+        # one slab of the filter's reverse mode on the kNN graph (p = case_orders)
+        from paper_1509_08863_gb300 import synth
+
+        src, dst, w, _, _ = synth.knn_mixture_edges(wl["n"], wl["k"], wl["dim"], wl["knn"], wl["sigma"], 3.0,
+                                                    wl["graph_seed"])
+        g = sf.csr_build(wl["n"], torch.as_tensor(src, device=dev), torch.as_tensor(dst, device=dev),
+                         torch.as_tensor(w, device=dev))
+        _, lh = sf.lambda_max_estimate(g, 60, None, seed=11)
+        Rs = torch.as_tensor(synth.gaussian_block(wl["n"], slab, wl["r_seed"]), dtype=torch.float32, device=dev)
+        Gs = torch.as_tensor(synth.standard_normal_block(wl["n"], slab, wl["g_seed"]), dtype=torch.float32,
+                             device=dev)
+        a = sf.cheb_coeffs(lh, 0.02 * lh, p, True)[0]
+        o = sf.Opts(slab_cols=slab, block_warps=warps, carveout_pct=carve, sweep_kernel=kind)
+        for _ in range(2):
+            sf.cheb_filter_backward(g, lh, a, Rs, Gs, False, o)
+        torch.cuda.synchronize()
+        sf.device_check()
+        print(json.dumps({"kernel_case": args.kernel_case, "orders": p, "status": "ok"}))
+        return 0
     algo = {"moments": sf.ALGO_CLENSHAW, "clenshaw": sf.ALGO_CLENSHAW, "forward": sf.ALGO_FORWARD}[mode]
     gr, R = make_inputs(wl)
-    dev = torch.device("cuda")
     g = sf.csr_build(wl["n"], torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
     Rs = torch.as_tensor(R[:, :slab], dtype=torch.float32, device=dev).contiguous()
     _, lh = sf.lambda_max_estimate(g, 40, None, seed=11)
-    p = args.case_orders
     a = sf.cheb_coeffs(lh, 0.05 * lh, p, True)
     o = sf.Opts(storage=st, algo=algo, slab_cols=slab, block_warps=warps, carveout_pct=carve, sweep_kernel=kind)
     for _ in range(2):
@@ -193,9 +223,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash():
+SWEEP_SOURCES = ("sf_internal.cuh", "sf_step.cuh", "sf_cheb.cu", "sf_sell.cu", "sf_adjoint.cu")
+
+
+def kernel_source_hash(sources=SWEEP_SOURCES):
+    """Hash of the CUDA sources a committed ncu figure depends on: the figure is
+    used only while the hash matches the one recorded with it."""
     h = hashlib.sha256()
-    for fn in ("sf_step.cuh", "sf_cheb.cu"):
+    for fn in sources:
         with open(os.path.join(ROOT, "paper_1509_08863_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -208,7 +243,7 @@ def traffic_from_profile(workload, variant):
     try:
         with open(path) as f:
             d = json.load(f)
-        if d.get("kernel_source_sha") == kernel_source_hash():
+        if d.get("kernel_source_sha") == kernel_source_hash(tuple(d.get("sources", SWEEP_SOURCES))):
             return d["variants"][variant]["dram_bytes_per_launch"]
     except Exception:
         pass
