@@ -15,6 +15,8 @@ follows. Parity status:
   estimate of lambda_k to compare with).
 * kmeans: pinned (brute-force argmin, numpy means, separated clusters,
   monotone inertia, ties).
+* normalize (+ cheb_filter on its result): pinned (closed-form normalised
+  spectra, the null vector, the dense spectral polynomial).
 """
 from __future__ import annotations
 
@@ -80,6 +82,11 @@ def _load():
                                          C.c_int64, _f64p, C.c_double, C.c_int32, C.c_double]
         lib.oracle_features.restype = None
         lib.oracle_features.argtypes = [C.c_int32, C.c_int64, _f64p, C.c_int32, _f64p]
+        lib.oracle_normalize.restype = None
+        lib.oracle_normalize.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+        lib.oracle_cheb_filter_diag.restype = None
+        lib.oracle_cheb_filter_diag.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, C.c_double, C.c_int32,
+                                                C.c_int32, _f64p, C.c_int64, _f64p, _f64p]
         lib.oracle_kmeans.restype = C.c_double
         lib.oracle_kmeans.argtypes = [C.c_int32, C.c_int32, C.c_int32, _f32p, _f32p, C.c_int32, _i32p,
                                       C.POINTER(C.c_int32)]
@@ -95,13 +102,16 @@ def _c(a, dt):
 
 
 class CSR:
-    """Symmetric CSR of W: rowptr int32[n+1], colidx int32[nnz], val float64[nnz]."""
+    """Symmetric CSR of W: rowptr int32[n+1], colidx int32[nnz], val float64[nnz];
+    `diag` (float64[n]) replaces the row sums as the diagonal of L when set
+    (the normalised Laplacian)."""
 
-    def __init__(self, n, rowptr, colidx, val):
+    def __init__(self, n, rowptr, colidx, val, diag=None):
         self.n = int(n)
         self.rowptr = rowptr
         self.colidx = colidx
         self.val = val
+        self.diag = diag
 
     @property
     def nnz(self) -> int:
@@ -190,8 +200,22 @@ def cheb_filter(g: CSR, lam_max: float, coeffs, R) -> np.ndarray:
     n_cut, p1 = a.shape
     n, n_sig = R.shape
     Y = np.zeros((n_cut, n, n_sig))
-    _load().oracle_cheb_filter(g.n, g.rowptr, g.colidx, g.val, lam_max, n_cut, p1 - 1, a, n_sig, R, Y)
+    if g.diag is None:
+        _load().oracle_cheb_filter(g.n, g.rowptr, g.colidx, g.val, lam_max, n_cut, p1 - 1, a, n_sig, R, Y)
+    else:
+        _load().oracle_cheb_filter_diag(g.n, g.rowptr, g.colidx, g.val, _c(g.diag, np.float64), lam_max, n_cut,
+                                        p1 - 1, a, n_sig, R, Y)
     return Y
+
+
+def normalize(g: CSR) -> CSR:
+    """The normalised Laplacian I - S^{-1/2} W S^{-1/2} (footnote of §2.1) as
+    weights w_ij / sqrt(s_i s_j) and an explicit unit diagonal (0 for isolated
+    nodes)."""
+    val = np.zeros_like(g.val)
+    diag = np.zeros(g.n)
+    _load().oracle_normalize(g.n, g.rowptr, g.colidx, _c(g.val, np.float64), val, diag)
+    return CSR(g.n, g.rowptr, g.colidx, val, diag)
 
 
 def moments(g: CSR, lam_max: float, R, m_max: int) -> np.ndarray:

@@ -273,12 +273,15 @@ void oracle_cheb_coeffs(double lam_max, double lc, int32_t p, int32_t jackson, d
 /* Fast filtering F^m_h R of (3) / (6) / (11).                               */
 /* ------------------------------------------------------------------------ */
 
-/* Y = Lt X for an n x c row-major block, Lt = (2 / lam_max) L - I. */
-static void lt_apply(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
-                     double lam_max, int64_t c, const double *X, double *Y) {
+/* Y = Lt X for an n x c row-major block, Lt = (2 / lam_max) L - I, with
+ * L = S - W; the diagonal S is the row sums of W unless `diag` gives it. */
+static void lt_apply_d(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                       const double *diag, double lam_max, int64_t c, const double *X, double *Y) {
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e];
+        if (diag) s = diag[i];
+        else
+            for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += val[e];
         for (int64_t r = 0; r < c; ++r) {
             double wx = 0.0;
             for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
@@ -287,6 +290,11 @@ static void lt_apply(int32_t n, const int32_t *rowptr, const int32_t *colidx, co
             Y[(int64_t)i * c + r] = (2.0 / lam_max) * lx - X[(int64_t)i * c + r];
         }
     }
+}
+
+static void lt_apply(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                     double lam_max, int64_t c, const double *X, double *Y) {
+    lt_apply_d(n, rowptr, colidx, val, NULL, lam_max, c, X, Y);
 }
 
 /*
@@ -558,4 +566,50 @@ double oracle_kmeans(int32_t n, int32_t d, int32_t k, const float *F, float *C, 
     free(sum);
     free(cnt);
     return inertia;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Normalised Laplacian (the footnote of §2.1: I - S^{-1/2} W S^{-1/2}).     */
+/* ------------------------------------------------------------------------ */
+
+/* Written as the weights w'_ij = w_ij / sqrt(s_i s_j) and the diagonal
+ * d_i = 1, or 0 for an isolated node (whose row of S^{-1/2} is taken as 0).
+ * Parity: pinned (spectrum of K_n, C_n and bipartite graphs, the null vector
+ * S^{1/2} 1, numpy's dense eigenvalues). */
+void oracle_normalize(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                      double *val_out, double *diag_out) {
+    double *s = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    oracle_strength(n, rowptr, colidx, val, s);
+    for (int32_t i = 0; i < n; ++i) {
+        diag_out[i] = s[i] > 0.0 ? 1.0 : 0.0;
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int32_t j = colidx[e];
+            const double ss = s[i] * s[j];
+            val_out[e] = ss > 0.0 ? val[e] / sqrt(ss) : 0.0;
+        }
+    }
+    free(s);
+}
+
+/* oracle_cheb_filter for L = diag(d) - W (the normalised Laplacian's form). */
+void oracle_cheb_filter_diag(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                             const double *diag, double lam_max, int32_t n_cut, int32_t p, const double *a,
+                             int64_t n_sig, const double *R, double *Y) {
+    int64_t sz = (int64_t)n * n_sig;
+    double *Tm2 = (double *)malloc(sizeof(double) * (size_t)(sz > 0 ? sz : 1));
+    double *Tm1 = (double *)malloc(sizeof(double) * (size_t)(sz > 0 ? sz : 1));
+    double *Tj = (double *)malloc(sizeof(double) * (size_t)(sz > 0 ? sz : 1));
+    for (int64_t t = 0; t < sz; ++t) Tm1[t] = R[t];
+    for (int32_t q = 0; q < n_cut; ++q)
+        for (int64_t t = 0; t < sz; ++t) Y[q * sz + t] = a[q * (p + 1) + 0] * Tm1[t];
+    for (int32_t j = 1; j <= p; ++j) {
+        lt_apply_d(n, rowptr, colidx, val, diag, lam_max, n_sig, Tm1, Tj);
+        if (j >= 2)
+            for (int64_t t = 0; t < sz; ++t) Tj[t] = 2.0 * Tj[t] - Tm2[t];
+        for (int32_t q = 0; q < n_cut; ++q)
+            for (int64_t t = 0; t < sz; ++t) Y[q * sz + t] += a[q * (p + 1) + j] * Tj[t];
+        double *tmp = Tm2; Tm2 = Tm1; Tm1 = Tj; Tj = tmp;
+    }
+    free(Tm2); free(Tm1); free(Tj);
 }

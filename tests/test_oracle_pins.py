@@ -514,3 +514,65 @@ def test_kmeans_ties_and_empty_clusters(oracle_mod):
     assert np.all(labels == 0)
     np.testing.assert_array_equal(C[1], C0[1])
     np.testing.assert_array_equal(C[2], C0[2])
+
+
+# ------------------------------------------------------------------ normalised Laplacian (footnote of §2.1)
+def _dense_from_csr(g):
+    """Dense L = diag(d) - W' of an oracle CSR (with its explicit diagonal when set)."""
+    n = g.n
+    W = np.zeros((n, n))
+    for i in range(n):
+        for e in range(g.rowptr[i], g.rowptr[i + 1]):
+            W[i, g.colidx[e]] = g.val[e]
+    d = W.sum(1) if g.diag is None else np.asarray(g.diag)
+    return np.diag(d) - W
+
+
+def test_normalized_laplacian_closed_form_spectra(oracle_mod):
+    """K_n: eigenvalues 0 and n/(n-1) (n-1 times); C_n (2-regular): 1 - cos(2 pi j / n);
+    a connected bipartite graph (star S_n) has eigenvalues 0, 1 (n-2 times) and 2."""
+    n = 9
+    s, d = np.triu_indices(n, 1)
+    ev = np.linalg.eigvalsh(_dense_from_csr(oracle_mod.normalize(oracle_mod.csr_build(n, s, d))))
+    np.testing.assert_allclose(ev, np.r_[0.0, np.full(n - 1, n / (n - 1))], atol=1e-12)
+    n = 11
+    s = np.arange(n)
+    ev = np.linalg.eigvalsh(_dense_from_csr(oracle_mod.normalize(oracle_mod.csr_build(n, s, (s + 1) % n))))
+    np.testing.assert_allclose(ev, np.sort(1 - np.cos(2 * np.pi * np.arange(n) / n)), atol=1e-12)
+    n = 7
+    ev = np.linalg.eigvalsh(_dense_from_csr(oracle_mod.normalize(oracle_mod.csr_build(n, np.zeros(n - 1, int),
+                                                                                        np.arange(1, n)))))
+    np.testing.assert_allclose(ev, np.r_[0.0, np.ones(n - 2), 2.0], atol=1e-12)
+
+
+def test_normalized_laplacian_matches_dense_definition(oracle_mod):
+    """Against I - S^{-1/2} W S^{-1/2} built densely from the edge list, with
+    an isolated node (its row and column stay 0): same matrix, null vector
+    S^{1/2} 1 on the connected part, spectrum inside [0, 2]."""
+    n = 60
+    src, dst, w = random_graph(n - 1, 400, 13)  # node n - 1 isolated
+    g = oracle_mod.csr_build(n, src, dst, w)
+    Ln = _dense_from_csr(oracle_mod.normalize(g))
+    W = dense_w(n, src, dst, w)
+    s = W.sum(1)
+    dinv = np.where(s > 0, 1.0 / np.sqrt(np.where(s > 0, s, 1.0)), 0.0)
+    ref = np.diag((s > 0).astype(float)) - dinv[:, None] * W * dinv[None, :]
+    np.testing.assert_allclose(Ln, ref, atol=1e-14)
+    np.testing.assert_allclose(Ln @ np.sqrt(s), 0.0, atol=1e-12)
+    ev = np.linalg.eigvalsh(Ln)
+    assert ev.min() > -1e-12 and ev.max() < 2 + 1e-12
+
+
+def test_filter_on_normalized_laplacian_equals_spectral_polynomial(oracle_mod):
+    """The explicit-diagonal filter equals chi P(Lt) chi^T R for the dense
+    normalised Laplacian (lam_hat = 2, its spectral bound)."""
+    n, p = 80, 30
+    src, dst, w = random_graph(n, 500, 17)
+    gn = oracle_mod.normalize(oracle_mod.csr_build(n, src, dst, w))
+    lam, chi = np.linalg.eigh(_dense_from_csr(gn))
+    lh = 2.0
+    a = oracle_mod.cheb_coeffs(lh, 0.4, p, True)[0]
+    R = np.random.default_rng(3).standard_normal((n, 5))
+    Y = oracle_mod.cheb_filter(gn, lh, a, R)[0]
+    ref = chi @ (cheb_eval(a, 2 * lam / lh - 1)[:, None] * (chi.T @ R))
+    np.testing.assert_allclose(Y, ref, atol=1e-11)
