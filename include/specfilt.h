@@ -177,6 +177,18 @@ SF_API sf_status sf_graph_csr(const sf_graph *g, const int32_t **rowptr, const i
  */
 SF_API sf_status sf_graph_set_values(sf_graph *g, const float *val, void *stream);
 
+/*
+ * The normalised Laplacian I - S^{-1/2} W S^{-1/2} (the footnote of §2.1,
+ * "other types of Laplacians, such as the normalized Laplacian") as a new
+ * graph: weights w_ij / sqrt(s_i s_j) (FP64, rounded to FP32) and an explicit
+ * diagonal 1 in place of the row sums (0 for an isolated node). Every
+ * filtering entry point then works on it unchanged (its spectrum lies in
+ * [0, 2], so sf_lambda_max_estimate's bound is 2); sf_graph_set_values and
+ * sf_cheb_filter_backward reject it. The caller frees *out with
+ * sf_graph_free. Synchronises `stream`.
+ */
+SF_API sf_status sf_graph_normalize(const sf_graph *g, void *stream, sf_graph **out);
+
 SF_API void sf_graph_free(sf_graph *g);
 
 /* ---------------------------------------------------------------------- */

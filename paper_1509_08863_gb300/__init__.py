@@ -155,6 +155,7 @@ def lib():
         "sf_profile_end": (_i32, [C.POINTER(_i64), _dp, _dp]),
         "sf_profile_variant": (_i32, [_i32, C.POINTER(_i64), _dp, _dp]),
         "sf_kmeans": (_i32, [_vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_i32), _dp, _vp]),
+        "sf_graph_normalize": (_i32, [_vp, _vp, C.POINTER(_vp)]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -262,6 +263,12 @@ class Graph:
 
         return (view(rp, (n + 1,), "<i4", torch.int32), view(ci, (nnz,), "<i4", torch.int32),
                 view(va, (nnz,), "<f4", torch.float32), view(st, (n,), "<f8", torch.float64))
+
+    def normalized(self) -> "Graph":
+        """The normalised Laplacian I - S^-1/2 W S^-1/2 (footnote of §2.1) as a new graph."""
+        out = _vp()
+        _check(lib().sf_graph_normalize(self._h, _stream(), C.byref(out)), "sf_graph_normalize")
+        return Graph(out.value)
 
     def set_values(self, val):
         torch = _torch()

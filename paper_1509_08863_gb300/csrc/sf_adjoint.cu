@@ -250,6 +250,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     SF_ARG(coeffs && R && G, "coeffs/R/G is NULL");
     SF_ARG(g->nnz == 0 || grad_val, "grad_val is NULL");
     SF_ARG(g->device == current_device(), "graph lives on another device");
+    SF_ARG(!g->normalized, "the adjoint needs L = S - W with S the row sums of W (not a normalised graph)");
     for (int j = 0; j <= p; ++j) SF_ARG(isfinite(coeffs[j]), "coefficient %d is not finite", j);
     sf_opts o = {};
     if (opts) o = *opts;

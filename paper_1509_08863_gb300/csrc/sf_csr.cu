@@ -205,6 +205,23 @@ sf_status radix_sort(uint64_t *&keys, float *&vals, uint64_t *&keys_alt, float *
     return SF_OK;
 }
 
+// Normalised Laplacian I - S^-1/2 W S^-1/2 (the footnote of §2.1): weights
+// w_ij / sqrt(s_i s_j) computed in FP64 and rounded to FP32, diagonal 1 (0 for
+// an isolated node). One thread per row.
+__global__ void normalize_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, const float *val,
+                                 const double *s, float *val_out, double *diag_out, int32_t *any) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double si = s[i];
+    diag_out[i] = si > 0.0 ? 1.0 : 0.0;
+    if (si > 0.0) *any = 1;
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const double ss = si * s[colidx[e]];
+        const double w = val ? (double)val[e] : 1.0;
+        val_out[e] = ss > 0.0 ? (float)(w / sqrt(ss)) : 0.0f;
+    }
+}
+
 static void graph_release(sf_graph *g) {
     if (!g) return;
     sell_release(&g->sell);
@@ -349,8 +366,55 @@ SF_API sf_status sf_graph_csr(const sf_graph *g, const int32_t **rowptr, const i
     return SF_OK;
 }
 
+SF_API sf_status sf_graph_normalize(const sf_graph *g, void *stream, sf_graph **out) {
+    SF_ARG(g && out, "graph/out is NULL");
+    SF_ARG(!g->normalized, "the graph is already normalised");
+    SF_ARG(g->device == current_device(), "graph lives on another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    sf_graph *h = new sf_graph();
+    h->n = g->n;
+    h->nnz = g->nnz;
+    h->unit_weights = 0;
+    h->normalized = 1;
+    h->device = g->device;
+    auto fail = [&](sf_status e) {
+        graph_release(h);
+        return e;
+    };
+    const size_t nz = (size_t)g->nnz + kCsrPad;
+    if (cudaMalloc(&h->rowptr, sizeof(int32_t) * (size_t)(g->n + 1 + kCsrPad)) != cudaSuccess ||
+        cudaMalloc(&h->colidx, sizeof(int32_t) * nz) != cudaSuccess ||
+        cudaMalloc(&h->val, sizeof(float) * nz) != cudaSuccess ||
+        cudaMalloc(&h->strength, sizeof(double) * (size_t)g->n) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation failed for the normalised graph");
+        return fail(SF_ERR_OOM);
+    }
+    sf_status st;
+    Scratch sc(s);
+    int32_t *any = nullptr;
+    if ((st = sc.get(&any, 1))) return fail(st);
+    if (cudaMemcpyAsync(h->rowptr, g->rowptr, sizeof(int32_t) * (size_t)(g->n + 1 + kCsrPad),
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->colidx, g->colidx, sizeof(int32_t) * nz, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(h->val, 0, sizeof(float) * nz, s) != cudaSuccess ||
+        cudaMemsetAsync(any, 0, sizeof(int32_t), s) != cudaSuccess)
+        return fail(cuda_fail(cudaGetLastError(), "copying the pattern"));
+    normalize_kernel<<<(g->n + 255) / 256, 256, 0, s>>>(g->n, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val,
+                                                        g->strength, h->val, h->strength, any);
+    if ((st = check_launch("normalize_kernel"))) return fail(st);
+    int32_t hany = 0;
+    if (cudaMemcpyAsync(&hany, any, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(cuda_fail(cudaGetLastError(), "reading the normalised graph"));
+    h->max_strength = hany ? 1.0 : 0.0;
+    *out = h;
+    return SF_OK;
+}
+
 SF_API sf_status sf_graph_set_values(sf_graph *g, const float *val, void *stream) {
     SF_ARG(g, "graph is NULL");
+    SF_ARG(!g->normalized, "a normalised graph keeps the weights it was built with (normalise the new weights)");
     SF_ARG(g->nnz == 0 || val, "val is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nnz > 0)

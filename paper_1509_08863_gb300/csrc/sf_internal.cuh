@@ -162,6 +162,7 @@ struct sf_graph {
     double *strength = nullptr;
     double max_strength = 0.0;
     int32_t unit_weights = 1;
+    int32_t normalized = 0;  // the diagonal (strength) is 1 / 0, not the row sums: I - S^-1/2 W S^-1/2
     int device = 0;
     mutable SellMatrix sell;
     mutable std::mutex sell_mu;

@@ -545,3 +545,37 @@ def test_gather_ceiling_diagnostic(sf):
     for bad in ((0, 64, 32), (1000, 48, 32), (1000, 64, 30), (1000, 64, 0)):
         with pytest.raises(sf.SpecFiltError):
             sf.gather_ceiling(*bad, 1)
+
+
+def test_normalized_laplacian_matches_oracle(sf, oracle_mod):
+    """The normalised graph (footnote of §2.1): weights equal the oracle's
+    rounded to FP32, unit diagonal (0 for the isolated node), lam_max <= 2 (= 2
+    on a bipartite graph), filter and moments within the FP32 bounds of the
+    oracle's explicit-diagonal filter; the adjoint and set_values refuse it."""
+    n, n_sig, p = 2001, 21, 40
+    src, dst, w = random_graph(n - 1, 16000, 41)  # node n - 1 isolated
+    g, go = build_both(sf, oracle_mod, n, src, dst, w)
+    gn = g.normalized()
+    gno = oracle_mod.normalize(go)
+    rp, ci, va, st = gn.csr()
+    np.testing.assert_array_equal(va.cpu().numpy(), gno.val.astype(np.float32))
+    np.testing.assert_array_equal(st.cpu().numpy(), gno.diag)
+    th, lh = sf.lambda_max_estimate(gn, 80, None, seed=4)
+    assert th <= 2.0 + 1e-9 and lh <= 2.0
+    R = np.random.default_rng(8).standard_normal((n, n_sig)) / math.sqrt(n_sig)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    a = oracle_mod.cheb_coeffs(lh, [0.2 * lh, 0.5 * lh], p, True)
+    Yo = oracle_mod.cheb_filter(gno, lh, a, R)
+    for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+        Y = sf.cheb_filter(gn, lh, a, Rt, sf.Opts(algo=algo)).cpu().numpy()
+        for c in range(2):
+            assert rel(Y[c], Yo[c]) <= 1e-5
+    # bipartite (a star): the normalised spectrum reaches 2
+    m = 50
+    gs = sf.csr_build(m, *cuda_edges(np.zeros(m - 1, int), np.arange(1, m)))
+    th_s, _ = sf.lambda_max_estimate(gs.normalized(), m, None, seed=1)
+    assert abs(th_s - 2.0) <= 1e-6  # the weights 1/sqrt(s_i s_j) are rounded to FP32
+    with pytest.raises(sf.SpecFiltError):
+        sf.cheb_filter_backward(gn, lh, a[0], Rt, Rt, False)
+    with pytest.raises(sf.SpecFiltError):
+        gn.set_values(va)
