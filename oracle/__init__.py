@@ -87,6 +87,14 @@ def _load():
         lib.oracle_cheb_filter_diag.restype = None
         lib.oracle_cheb_filter_diag.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, C.c_double, C.c_int32,
                                                 C.c_int32, _f64p, C.c_int64, _f64p, _f64p]
+        lib.oracle_adjusted_rand.restype = C.c_double
+        lib.oracle_adjusted_rand.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.c_int32]
+        lib.oracle_stability.restype = None
+        lib.oracle_stability.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int64, _f64p,
+                                         C.c_int32, _f64p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                         _f64p, _f64p]
+        lib.oracle_stability_init_row.restype = C.c_int32
+        lib.oracle_stability_init_row.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         lib.oracle_kmeans.restype = C.c_double
         lib.oracle_kmeans.argtypes = [C.c_int32, C.c_int32, C.c_int32, _f32p, _f32p, C.c_int32, _i32p,
                                       C.POINTER(C.c_int32)]
@@ -305,3 +313,30 @@ def kmeans(F, C0, max_iter: int):
     iters = C.c_int32(0)
     inertia = lib.oracle_kmeans(n, d, k, F, cent, int(max_iter), labels, C.byref(iters))
     return labels, cent, iters.value, inertia
+
+
+def adjusted_rand(a, b) -> float:
+    """Adjusted Rand index of two labelings (§4.3 uses it in Eq. (12))."""
+    a = _c(a, np.int32)
+    b = _c(b, np.int32)
+    return _load().oracle_adjusted_rand(len(a), a, b, int(a.max()) + 1, int(b.max()) + 1)
+
+
+def stability(g: CSR, lam_max: float, p: int, Rc, R_blocks, kmin: int, kmax: int, max_iter: int, seed: int,
+              starts: int = 1):
+    """gamma(k) of §4.3 / Eq. (12) for k = kmin..kmax (and the lam_k used):
+    J = len(R_blocks) realisations of the filtered signals, count probes Rc,
+    k-means from `starts` seeded starts per clustering (lowest inertia kept)."""
+    Rc = _c(Rc, np.float64)
+    R = _c(np.stack(R_blocks), np.float64)
+    J, n, eta = R.shape
+    K = kmax - kmin + 1
+    gamma = np.zeros(K)
+    lam_k = np.zeros(K)
+    _load().oracle_stability(g.n, g.rowptr, g.colidx, g.val, lam_max, p, eta, Rc, J, R, kmin, kmax, max_iter,
+                             int(starts), int(seed), gamma, lam_k)
+    return gamma, lam_k
+
+
+def stability_init_row(seed: int, j: int, k: int, t: int, c: int, n: int) -> int:
+    return _load().oracle_stability_init_row(int(seed), j, k, t, c, n)

@@ -613,3 +613,120 @@ void oracle_cheb_filter_diag(int32_t n, const int32_t *rowptr, const int32_t *co
     }
     free(Tm2); free(Tm1); free(Tj);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Stability of the clusterings (§4.3, Eq. (12)).                            */
+/* ------------------------------------------------------------------------ */
+
+/* Adjusted Rand index of two labelings (Hubert and Arabie 1985), from the
+ * contingency table n_uv and its margins, with x(x - 1)/2 pair counts:
+ * (sum n_uv choose 2 - E) / (max - E), E = (sum a_u choose 2)(sum b_v choose 2)
+ * / (n choose 2), max = ((sum a_u choose 2) + (sum b_v choose 2)) / 2; 1 when
+ * max = E (both labelings trivial). Labels in [0, ka) and [0, kb).
+ * Parity: pinned (brute-force pair counting, identity and permutations). */
+double oracle_adjusted_rand(int32_t n, const int32_t *a, const int32_t *b, int32_t ka, int32_t kb) {
+    int64_t *t = (int64_t *)calloc((size_t)ka * (size_t)kb, sizeof(int64_t));
+    int64_t *ra = (int64_t *)calloc((size_t)ka, sizeof(int64_t));
+    int64_t *rb = (int64_t *)calloc((size_t)kb, sizeof(int64_t));
+    for (int32_t i = 0; i < n; ++i) {
+        t[(int64_t)a[i] * kb + b[i]] += 1;
+        ra[a[i]] += 1;
+        rb[b[i]] += 1;
+    }
+    double sij = 0.0, sa = 0.0, sb = 0.0;
+    for (int64_t u = 0; u < (int64_t)ka * kb; ++u) sij += 0.5 * (double)t[u] * (double)(t[u] - 1);
+    for (int32_t u = 0; u < ka; ++u) sa += 0.5 * (double)ra[u] * (double)(ra[u] - 1);
+    for (int32_t v = 0; v < kb; ++v) sb += 0.5 * (double)rb[v] * (double)(rb[v] - 1);
+    free(t);
+    free(ra);
+    free(rb);
+    const double pairs = 0.5 * (double)n * (double)(n - 1);
+    const double expct = pairs > 0.0 ? sa * sb / pairs : 0.0;
+    const double top = 0.5 * (sa + sb);
+    return (top == expct) ? 1.0 : (sij - expct) / (top - expct);
+}
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) of counter i under `seed`:
+ * z = seed + (i + 1) * 0x9E3779B97F4A7C15, then two xor-shift-multiply rounds.
+ * The stability measure's k-means starts use it to pick rows. */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Initial centroid c of start t of realisation j for k clusters: row
+ * splitmix64_at(seed, (j << 40) | (k << 20) | (t << 10) | c) mod n
+ * (k < 2^20, t < 2^10, c < 2^10). */
+int32_t oracle_stability_init_row(uint64_t seed, int32_t j, int32_t k, int32_t t, int32_t c, int32_t n) {
+    const uint64_t ctr = ((uint64_t)j << 40) | ((uint64_t)k << 20) | ((uint64_t)t << 10) | (uint64_t)c;
+    return (int32_t)(splitmix64_at(seed, ctr) % (uint64_t)n);
+}
+
+/* The stability measure of §4.3, Eq. (12), step by step: for every k in
+ * [kmin, kmax], lam_k by the dichotomy of §3.2 on the count probes Rc (target
+ * k - 1/2); for every realisation j of the eta signals (R_j, block j of R),
+ * the filtered block at lam_k (Jackson-damped coefficients, order p), its
+ * normalised rows rounded to FP32, and k-means (oracle_kmeans, max_iter) from
+ * `starts` sets of rows that oracle_stability_init_row picks, keeping the
+ * lowest inertia (the first on ties); gamma(k) = the mean adjusted Rand
+ * index over the J (J - 1) / 2 pairs of realisations (equal to the mean over
+ * ordered pairs i != j of Eq. (12)). gamma and lam_k have kmax - kmin + 1
+ * entries. Parity: its parts are pinned; the composition is checked on graphs
+ * with a clear cluster structure (gamma = 1 at the true k). */
+void oracle_stability(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                      double lam_max, int32_t p, int64_t eta, const double *Rc, int32_t J, const double *R,
+                      int32_t kmin, int32_t kmax, int32_t max_iter, int32_t starts, uint64_t seed, double *gamma,
+                      double *lam_k) {
+    const int32_t K = kmax - kmin + 1;
+    const int64_t sz = (int64_t)n * eta;
+    double *a = (double *)malloc(sizeof(double) * (size_t)K * (size_t)(p + 1));
+    for (int32_t q = 0; q < K; ++q) {
+        lam_k[q] = oracle_dichotomy(n, rowptr, colidx, val, lam_max, p, 1, eta, Rc, (double)(kmin + q) - 0.5, 40,
+                                    1e-9);
+        oracle_cheb_coeffs(lam_max, lam_k[q], p, 1, a + (int64_t)q * (p + 1));
+    }
+    double *Y = (double *)malloc(sizeof(double) * (size_t)(K * sz > 0 ? K * sz : 1));
+    double *Fd = (double *)malloc(sizeof(double) * (size_t)(sz > 0 ? sz : 1));
+    float *F = (float *)malloc(sizeof(float) * (size_t)(sz > 0 ? sz : 1));
+    float *C = (float *)malloc(sizeof(float) * (size_t)kmax * (size_t)eta);
+    int32_t *labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)J * K * (size_t)(n > 0 ? n : 1));
+    int32_t *trial = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int32_t j = 0; j < J; ++j) {
+        oracle_cheb_filter(n, rowptr, colidx, val, lam_max, K, p, a, eta, R + (int64_t)j * sz, Y);
+        for (int32_t q = 0; q < K; ++q) {
+            const int32_t k = kmin + q;
+            oracle_features(n, eta, Y + (int64_t)q * sz, 1, Fd);
+            for (int64_t t = 0; t < sz; ++t) F[t] = (float)Fd[t];
+            int32_t *lab = labels + ((int64_t)j * K + q) * n;
+            double best = INFINITY;
+            for (int32_t st = 0; st < starts; ++st) {
+                for (int32_t c = 0; c < k; ++c) {
+                    const int32_t r = oracle_stability_init_row(seed, j, k, st, c, n);
+                    for (int64_t t = 0; t < eta; ++t) C[(int64_t)c * eta + t] = F[(int64_t)r * eta + t];
+                }
+                for (int32_t i = 0; i < n; ++i) trial[i] = -1;
+                int32_t it = 0;
+                const double inertia = oracle_kmeans(n, (int32_t)eta, k, F, C, max_iter, trial, &it);
+                if (inertia < best) {
+                    best = inertia;
+                    for (int32_t i = 0; i < n; ++i) lab[i] = trial[i];
+                }
+            }
+        }
+    }
+    for (int32_t q = 0; q < K; ++q) {
+        const int32_t k = kmin + q;
+        double acc = 0.0;
+        int64_t pairs = 0;
+        for (int32_t i = 0; i < J; ++i)
+            for (int32_t j = i + 1; j < J; ++j) {
+                acc += oracle_adjusted_rand(n, labels + ((int64_t)i * K + q) * n, labels + ((int64_t)j * K + q) * n,
+                                            k, k);
+                ++pairs;
+            }
+        gamma[q] = pairs > 0 ? acc / (double)pairs : 1.0;
+    }
+    free(a); free(Y); free(Fd); free(F); free(C); free(labels); free(trial);
+}

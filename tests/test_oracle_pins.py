@@ -576,3 +576,71 @@ def test_filter_on_normalized_laplacian_equals_spectral_polynomial(oracle_mod):
     Y = oracle_mod.cheb_filter(gn, lh, a, R)[0]
     ref = chi @ (cheb_eval(a, 2 * lam / lh - 1)[:, None] * (chi.T @ R))
     np.testing.assert_allclose(Y, ref, atol=1e-11)
+
+
+# ------------------------------------------------------------------ stability (§4.3, Eq. (12))
+def _ari_bruteforce(a, b):
+    """Adjusted Rand index by counting every pair of items (Hubert and Arabie):
+    pairs together in both, in a only, in b only."""
+    n = len(a)
+    both = in_a = in_b = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            sa, sb = a[i] == a[j], b[i] == b[j]
+            both += sa and sb
+            in_a += sa
+            in_b += sb
+    pairs = n * (n - 1) / 2
+    expected = in_a * in_b / pairs
+    top = 0.5 * (in_a + in_b)
+    return 1.0 if top == expected else (both - expected) / (top - expected)
+
+
+def test_adjusted_rand_index(oracle_mod):
+    rng = np.random.default_rng(9)
+    for n, ka, kb in ((40, 3, 4), (57, 5, 2), (25, 1, 3)):
+        a = rng.integers(0, ka, n)
+        b = rng.integers(0, kb, n)
+        assert oracle_mod.adjusted_rand(a, b) == pytest.approx(_ari_bruteforce(a, b), abs=1e-12)
+    a = rng.integers(0, 6, 500)
+    assert oracle_mod.adjusted_rand(a, a) == 1.0
+    assert oracle_mod.adjusted_rand(a, (a * 5 + 1) % 6) == pytest.approx(1.0)  # relabelled
+    assert abs(oracle_mod.adjusted_rand(a, rng.integers(0, 6, 500))) < 0.05
+
+
+def test_stability_peaks_at_the_true_number_of_clusters(oracle_mod):
+    """Eq. (12) on k well-separated communities (dense blocks, few links
+    between them), k-means with 8 seeded starts per clustering: every
+    realisation finds the same partition at the true k (gamma = 1), and the
+    other candidates are less stable."""
+    k, m = 4, 40
+    n = k * m
+    rng = np.random.default_rng(21)
+    src, dst = [], []
+    for c in range(k):
+        for i in range(m):
+            for j in range(i + 1, m):
+                if rng.random() < 0.5:
+                    src.append(c * m + i)
+                    dst.append(c * m + j)
+    for _ in range(12):  # sparse links between communities
+        u, v = rng.integers(0, n, 2)
+        src.append(u)
+        dst.append(v)
+    g = oracle_mod.csr_build(n, np.array(src), np.array(dst))
+    s = oracle_mod.strength(g)
+    th = oracle_mod.lanczos_max(g, 60, rng.standard_normal(n))
+    lh = oracle_mod.lambda_hat(th, s)
+    eta = 12
+    Rc = rng.standard_normal((n, eta)) / np.sqrt(eta)
+    Rs = [rng.standard_normal((n, eta)) / np.sqrt(eta) for _ in range(4)]
+    gamma, lam_k = oracle_mod.stability(g, lh, 60, Rc, Rs, 2, 6, 50, 7, starts=8)
+    assert gamma[k - 2] == pytest.approx(1.0)
+    assert np.argmax(gamma) == k - 2
+    assert np.all(np.diff(lam_k) >= 0)  # more clusters, higher cutoff
+    # the init rule is SplitMix64 (Steele, Lea and Flood 2014) of the packed counter, mod n
+    z = (7 + (((1 << 40) | (3 << 20) | (5 << 10) | 2) + 1) * 0x9E3779B97F4A7C15) & (2**64 - 1)
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2**64 - 1)
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2**64 - 1)
+    z ^= z >> 31
+    assert oracle_mod.stability_init_row(7, 1, 3, 5, 2, n) == z % n
