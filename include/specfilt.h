@@ -481,6 +481,44 @@ enum {
 SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int32_t k, float *C, int32_t max_iter,
                            int32_t mode, int32_t *labels, int32_t *iters, double *inertia, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Stability of the clusterings (§4.3, Eq. (12))                           */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Adjusted Rand index (Hubert and Arabie 1985) of two labelings, the
+ * similarity §4.3 averages in Eq. (12).
+ *   a, b    device int32[n], labels in [0, ka) and [0, kb) (SF_ERR_ARG otherwise)
+ *   ka, kb  label ranges, ka * kb <= 2^24
+ *   ari     host out
+ * Contingency counts on the device (integer atomics: deterministic), the
+ * formula in FP64 on the host. Synchronises `stream`.
+ */
+SF_API sf_status sf_adjusted_rand(const int32_t *a, const int32_t *b, int32_t n, int32_t ka, int32_t kb,
+                                  void *stream, double *ari);
+
+/*
+ * gamma(k) of §4.3, Eq. (12), for k = kmin..kmax: the mean adjusted Rand
+ * index between the clusterings of J realisations of the eta random signals.
+ *   Rc          device float[N][eta]: the count's probe block; lam_k is the
+ *               dichotomy of the moments for the count k - 1/2 (one moment
+ *               sweep serves every k)
+ *   R           device float[J][N][eta]: the J realisations; each is filtered
+ *               at every lam_k in one forward sweep (order p, Jackson damping),
+ *               its rows are normalised and clustered by sf_kmeans into k
+ *               clusters from `starts` seeded starts (lowest inertia kept)
+ *   max_iter    k-means assignments per start
+ *   seed        start rows: SplitMix64 (Steele, Lea, Flood 2014) of
+ *               (j << 40) | (k << 20) | (t << 10) | c, modulo N, for start t
+ *               of realisation j, centroid c
+ *   opts        block storage and tiles of the sweeps (the algorithm is forward)
+ *   gamma       host out double[kmax - kmin + 1]; lam_k host out, same length
+ * Needs J >= 2, 1 <= kmin <= kmax <= 1023, starts <= 1023. Synchronises `stream`.
+ */
+SF_API sf_status sf_stability(const sf_graph *g, double lam_max, int32_t p, const float *Rc, const float *R,
+                              int32_t J, int32_t eta, int32_t kmin, int32_t kmax, int32_t max_iter, int32_t starts,
+                              uint64_t seed, const sf_opts *opts, void *stream, double *gamma, double *lam_k);
+
 /*
  * Measured ceiling of the sweep's gather pattern. A diagnostic with no
  * counterpart in the paper: it times a kernel that does nothing but the

@@ -156,6 +156,9 @@ def lib():
         "sf_profile_variant": (_i32, [_i32, C.POINTER(_i64), _dp, _dp]),
         "sf_kmeans": (_i32, [_vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_i32), _dp, _vp]),
         "sf_graph_normalize": (_i32, [_vp, _vp, C.POINTER(_vp)]),
+        "sf_adjusted_rand": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _dp]),
+        "sf_stability": (_i32, [_vp, _f64, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _i32, C.c_uint64, _vp, _vp,
+                                _dp, _dp]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -539,6 +542,34 @@ def kmeans(F, C0, max_iter: int = 50, mode: int = KMEANS_AUTO):
     _check(lib().sf_kmeans(_dev_ptr(Fd, torch.float32, "F"), int(n), int(d), int(k), Cw.data_ptr(), int(max_iter),
                            int(mode), labels.data_ptr(), C.byref(it), C.byref(inertia), _stream()), "sf_kmeans")
     return labels, Cw, it.value, inertia.value
+
+
+def adjusted_rand(a, b, ka: int | None = None, kb: int | None = None) -> float:
+    """Adjusted Rand index of two int32 label tensors on the device."""
+    torch = _torch()
+    ka = int(a.max().item()) + 1 if ka is None else ka
+    kb = int(b.max().item()) + 1 if kb is None else kb
+    r = _f64()
+    _check(lib().sf_adjusted_rand(_dev_ptr(a, torch.int32, "a"), _dev_ptr(b, torch.int32, "b"), int(a.shape[0]),
+                                  int(ka), int(kb), _stream(), C.byref(r)), "sf_adjusted_rand")
+    return r.value
+
+
+def stability(g: Graph, lam_max: float, p: int, Rc, R, kmin: int, kmax: int, max_iter: int = 50,
+              starts: int = 4, seed: int = 0, opts: Opts | None = None):
+    """gamma(k) of §4.3 / Eq. (12) for k = kmin..kmax and the lam_k used:
+    count probes Rc [N, eta], realisations R [J, N, eta] (FP32, on the device)."""
+    torch = _torch()
+    J, n, eta = R.shape
+    K = kmax - kmin + 1
+    gamma = np.zeros(K)
+    lam_k = np.zeros(K)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_stability(g.handle, float(lam_max), int(p), _dev_ptr(Rc, torch.float32, "Rc"),
+                              _dev_ptr(R, torch.float32, "R"), int(J), int(eta), int(kmin), int(kmax), int(max_iter),
+                              int(starts), int(seed), op, _stream(), gamma.ctypes.data_as(_dp),
+                              lam_k.ctypes.data_as(_dp)), "sf_stability")
+    return gamma, lam_k
 
 
 def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> float:
