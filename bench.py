@@ -739,6 +739,7 @@ def run_knn_grad(args, wl):
         "gradient_check": {"directional_fd": fd, "adjoint": an, "rel_diff": abs(fd - an) / max(abs(fd), 1e-300),
                            "h": h},
         "clustering": cluster_recovery(sf, g, lh, R, wl["k"], p, labels, seed=wl["r_seed"]),
+        "stability": stability_leg(sf, g, lh, p, n, eta, wl["k"], seed=wl["r_seed"]),
     }
     print(json.dumps(out))
     return 0
@@ -759,6 +760,28 @@ def adjusted_rand_index(a, b):
     expected = s_a * s_b / comb(len(a))
     top = 0.5 * (s_a + s_b)
     return float((s_ij - expected) / (top - expected)) if top != expected else 1.0
+
+
+def stability_leg(sf, g, lh, p, n, eta, k, seed, J=4, half_width=2, starts=4):
+    """gamma(k) of §4.3 / Eq. (12) around the generating k, J realisations."""
+    import torch
+
+    from paper_1509_08863_gb300 import synth
+
+    Rc = torch.as_tensor(synth.gaussian_block(n, eta, seed + 101), dtype=torch.float32, device="cuda")
+    R = torch.as_tensor(np.stack([synth.gaussian_block(n, eta, seed + 200 + j) for j in range(J)]),
+                        dtype=torch.float32, device="cuda")
+    kmin, kmax = max(2, k - half_width), k + half_width
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gamma, lam_k = sf.stability(g, lh, p, Rc, R, kmin, kmax, 50, starts, seed)
+    e1.record()
+    torch.cuda.synchronize()
+    ks = list(range(kmin, kmax + 1))
+    return {"k": ks, "gamma": [float(x) for x in gamma], "lam_k": [float(x) for x in lam_k],
+            "k_star": ks[int(np.argmax(gamma))], "generating_k": k, "realisations": J, "starts": starts,
+            "ms": e0.elapsed_time(e1)}
 
 
 def cluster_recovery(sf, g, lh, R, k, p, truth, seed, restarts=10):
