@@ -146,13 +146,18 @@ __global__ void km_assign_kernel(const float *F, int32_t n, int32_t d, const flo
 // stride d + 1: no bank conflicts). The 16 lanes of a row group then keep the
 // smallest score, ties to the lowest centroid.
 constexpr int kExRows = 32;
+// Row stride of the staged rows: d + 1 (scalar loads, no bank conflicts), or
+// d + 4 with 16-byte loads when d is a multiple of 4.
+__host__ __device__ constexpr int ex_ld(int d, bool v4) { return v4 ? d + 4 : d + 1; }
+
+template <bool V4>
 __global__ void __launch_bounds__(128) km_assign_blocked_kernel(const float *F, int32_t n, int32_t d, const float *C,
                                                                 int32_t k, const int32_t *list, const int32_t *count,
                                                                 int32_t *labels, int32_t *changed) {
-    extern __shared__ float s_ex[];
-    const int ld = d + 1;
-    float *sC = s_ex;                // [128][d + 1], rows >= k zero
-    float *sF = s_ex + 128 * ld;     // [32][d + 1]
+    extern __shared__ __align__(16) float s_ex[];
+    const int ld = ex_ld(d, V4);
+    float *sC = s_ex;                // [128][ld], rows >= k zero
+    float *sF = s_ex + 128 * ld;     // [32][ld]
     for (int t = threadIdx.x; t < 128 * d; t += blockDim.x) {
         const int c = t / d, j = t % d;
         sC[c * ld + j] = (c < k) ? C[(int64_t)c * d + j] : 0.0f;
@@ -178,19 +183,42 @@ __global__ void __launch_bounds__(128) km_assign_blocked_kernel(const float *F, 
             for (int m = 0; m < 8; ++m) acc[r][m] = 0.0f;
         const float *fr = sF + (4 * g) * ld;
         const float *cr = sC + h * ld;
-        for (int j = 0; j < d; ++j) {
-            float fv[4], cv[8];
+        if (V4) {
+            for (int j = 0; j < d; j += 4) {  // four columns per load, still added in index order
+                float4 fv[4], cv[8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) fv[r] = fr[r * ld + j];
+                for (int r = 0; r < 4; ++r) fv[r] = *reinterpret_cast<const float4 *>(fr + r * ld + j);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) cv[m] = cr[(16 * m) * ld + j];
+                for (int m = 0; m < 8; ++m) cv[m] = *reinterpret_cast<const float4 *>(cr + (16 * m) * ld + j);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const float t = __fsub_rn(fv[r], cv[m]);
-                    acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
-                }
+                    for (int m = 0; m < 8; ++m) {
+                        float t = __fsub_rn(fv[r].x, cv[m].x);
+                        acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                        t = __fsub_rn(fv[r].y, cv[m].y);
+                        acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                        t = __fsub_rn(fv[r].z, cv[m].z);
+                        acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                        t = __fsub_rn(fv[r].w, cv[m].w);
+                        acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                    }
+            }
+        } else {
+            for (int j = 0; j < d; ++j) {
+                float fv[4], cv[8];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) fv[r] = fr[r * ld + j];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) cv[m] = cr[(16 * m) * ld + j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const float t = __fsub_rn(fv[r], cv[m]);
+                        acc[r][m] = __fmaf_rn(t, t, acc[r][m]);
+                    }
+            }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -696,22 +724,24 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     // exact-decision kernel: register-blocked for k <= 128 and d <= 256, else a warp per row with the
     // centroids in shared memory when they fit
     const bool blocked = k <= 128 && d <= 256;
-    const size_t ex_smem = (size_t)(128 + kExRows) * (d + 1) * sizeof(float);
+    const bool ex_v4 = d % 4 == 0;
+    const size_t ex_smem = (size_t)(128 + kExRows) * ex_ld(d, ex_v4) * sizeof(float);
+    const void *ex_fn = ex_v4 ? (const void *)km_assign_blocked_kernel<true> : (const void *)km_assign_blocked_kernel<false>;
     const size_t c_smem = (size_t)k * (d + 1) * sizeof(float);
     const int smem_c = c_smem <= 160 * 1024 ? 1 : 0;
     if (blocked)
-        SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ex_smem));
+        SF_CHECK_CUDA(cudaFuncSetAttribute(ex_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex_smem));
     else if (smem_c)
         SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)c_smem));
     int ex_occ = 1;
-    if (blocked) SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ex_occ, km_assign_blocked_kernel, 128,
-                                                                             ex_smem));
+    if (blocked) SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ex_occ, ex_fn, 128, ex_smem));
     const int assign_grid = blocked ? (ex_occ > 0 ? ex_occ : 1) * sm_count() : (smem_c ? sm_count() : 4 * sm_count());
     auto exact = [&](const int32_t *lst, const int32_t *cnt) -> sf_status {
-        if (blocked)
-            km_assign_blocked_kernel<<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
+        if (blocked && ex_v4)
+            km_assign_blocked_kernel<true><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
+        else if (blocked)
+            km_assign_blocked_kernel<false><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
         else
             km_assign_kernel<<<assign_grid, 256, smem_c ? c_smem : 0, s>>>(F, n, d, C, k, lst, cnt, labels, changed,
                                                                            smem_c);

@@ -74,6 +74,10 @@ def test_kmeans_tensor_cores_match_oracle(sf, oracle_mod, d, k):
 def test_kmeans_other_shapes_use_cuda_cores(sf, oracle_mod):
     F, C0 = mixture(1500, 48, 200, seed=5)  # d not a multiple of 32, k > 128
     check_same(sf, oracle_mod, F, C0, 6, sf.KMEANS_AUTO)
+    F, C0 = mixture(900, 30, 9, seed=6)  # d not a multiple of 4: scalar shared-memory loads
+    check_same(sf, oracle_mod, F, C0, 6, sf.KMEANS_AUTO)
+    F, C0 = mixture(700, 300, 5, seed=7)  # d > 256: a warp per row
+    check_same(sf, oracle_mod, F, C0, 4, sf.KMEANS_AUTO)
     with pytest.raises(sf.SpecFiltError):
         sf.kmeans(torch.as_tensor(F, device="cuda"), torch.as_tensor(C0, device="cuda"), 3, sf.KMEANS_TENSOR)
 
