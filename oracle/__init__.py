@@ -17,6 +17,8 @@ follows. Parity status:
   monotone inertia, ties).
 * normalize (+ cheb_filter on its result): pinned (closed-form normalised
   spectra, the null vector, the dense spectral polynomial).
+* adjusted_rand, stability, cheb_order: pinned (brute-force pair counting;
+  gamma peaking at the true k; numpy's chebval on the same grid).
 """
 from __future__ import annotations
 
@@ -95,6 +97,8 @@ def _load():
                                          _f64p, _f64p]
         lib.oracle_stability_init_row.restype = C.c_int32
         lib.oracle_stability_init_row.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+        lib.oracle_cheb_order.restype = C.c_int32
+        lib.oracle_cheb_order.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32]
         lib.oracle_kmeans.restype = C.c_double
         lib.oracle_kmeans.argtypes = [C.c_int32, C.c_int32, C.c_int32, _f32p, _f32p, C.c_int32, _i32p,
                                       C.POINTER(C.c_int32)]
@@ -340,3 +344,9 @@ def stability(g: CSR, lam_max: float, p: int, Rc, R_blocks, kmin: int, kmax: int
 
 def stability_init_row(seed: int, j: int, k: int, t: int, c: int, n: int) -> int:
     return _load().oracle_stability_init_row(int(seed), j, k, t, c, n)
+
+
+def cheb_order(x: float, delta: float, w: float, jackson: bool = True, p_max: int = 1000) -> int:
+    """m*(lambda_c / lambda_N; delta) of §2.4 with the band |t - x| < w left out
+    (-1 when no order up to p_max meets delta)."""
+    return _load().oracle_cheb_order(float(x), float(delta), float(w), int(bool(jackson)), int(p_max))

@@ -730,3 +730,42 @@ void oracle_stability(int32_t n, const int32_t *rowptr, const int32_t *colidx, c
     }
     free(a); free(Y); free(Fd); free(F); free(C); free(labels); free(trial);
 }
+
+/* ------------------------------------------------------------------------ */
+/* The order m* of §2.4 (criterion (4)), tabulated against lambda_c/lambda_N. */
+/* ------------------------------------------------------------------------ */
+
+/* Smallest order m in [1, p_max] whose (optionally Jackson-damped) Chebyshev
+ * approximation P_m of the ideal low-pass h_x on [0, 1] (h = 1 for t <= x,
+ * else 0) satisfies |h(t) - P_m(t)| <= delta at every point t of the grid
+ * g / 4095 (g = 0..4095) and of the band edges x - w, x + w that lies in
+ * [0, 1] with |t - x| >= w; -1 when no order up to p_max does. P_m(t) =
+ * sum_j a_j cos(j arccos(2t - 1)), each T_j evaluated directly. The paper's
+ * sup over [0, lambda_N] cannot fall below 1/2 at the jump, so the band of
+ * half-width w around x is left out. Parity: pinned (numpy's chebval on the
+ * same grid, monotonicity in delta and w). */
+int32_t oracle_cheb_order(double x, double delta, double w, int32_t jackson, int32_t p_max) {
+    double *a = (double *)malloc(sizeof(double) * (size_t)(p_max + 1));
+    double pts[4098];
+    int32_t np = 0;
+    for (int32_t gi = 0; gi < 4096; ++gi) pts[np++] = (double)gi / 4095.0;
+    if (x - w >= 0.0) pts[np++] = x - w;
+    if (x + w <= 1.0) pts[np++] = x + w;
+    int32_t found = -1;
+    for (int32_t m = 1; m <= p_max && found < 0; ++m) {
+        oracle_cheb_coeffs(1.0, x, m, jackson, a);
+        double worst = 0.0;
+        for (int32_t q = 0; q < np; ++q) {
+            const double t = pts[q];
+            if (fabs(t - x) < w) continue;
+            const double y = acos(fmin(1.0, fmax(-1.0, 2.0 * t - 1.0)));
+            double v = 0.0;
+            for (int32_t j = 0; j <= m; ++j) v += a[j] * cos((double)j * y);
+            const double e = fabs((t <= x ? 1.0 : 0.0) - v);
+            if (e > worst) worst = e;
+        }
+        if (worst <= delta) found = m;
+    }
+    free(a);
+    return found;
+}

@@ -644,3 +644,30 @@ def test_stability_peaks_at_the_true_number_of_clusters(oracle_mod):
     z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2**64 - 1)
     z ^= z >> 31
     assert oracle_mod.stability_init_row(7, 1, 3, 5, 2, n) == z % n
+
+
+# ------------------------------------------------------------------ order table m* (§2.4, criterion (4))
+def test_cheb_order_matches_chebval_search(oracle_mod):
+    """m* against a search with numpy's Chebyshev evaluation (library routine)
+    on the same points, and its monotonicity: a looser tolerance or a wider
+    excluded band never needs a higher order."""
+    def search(x, delta, w, jackson, p_max=400):
+        t = np.r_[np.arange(4096) / 4095.0, [x - w] if x - w >= 0 else [], [x + w] if x + w <= 1 else []]
+        t = t[np.abs(t - x) >= w]
+        h = (t <= x).astype(float)
+        for m in range(1, p_max + 1):
+            a = oracle_mod.cheb_coeffs(1.0, x, m, jackson)[0]
+            if np.max(np.abs(h - cheb_eval(a, 2 * t - 1))) <= delta:
+                return m
+        return -1
+
+    for x, delta, w, jk in ((0.3, 0.1, 0.05, True), (0.1, 0.1, 0.02, True), (0.7, 0.05, 0.1, True),
+                            (0.5, 0.2, 0.1, False)):
+        assert oracle_mod.cheb_order(x, delta, w, jk, 400) == search(x, delta, w, jk)
+    base = oracle_mod.cheb_order(0.2, 0.1, 0.03)
+    assert oracle_mod.cheb_order(0.2, 0.2, 0.03) <= base
+    assert oracle_mod.cheb_order(0.2, 0.1, 0.06) <= base
+    # the undamped series overshoots by ~9% just outside the jump (Gibbs): with a band too narrow to hide the
+    # first overshoot, delta = 0.05 is out of reach; the damped series (a positive kernel) never overshoots
+    assert oracle_mod.cheb_order(0.4, 0.05, 1e-4, False, 300) == -1
+    assert oracle_mod.cheb_order(0.4, 0.05, 0.01, True, 2000) > 0
