@@ -192,6 +192,22 @@ SF_API sf_status sf_graph_normalize(const sf_graph *g, void *stream, sf_graph **
 SF_API void sf_graph_free(sf_graph *g);
 
 /* ---------------------------------------------------------------------- */
+/* The order m* (§2.4, criterion (4))                                      */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * The smallest order m in [1, p_max] whose Chebyshev approximation (Jackson-
+ * damped when `jackson`) of the ideal low-pass h_x on [0, 1] (h = 1 for
+ * t <= x) stays within delta of h at every point t of the grid g / 4095
+ * (g = 0..4095) and the band edges x +- w with |t - x| >= w; *m_star = -1 when
+ * no order up to p_max does. x = lambda_c / lambda_N. The criterion of §2.4
+ * takes the sup over all of [0, lambda_N], which no polynomial can bring
+ * below 1/2 at the jump: the band of half-width w (a fraction of lambda_N)
+ * around it is left out. Host only; the paper's tolerance is delta = 0.1.
+ */
+SF_API sf_status sf_cheb_order(double x, double delta, double w, int32_t jackson, int32_t p_max, int32_t *m_star);
+
+/* ---------------------------------------------------------------------- */
 /* lambda_N (§4.1 step 1)                                                  */
 /* ---------------------------------------------------------------------- */
 

@@ -159,6 +159,7 @@ def lib():
         "sf_adjusted_rand": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _dp]),
         "sf_stability": (_i32, [_vp, _f64, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _i32, C.c_uint64, _vp, _vp,
                                 _dp, _dp]),
+        "sf_cheb_order": (_i32, [_f64, _f64, _f64, _i32, _i32, C.POINTER(_i32)]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -570,6 +571,14 @@ def stability(g: Graph, lam_max: float, p: int, Rc, R, kmin: int, kmax: int, max
                               int(starts), int(seed), op, _stream(), gamma.ctypes.data_as(_dp),
                               lam_k.ctypes.data_as(_dp)), "sf_stability")
     return gamma, lam_k
+
+
+def cheb_order(x: float, delta: float, w: float, jackson: bool = True, p_max: int = 1000) -> int:
+    """m*(lambda_c / lambda_N; delta) of §2.4 with the band |t - x| < w left out (-1: none up to p_max)."""
+    m = _i32()
+    _check(lib().sf_cheb_order(float(x), float(delta), float(w), int(bool(jackson)), int(p_max), C.byref(m)),
+           "sf_cheb_order")
+    return m.value
 
 
 def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> float:

@@ -1,6 +1,8 @@
 // Status handling, allocation, scans and reductions, host-side FP64 math
 // (coefficients, counts from moments, dichotomy), profiling hooks.
 #include <math.h>
+
+#include <vector>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -346,6 +348,43 @@ SF_API sf_status sf_dichotomy(const double *moments, int32_t p, double lam_max, 
         else lo = mid;
     }
     *lam_k = hi;
+    return SF_OK;
+}
+
+SF_API sf_status sf_cheb_order(double x, double delta, double w, int32_t jackson, int32_t p_max, int32_t *m_star) {
+    SF_ARG(m_star, "m_star is NULL");
+    SF_ARG(x >= 0.0 && x <= 1.0, "x = lambda_c / lambda_N must lie in [0, 1]");
+    SF_ARG(delta > 0.0 && w >= 0.0 && p_max >= 1 && p_max <= 100000, "need delta > 0, w >= 0, 1 <= p_max <= 100000");
+    // evaluation points: the uniform grid g / 4095 and the band edges, outside the band |t - x| < w
+    std::vector<double> pts;
+    pts.reserve(4098);
+    for (int gi = 0; gi < 4096; ++gi) pts.push_back((double)gi / 4095.0);
+    if (x - w >= 0.0) pts.push_back(x - w);
+    if (x + w <= 1.0) pts.push_back(x + w);
+    std::vector<double> a((size_t)p_max + 1);
+    *m_star = -1;
+    for (int m = 1; m <= p_max; ++m) {
+        cheb_coeffs_host(1.0, x, m, jackson, a.data());
+        double worst = 0.0;
+        for (double t : pts) {
+            if (fabs(t - x) < w) continue;
+            // Clenshaw: b_j = a_j + 2 y b_{j+1} - b_{j+2}; P = a_0 + y b_1 - b_2
+            const double y = 2.0 * t - 1.0;
+            double b1 = 0.0, b2 = 0.0;
+            for (int j = m; j >= 1; --j) {
+                const double b0 = a[j] + 2.0 * y * b1 - b2;
+                b2 = b1;
+                b1 = b0;
+            }
+            const double v = a[0] + y * b1 - b2;
+            const double e = fabs((t <= x ? 1.0 : 0.0) - v);
+            if (e > worst) worst = e;
+        }
+        if (worst <= delta) {
+            *m_star = m;
+            break;
+        }
+    }
     return SF_OK;
 }
 

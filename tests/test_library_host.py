@@ -75,3 +75,13 @@ def test_argument_errors_without_gpu(sflib):
     st = L.sf_cheb_coeffs(-1.0, cut.ctypes.data_as(C.POINTER(C.c_double)), 1, 2, 1,
                           out.ctypes.data_as(C.POINTER(C.c_double)))
     assert st == 1 and b"lam_max" in L.sf_last_error()
+
+
+def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
+    """The order table m* of §2.4 (host FP64, Clenshaw evaluation) equals the
+    oracle's (direct cos(j arccos) evaluation) on a spread of cutoffs."""
+    for x in (0.01, 0.05, 0.2, 0.5, 0.9):
+        for delta, w in ((0.1, 0.01), (0.1, 0.05), (0.05, 0.02)):
+            assert sflib.cheb_order(x, delta, w, True, 800) == oracle_mod.cheb_order(x, delta, w, True, 800)
+    with pytest.raises(sflib.SpecFiltError):
+        sflib.cheb_order(1.5, 0.1, 0.01)
