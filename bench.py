@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-kmeans", action="store_true")
     ap.add_argument("--kernel-case", default=None,
                     help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward|adjoint|"
-                         "kmeans, STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
+                         "kmeans|batched, STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
     ap.add_argument("--filter-algo", default="auto", choices=["auto", "clenshaw", "forward"],
@@ -116,6 +116,25 @@ def run_kernel_case(args, wl):
         o = sf.Opts(slab_cols=slab, block_warps=warps, carveout_pct=carve, sweep_kernel=kind)
         for _ in range(2):
             sf.cheb_filter_backward(g, lh, a, Rs, Gs, False, o)
+        torch.cuda.synchronize()
+        sf.device_check()
+        print(json.dumps({"kernel_case": args.kernel_case, "orders": p, "status": "ok"}))
+        return 0
+    if mode == "batched":
+        # the 256-graph batch, one forward sweep launch per order for all graphs (p = case_orders)
+        from paper_1509_08863_gb300 import synth
+
+        graphs, _ = synth.batched_sbm(wl["n_graphs"], wl["graph_seed"])
+        gs = [sf.csr_build(gr.n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+              for gr in graphs]
+        lams = np.array([sf.lambda_max_estimate(g, 40, None, seed=11)[1] for g in gs])
+        b = sf.batch_build(gs)
+        n_tot = b.info()[0]
+        Rb = torch.as_tensor(synth.gaussian_block(n_tot, slab, wl["r_seed"]), dtype=torch.float32, device=dev)
+        coeffs = np.stack([sf.cheb_coeffs(lams[i], 0.1 * lams[i], p, True)[0] for i in range(len(gs))])
+        o = sf.Opts(storage=st, slab_cols=slab, block_warps=warps, carveout_pct=carve, sweep_kernel=kind)
+        for _ in range(2):
+            sf.cheb_filter_batched(b, lams, coeffs, Rb, o)
         torch.cuda.synchronize()
         sf.device_check()
         print(json.dumps({"kernel_case": args.kernel_case, "orders": p, "status": "ok"}))
