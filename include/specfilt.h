@@ -536,6 +536,16 @@ SF_API sf_status sf_stability(const sf_graph *g, double lam_max, int32_t p, cons
                               uint64_t seed, const sf_opts *opts, void *stream, double *gamma, double *lam_k);
 
 /*
+ * Self-test of the failure path (no counterpart in the paper): one block
+ * waits on an mbarrier that nothing completes, gives up after `polls` polls
+ * (1..2^20) and sets the device status word exactly as a sweep kernel whose
+ * staged copy never landed would; the next sf_device_check then returns
+ * SF_ERR_TIMEOUT and clears the word. Nothing faults and the context stays
+ * usable. Asynchronous on `stream`.
+ */
+SF_API sf_status sf_selftest_bounded_wait(int32_t polls, void *stream);
+
+/*
  * Measured ceiling of the sweep's gather pattern. A diagnostic with no
  * counterpart in the paper: it times a kernel that does nothing but the
  * sweep's data movement without its arithmetic -- for every output row, sum

@@ -160,6 +160,7 @@ def lib():
         "sf_stability": (_i32, [_vp, _f64, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _i32, C.c_uint64, _vp, _vp,
                                 _dp, _dp]),
         "sf_cheb_order": (_i32, [_f64, _f64, _f64, _i32, _i32, C.POINTER(_i32)]),
+        "sf_selftest_bounded_wait": (_i32, [_i32, _vp]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -588,6 +589,11 @@ def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> flo
     _check(lib().sf_gather_ceiling(int(n_rows), int(row_bytes), int(deg), int(reps), _stream(), C.byref(r)),
            "sf_gather_ceiling")
     return r.value
+
+
+def selftest_bounded_wait(polls: int = 1000):
+    """Make a kernel's bounded wait give up (nothing faults); the next device_check raises SF_ERR_TIMEOUT."""
+    _check(lib().sf_selftest_bounded_wait(int(polls), _stream()), "sf_selftest_bounded_wait")
 
 
 def device_check():

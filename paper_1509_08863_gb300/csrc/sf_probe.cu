@@ -1,9 +1,10 @@
-// Gather ceiling (sf_gather_ceiling): the sweep kernel's random-row data
-// movement alone, timed on synthetic data, as the practical ceiling its
-// launches are compared with.
+// Diagnostics: the gather ceiling (sf_gather_ceiling), the sweep kernel's
+// random-row data movement alone, timed on synthetic data, as the practical
+// ceiling its launches are compared with; and the self-test of the bounded
+// waits (sf_selftest_bounded_wait).
 #include <math.h>
 
-#include "sf_internal.cuh"
+#include "sf_step.cuh"
 
 namespace sf {
 
@@ -83,9 +84,32 @@ static void probe_launch(int grid, cudaStream_t s, const uint16_t *T, const int3
     probe_gather_kernel<LPR><<<grid, 256, 0, s>>>(T, idx, n, deg, out);
 }
 
+// One block waits on an mbarrier that nothing ever completes, with the same
+// try-wait the sweep kernels use, gives up after `polls` polls and sets the
+// device status word as a sweep kernel whose staged copy never landed would.
+__global__ void selftest_wait_kernel(int32_t polls, int32_t *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool landed = false;
+    for (int32_t i = 0; i < polls && !landed; ++i) landed = mbar_try_wait(&bar, 0);
+    if (!landed && threadIdx.x == 0) atomicOr(status, 1);
+}
+
 }  // namespace sf
 
 using namespace sf;
+
+extern "C" SF_API sf_status sf_selftest_bounded_wait(int32_t polls, void *stream) {
+    SF_ARG(polls >= 1 && polls <= (1 << 20), "polls must be in [1, 2^20]");
+    int32_t *status = device_status();
+    SF_ARG(status, "device status word unavailable");
+    selftest_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(polls, status);
+    return check_launch("selftest_wait_kernel");
+}
 
 extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps,
                                               void *stream, double *rows_per_s) {

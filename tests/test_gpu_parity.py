@@ -579,3 +579,20 @@ def test_normalized_laplacian_matches_oracle(sf, oracle_mod):
         sf.cheb_filter_backward(gn, lh, a[0], Rt, Rt, False)
     with pytest.raises(sf.SpecFiltError):
         gn.set_values(va)
+
+
+def test_bounded_wait_gives_up_without_fault(sf, oracle_mod):
+    """A wait that can never be satisfied gives up after its poll budget, the
+    host reads SF_ERR_TIMEOUT, the flag clears, and the context keeps working."""
+    sf.selftest_bounded_wait(2000)
+    with pytest.raises(sf.SpecFiltError) as e:
+        sf.device_check()
+    assert e.value.status == 4  # SF_ERR_TIMEOUT
+    sf.device_check()  # cleared
+    gr = config1_graph()
+    g = sf.csr_build(gr.n, *cuda_edges(gr.src, gr.dst))
+    _, lh = sf.lambda_max_estimate(g, 30, None, seed=1)
+    R = torch.ones((gr.n, 8), device="cuda")
+    Y = sf.cheb_filter(g, lh, sf.cheb_coeffs(lh, 0.3 * lh, 10, True), R)
+    sf.device_check()
+    assert torch.isfinite(Y).all()
