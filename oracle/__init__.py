@@ -11,8 +11,8 @@ follows. Parity status:
 
 * csr_build, strength, lanczos_max, cheb_coeffs, jackson, cheb_filter,
   moments, eigencount, features, cheb_filter_backward: pinned (CPU tests).
-* dichotomy: parity unpinned beyond self-consistency (the paper prints no
-  estimate of lambda_k to compare with).
+* dichotomy: pinned (exact counts with the identity as the signal block
+  against a bisection on the dense spectrum).
 * kmeans: pinned (brute-force argmin, numpy means, separated clusters,
   monotone inertia, ties).
 * normalize (+ cheb_filter on its result): pinned (closed-form normalised

@@ -378,7 +378,8 @@ void oracle_eigencount(int32_t n, const int32_t *rowptr, const int32_t *colidx, 
  * count(lc) >= k, found by bisection (each count computed by a full filter of
  * R as in oracle_eigencount), stopping after max_iter halvings or when the
  * bracket is narrower than tol * lam_max. Returns the upper end.
- * Parity unpinned beyond self-consistency: the paper prints no lambda_k.
+ * Parity: pinned (with the identity as the signal block the count is exactly
+ * tr(P(Lt)^2), and the result equals a bisection on the dense spectrum).
  */
 double oracle_dichotomy(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                         double lam_max, int32_t p, int32_t jackson, int64_t n_sig, const double *R,

@@ -357,6 +357,38 @@ def test_dichotomy_on_disjoint_cliques(oracle_mod):
     assert oracle_mod.eigencount(g, lam_max, a_lo, R)[0] < k - 0.5
 
 
+def test_dichotomy_matches_spectral_bisection(oracle_mod):
+    """With the identity as the signal block the count is exact,
+    ||F I||_F^2 = tr(P(Lt)^2) = sum_l P(lt_l)^2, so the dichotomy must land on
+    the cutoff an independent bisection finds from the dense spectrum (numpy's
+    eigensolver and Chebyshev evaluation), for targets between and on the
+    plateaus of the count."""
+    n = 48
+    src, dst, w = random_graph(n, 260, 5)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, dst, w)))
+    lam_max = 1.01 * lam[-1]
+    p = 40
+    R = np.eye(n)
+
+    def count(lc):
+        a = oracle_mod.cheb_coeffs(lam_max, lc, p, True)[0]
+        return float(np.sum(cheb_eval(a, 2 * lam / lam_max - 1) ** 2))
+
+    for target in (2.5, 7.2, 15.5, 30.0):
+        lo, hi = 0.0, lam_max
+        for _ in range(40):
+            if hi - lo <= 1e-9 * lam_max:
+                break
+            mid = 0.5 * (lo + hi)
+            if count(mid) >= target:
+                hi = mid
+            else:
+                lo = mid
+        got = oracle_mod.dichotomy(g, lam_max, p, R, target, True, 40, 1e-9)
+        assert got == pytest.approx(hi, rel=1e-12, abs=1e-12)
+
+
 # --------------------------------------------------------------------------
 # Features (6)/(11)
 # --------------------------------------------------------------------------
