@@ -11,8 +11,10 @@
 //    (TF32 operands staged by TMA in 128-byte swizzled shared memory, FP32
 //    accumulators in TMEM), e_c = |c_c|^2 - 2 G_ic; the row takes the tensor
 //    argmin when its two best candidates are further apart than twice the
-//    bound on |e_c + |f_i|^2 - d(f_i, c_c)|, and is otherwise queued for the
-//    CUDA-core decision. Both give the same labels.
+//    bound on |e_c + |f_i|^2 - d(f_i, c_c)|, and is otherwise queued with the
+//    set of centroids within that margin of its best (no other centroid can
+//    win in FP32), which km_assign_cands_kernel then decides exactly. Both
+//    give the same labels.
 // Bound: TF32 keeps 10 mantissa bits (truncation error < 2^-10 per operand),
 // so |G_ic - f_i.c_c| <= (2^-9 + 2^-16) |f_i| |c_c| with FP32 accumulation
 // of 128 products; |c|^2 and the FP32 sum d carry <= 2^-16 (|f| + |c|)^2.
@@ -251,6 +253,63 @@ __global__ void __launch_bounds__(128) km_assign_blocked_kernel(const float *F, 
     }
 }
 
+// The exact decision for queued rows over their candidate centroids only
+// (cmask bits, from the tensor-core pass): a warp per row, lanes over the
+// candidates in increasing order, each an FP32 fused-multiply-add chain in
+// index order; the smallest score wins, ties to the lowest centroid. Centroids
+// staged in shared memory with row stride d + 1.
+__global__ void km_assign_cands_kernel(const float *F, int32_t d, const float *C, int32_t k, const int32_t *list,
+                                       const int32_t *count, const uint32_t *cmask, int32_t *labels,
+                                       int32_t *changed) {
+    extern __shared__ float s_cc[];
+    const int32_t ldc = d + 1;
+    for (int64_t t = threadIdx.x; t < (int64_t)k * d; t += blockDim.x) s_cc[(t / d) * ldc + t % d] = C[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)*count;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t i = list[w];
+        const uint4 m4 = *reinterpret_cast<const uint4 *>(cmask + w * 4);
+        const uint32_t m[4] = {m4.x, m4.y, m4.z, m4.w};
+        const int n0 = __popc(m[0]), n1 = __popc(m[1]), n2 = __popc(m[2]);
+        const int ncand = n0 + n1 + n2 + __popc(m[3]);
+        const float *f = F + (int64_t)i * d;
+        float bd = INFINITY;
+        int32_t bc = 0x7fffffff;
+        for (int t = lane; t < ncand; t += 32) {  // the t-th candidate in increasing order
+            int q = 0, rem = t;
+            if (rem >= n0) { rem -= n0; q = 1; if (rem >= n1) { rem -= n1; q = 2; if (rem >= n2) { rem -= n2; q = 3; } } }
+            uint32_t bits = m[q];
+            for (int r = 0; r < rem; ++r) bits &= bits - 1u;
+            const int c = q * 32 + (__ffs(bits) - 1);
+            const float *cc = s_cc + (int64_t)c * ldc;
+            float acc = 0.f;
+            for (int j = 0; j < d; ++j) {
+                const float tt = __fsub_rn(__ldg(f + j), cc[j]);
+                acc = __fmaf_rn(tt, tt, acc);
+            }
+            if (acc < bd || (acc == bd && c < bc)) {
+                bd = acc;
+                bc = c;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, bd, off);
+            const int32_t oc = __shfl_xor_sync(0xffffffffu, bc, off);
+            if (od < bd || (od == bd && oc < bc)) {
+                bd = od;
+                bc = oc;
+            }
+        }
+        if (lane == 0) {
+            if (labels[i] != bc) *changed = 1;
+            labels[i] = bc;
+        }
+    }
+}
+
 // inertia partials: part[b] = sum over this block's rows (block order) of d(f_i, c_label_i)
 __global__ void km_inertia_kernel(const float *F, int32_t n, int32_t d, const float *C, const int32_t *labels,
                                   double *part) {
@@ -402,6 +461,7 @@ struct TcParams {
     int32_t *labels;
     int32_t *changed;
     int32_t *list;                 // rows left to the exact decision
+    uint32_t *cmask;               // [list slot][4]: the centroids each queued row must still compare
     int32_t *count;
     int32_t *status;               // bit 0: a bounded wait gave up
 };
@@ -570,27 +630,56 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int v = 0; v < 4; ++v)
                 if (v != w) b2 = fminf(b2, t1[v]);
-            // the accumulator may be overwritten once every epilogue warp has read it
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_tempty[s]);
             bool queue = false;
+            float e_bound = 0.0f;
             if (row < P.n) {
                 const float fi = __ldg(P.fn + row);
-                const float e_bound = 0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax);
+                e_bound = 0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax);
                 queue = P.k > 1 && !(b2 - b1 > 2.0f * e_bound);
                 if (!queue) {
                     if (P.labels[row] != c1) *P.changed = 1;
                     P.labels[row] = c1;
                 }
             }
-            // one queue slot reservation per warp
+            // a queued row keeps the centroids not provably worse than its best, e_c - e_best <= 2 E_i
+            // (a second read of the accumulator); any other centroid's FP32 distance exceeds the best's
+            uint32_t cm[4] = {0u, 0u, 0u, 0u};
             const unsigned qm = __ballot_sync(0xffffffffu, queue);
+            if (qm) {
+                const float tau = b1 + 2.0f * e_bound;
+                for (int c0 = 0; c0 < P.nmma; c0 += 16) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + (uint32_t)s * P.ncols + (uint32_t)c0 + ((uint32_t)(q * 32) << 16);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int c = c0 + u;
+                        const float e = fmaf(-2.0f, __uint_as_float(r[u]), s_cn2[c]);  // +inf past k
+                        if (e <= tau) cm[c >> 5] |= 1u << (c & 31);
+                    }
+                }
+            }
+            // the accumulator may be overwritten once every epilogue warp has read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_tempty[s]);
+            // one queue slot reservation per warp
             if (qm) {
                 int32_t slot0 = 0;
                 if (lane == 0) slot0 = atomicAdd(P.count, __popc(qm));
                 slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-                if (queue) P.list[slot0 + __popc(qm & ((1u << lane) - 1u))] = (int32_t)row;
+                if (queue) {
+                    const int32_t slot = slot0 + __popc(qm & ((1u << lane) - 1u));
+                    P.list[slot] = (int32_t)row;
+                    *reinterpret_cast<uint4 *>(P.cmask + (int64_t)slot * 4) = make_uint4(cm[0], cm[1], cm[2], cm[3]);
+                }
             }
         }
     }
@@ -675,6 +764,7 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
     float *fn = nullptr, *cn2 = nullptr, *cmax = nullptr;
+    uint32_t *cmask = nullptr;
     int32_t *changed = nullptr, *bad = nullptr, *list = nullptr, *count = nullptr, *offs = nullptr, *coffs = nullptr;
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     double *part = nullptr, *ipart = nullptr, *isum = nullptr;
@@ -704,6 +794,8 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         if ((st = encode_rows(&mapF, F, n, d, kTcRows)) || (st = encode_rows(&mapC, C, k, d, nmma))) return st;
         tc_smem = tc_smem_bytes(d, nmma);
         SF_CHECK_CUDA(cudaFuncSetAttribute(kmeans_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+        SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_cands_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)((size_t)k * (d + 1) * sizeof(float))));
         const int n_tiles = (n + kTcRows - 1) / kTcRows;
         tc_grid = n_tiles < sm_count() ? n_tiles : sm_count();
         T.n = n;
@@ -718,6 +810,8 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         T.changed = changed;
         T.list = list;
         T.count = count;
+        if ((st = sc.get(&cmask, (size_t)n * 4))) return st;
+        T.cmask = cmask;
         T.status = device_status();
         SF_ARG(T.status, "device status word unavailable");
     }
@@ -766,7 +860,9 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
                 profile_record(ea, eb, (double)n * d * 4 + (double)tc_grid * k * d * 4 + (double)n * 8,
                                kProfTagKmeansTc);
             }
-            if ((st = exact(list, count))) return st;
+            km_assign_cands_kernel<<<4 * sm_count(), 256, (size_t)k * (d + 1) * sizeof(float), s>>>(
+                F, d, C, k, list, count, cmask, labels, changed);
+            if ((st = check_launch("km_assign_cands_kernel"))) return st;
         } else {
             if ((st = exact(nullptr, nullptr))) return st;
         }
