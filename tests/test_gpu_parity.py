@@ -384,6 +384,27 @@ def test_backward_matches_oracle(sf, oracle_mod, ckpt):
     assert rel(gR.cpu().numpy(), gR_o) <= 2e-5
 
 
+@pytest.mark.parametrize("slab", [8, 32, 64, 128])
+def test_backward_lane_widths_and_unit_weights(sf, oracle_mod, slab):
+    """Every lane-group width of the sampled-product kernel (2, 8, 16, 32 lanes
+    per row), on a ragged size (N = 1037, 21 signals: a partial slab) and on
+    unit weights (the unweighted sweep path)."""
+    n, n_sig, p = 1037, 21, 13
+    src, dst, _ = random_graph(n, 6000, 37)
+    g, go = build_both(sf, oracle_mod, n, src, dst, None)
+    lh = 2.0 * oracle_mod.strength(go).max()
+    rng = np.random.default_rng(slab)
+    R = rng.standard_normal((n, n_sig)).astype(np.float32)
+    G = rng.standard_normal((n, n_sig)).astype(np.float32)
+    a = oracle_mod.cheb_coeffs(lh, 0.3 * lh, p, True)[0]
+    gv_o, ga_o, gR_o = oracle_mod.cheb_filter_backward(go, lh, a, R.astype(np.float64), G.astype(np.float64), True)
+    gv, ga, gR = sf.cheb_filter_backward(g, lh, a, torch.as_tensor(R, device="cuda"), torch.as_tensor(G, device="cuda"),
+                                         True, sf.Opts(slab_cols=slab))
+    assert rel(gv.cpu().numpy(), gv_o) <= 2e-4
+    assert rel(ga, ga_o) <= 2e-5
+    assert rel(gR.cpu().numpy(), gR_o) <= 2e-5
+
+
 def test_backward_checkpoint_equals_store(sf, oracle_mod):
     n, n_sig, p = 900, 20, 30
     src, dst, w = random_graph(n, 6000, 41)
