@@ -11,10 +11,10 @@
 //    (TF32 operands staged by TMA in 128-byte swizzled shared memory, FP32
 //    accumulators in TMEM), e_c = |c_c|^2 - 2 G_ic; the row takes the tensor
 //    argmin when its two best candidates are further apart than twice the
-//    bound on |e_c + |f_i|^2 - d(f_i, c_c)|, and is otherwise queued with the
-//    set of centroids within that margin of its best (no other centroid can
-//    win in FP32), which km_assign_cands_kernel then decides exactly. Both
-//    give the same labels.
+//    bound on |e_c + |f_i|^2 - d(f_i, c_c)|, and is otherwise queued with a
+//    superset of the centroids within that margin of its best (no other
+//    centroid can win in FP32), which km_assign_cands_kernel then decides
+//    exactly. Both give the same labels.
 // Bound: TF32 keeps 10 mantissa bits (truncation error < 2^-10 per operand),
 // so |G_ic - f_i.c_c| <= (2^-9 + 2^-16) |f_i| |c_c| with FP32 accumulation
 // of 128 products; |c|^2 and the FP32 sum d carry <= 2^-16 (|f| + |c|)^2.
@@ -577,9 +577,15 @@ __global__ void __launch_bounds__(192, 1)
             if (!tc_wait(&s_tfull[s], (uint32_t)(t >> 1) & 1u, abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int64_t row = (int64_t)tile * kTcRows + q * 32 + lane;
-            // four interleaved best / second-best trackers (columns u % 4), branch-free
+            // the row's error margin first: the candidate test below needs it
+            const float fi = row < P.n ? __ldg(P.fn + row) : 0.0f;
+            const float two_e = 2.0f * (0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax));
+            // four interleaved best / second-best trackers (columns u % 4), branch-free; a column is a
+            // candidate when e_c <= (its tracker's best so far) + 2 E_i: a superset of the centroids within
+            // 2 E_i of the final best, since every tracker's best only decreases towards values >= it
             float t1[4], t2[4];
             int32_t tc[4];
+            uint32_t cm0 = 0u, cm1 = 0u, cm2 = 0u, cm3 = 0u;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 t1[v] = INFINITY;
@@ -607,6 +613,7 @@ __global__ void __launch_bounds__(192, 1)
                           "=r"(r[30]), "=r"(r[31])
                         : "r"(taddr + 16u));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                uint32_t wb = 0u;  // candidate bits of columns c0 .. c0 + 31
 #pragma unroll
                 for (int u = 0; u < 32; ++u) {
                     if (u < 16 || two) {
@@ -616,9 +623,18 @@ __global__ void __launch_bounds__(192, 1)
                         t2[v] = fminf(t2[v], fmaxf(t1[v], e));
                         tc[v] = lt ? c0 + u : tc[v];
                         t1[v] = fminf(t1[v], e);
+                        wb |= (c0 + u < P.k && e <= t1[v] + two_e) ? (1u << u) : 0u;
                     }
                 }
+                if (c0 == 0) cm0 = wb;
+                else if (c0 == 32) cm1 = wb;
+                else if (c0 == 64) cm2 = wb;
+                else cm3 = wb;
             }
+            // the accumulator may be overwritten once every epilogue warp has read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_tempty[s]);
             // merge: smallest value, ties to the lowest column; second = the others' best or the winner's second
             int w = 0;
 #pragma unroll
@@ -631,45 +647,14 @@ __global__ void __launch_bounds__(192, 1)
             for (int v = 0; v < 4; ++v)
                 if (v != w) b2 = fminf(b2, t1[v]);
             bool queue = false;
-            float e_bound = 0.0f;
             if (row < P.n) {
-                const float fi = __ldg(P.fn + row);
-                e_bound = 0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax);
-                queue = P.k > 1 && !(b2 - b1 > 2.0f * e_bound);
+                queue = P.k > 1 && !(b2 - b1 > two_e);
                 if (!queue) {
                     if (P.labels[row] != c1) *P.changed = 1;
                     P.labels[row] = c1;
                 }
             }
-            // a queued row keeps the centroids not provably worse than its best, e_c - e_best <= 2 E_i
-            // (a second read of the accumulator); any other centroid's FP32 distance exceeds the best's
-            uint32_t cm[4] = {0u, 0u, 0u, 0u};
             const unsigned qm = __ballot_sync(0xffffffffu, queue);
-            if (qm) {
-                const float tau = b1 + 2.0f * e_bound;
-                for (int c0 = 0; c0 < P.nmma; c0 += 16) {
-                    uint32_t r[16];
-                    const uint32_t taddr = tmem + (uint32_t)s * P.ncols + (uint32_t)c0 + ((uint32_t)(q * 32) << 16);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                        "%12, %13, %14, %15}, [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(taddr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int c = c0 + u;
-                        const float e = fmaf(-2.0f, __uint_as_float(r[u]), s_cn2[c]);  // +inf past k
-                        if (e <= tau) cm[c >> 5] |= 1u << (c & 31);
-                    }
-                }
-            }
-            // the accumulator may be overwritten once every epilogue warp has read it
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&s_tempty[s]);
             // one queue slot reservation per warp
             if (qm) {
                 int32_t slot0 = 0;
@@ -678,7 +663,7 @@ __global__ void __launch_bounds__(192, 1)
                 if (queue) {
                     const int32_t slot = slot0 + __popc(qm & ((1u << lane) - 1u));
                     P.list[slot] = (int32_t)row;
-                    *reinterpret_cast<uint4 *>(P.cmask + (int64_t)slot * 4) = make_uint4(cm[0], cm[1], cm[2], cm[3]);
+                    *reinterpret_cast<uint4 *>(P.cmask + (int64_t)slot * 4) = make_uint4(cm0, cm1, cm2, cm3);
                 }
             }
         }
