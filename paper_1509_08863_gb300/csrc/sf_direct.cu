@@ -27,9 +27,11 @@ static StepFn direct_fn_lpr(int lpr, int mode) {
 }
 
 StepFn direct_step_fn(int storage, int lpr, int mode, bool weighted) {
-    if (storage == SF_F32) return weighted ? direct_fn_lpr<float, true>(lpr, mode) : direct_fn_lpr<float, false>(lpr, mode);
+    if (storage == SF_F32)
+        return weighted ? direct_fn_lpr<float, true>(lpr, mode) : direct_fn_lpr<float, false>(lpr, mode);
     if (storage == SF_BF16)
-        return weighted ? direct_fn_lpr<__nv_bfloat16, true>(lpr, mode) : direct_fn_lpr<__nv_bfloat16, false>(lpr, mode);
+        return weighted ? direct_fn_lpr<__nv_bfloat16, true>(lpr, mode)
+                        : direct_fn_lpr<__nv_bfloat16, false>(lpr, mode);
     if (storage == SF_F16)
         return weighted ? direct_fn_lpr<__half, true>(lpr, mode) : direct_fn_lpr<__half, false>(lpr, mode);
     return nullptr;

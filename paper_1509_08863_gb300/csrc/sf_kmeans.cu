@@ -279,7 +279,8 @@ __global__ void km_assign_cands_kernel(const float *F, int32_t d, const float *C
         int32_t bc = 0x7fffffff;
         for (int t = lane; t < ncand; t += 32) {  // the t-th candidate in increasing order
             int q = 0, rem = t;
-            if (rem >= n0) { rem -= n0; q = 1; if (rem >= n1) { rem -= n1; q = 2; if (rem >= n2) { rem -= n2; q = 3; } } }
+            const int cnt[3] = {n0, n1, n2};
+            while (q < 3 && rem >= cnt[q]) rem -= cnt[q++];
             uint32_t bits = m[q];
             for (int r = 0; r < rem; ++r) bits &= bits - 1u;
             const int c = q * 32 + (__ffs(bits) - 1);
@@ -757,8 +758,8 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     const int ig = 2 * sm_count();
     sf_status st;
     if ((st = sc.get(&fn, (size_t)n)) || (st = sc.get(&cn2, (size_t)k)) || (st = sc.get(&cmax, 1)) ||
-        (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) || (st = sc.get(&count, 2)) ||
-        (st = sc.get(&offs, (size_t)k + 1)) || (st = sc.get(&coffs, (size_t)k + 1)) ||
+        (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
+        (st = sc.get(&count, 2)) || (st = sc.get(&offs, (size_t)k + 1)) || (st = sc.get(&coffs, (size_t)k + 1)) ||
         (st = sc.get(&keys, (size_t)n)) || (st = sc.get(&keys_alt, (size_t)n)) ||
         (st = sc.get(&part, (size_t)max_chunks * d)) || (st = sc.get(&ipart, (size_t)ig)) ||
         (st = sc.get(&isum, 1)))
@@ -800,21 +801,23 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         T.status = device_status();
         SF_ARG(T.status, "device status word unavailable");
     }
-    // exact-decision kernel: register-blocked for k <= 128 and d <= 256, else a warp per row with the
-    // centroids in shared memory when they fit
+    // CUDA-core assignment of every row: register-blocked for k <= 128 and d <= 256, else a warp per row
+    // with the centroids in shared memory when they fit
     const bool blocked = k <= 128 && d <= 256;
     const bool ex_v4 = d % 4 == 0;
     const size_t ex_smem = (size_t)(128 + kExRows) * ex_ld(d, ex_v4) * sizeof(float);
-    const void *ex_fn = ex_v4 ? (const void *)km_assign_blocked_kernel<true> : (const void *)km_assign_blocked_kernel<false>;
+    const void *ex_fn =
+        ex_v4 ? (const void *)km_assign_blocked_kernel<true> : (const void *)km_assign_blocked_kernel<false>;
     const size_t c_smem = (size_t)k * (d + 1) * sizeof(float);
     const int smem_c = c_smem <= 160 * 1024 ? 1 : 0;
-    if (blocked)
+    int ex_occ = 1;
+    if (!tc && blocked) {
         SF_CHECK_CUDA(cudaFuncSetAttribute(ex_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ex_smem));
-    else if (smem_c)
+        SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ex_occ, ex_fn, 128, ex_smem));
+    } else if (!tc && smem_c) {
         SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)c_smem));
-    int ex_occ = 1;
-    if (blocked) SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ex_occ, ex_fn, 128, ex_smem));
+    }
     const int assign_grid = blocked ? (ex_occ > 0 ? ex_occ : 1) * sm_count() : (smem_c ? sm_count() : 4 * sm_count());
     auto exact = [&](const int32_t *lst, const int32_t *cnt) -> sf_status {
         if (blocked && ex_v4)
