@@ -485,8 +485,9 @@ enum {
  * Iteration: assignment label_i = argmin_c d(f_i, c_c), ties to the lowest c,
  * with d the FP32 fused-multiply-add sum of (f_ij - c_cj)^2 in index order;
  * stop when no label changed (from the second assignment on); otherwise
- * c_c = (FP64 sum of its rows / count) rounded to FP32, empty clusters
- * keeping their centroid. With tensor cores (d a multiple of 32 in [32, 128],
+ * c_c = (sum of its rows / count) rounded to FP32, empty clusters keeping
+ * their centroid, the sum exact over the values rounded down to multiples
+ * of 2^-sh, with n max|F_ij| 2^sh just below 2^62. With tensor cores (d a multiple of 32 in [32, 128],
  * k <= 128, F and C 16-byte aligned) the products f_i.c_c come from tcgen05
  * TF32 MMAs and every row whose two best candidates lie within the products'
  * error bound is decided again with the exact FP32 sum on CUDA cores, so both

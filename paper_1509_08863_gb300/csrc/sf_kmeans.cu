@@ -22,29 +22,39 @@
 // 2^-16 (|f_i| + c_max)^2, and a row is decided by the tensor cores when the
 // gap between its two best e exceeds 2 E_i.
 //
-// Update. Rows are sorted by (label, row) (stable radix sort), cut into
-// chunks of at most kChunkRows rows within each cluster; each chunk's column
-// sums are FP64 in row order, and each cluster adds its chunks in order:
-// c_c = (float)(sum / count); an empty cluster keeps its centroid. Every
-// step is deterministic.
+// Update. c_c = (sum of its rows / count) rounded to FP32, an empty cluster
+// keeping its centroid. The sums are exact integer sums of the values
+// rounded down to multiples of 2^-sh, with 2^sh as large as keeps n max|F_ij| 2^sh
+// below 2^62 (an absolute error below n 2^-sh <= 2^-60 n^2 max|F_ij| per
+// sum, under the bound of about 2^-53 n^2 max|F_ij| of an FP64 sum in row
+// order); integer addition is associative, so blocks and atomics may add
+// in any order and the centroids are deterministic.
 #include <cuda.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "sf_step.cuh"
 
 namespace sf {
 
-constexpr int kChunkRows = 256;
 constexpr int kTcRows = 128;  // rows of F per tensor-core tile (MMA M)
 
 // ------------------------------------------------------------ small kernels
-// |f_i| (FP32, rounded up by 2^-20 relative), one warp per row
-__global__ void km_row_norm_kernel(const float *F, int32_t n, int32_t d, float *fn, int32_t *bad) {
+// |f_i| (FP32, rounded up by 2^-20 relative), one warp per row; fmax_bits:
+// the largest |F_ij| (float bits, atomicMax of non-negative floats as ints)
+__global__ void km_row_norm_kernel(const float *F, int32_t n, int32_t d, float *fn, int32_t *bad,
+                                   int32_t *fmax_bits) {
     const int lane = threadIdx.x & 31;
+    float mx = 0.f;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
          i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         float s = 0.f;
-        for (int j = lane; j < d; j += 32) s = fmaf(F[i * d + j], F[i * d + j], s);
+        for (int j = lane; j < d; j += 32) {
+            const float x = F[i * d + j];
+            s = fmaf(x, x, s);
+            mx = fmaxf(mx, fabsf(x));
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) {
@@ -52,6 +62,9 @@ __global__ void km_row_norm_kernel(const float *F, int32_t n, int32_t d, float *
             if (!isfinite(s)) *bad = 1;
         }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && mx > 0.f) atomicMax(fmax_bits, __float_as_int(mx));
 }
 
 // cn2[c] = |c_c|^2 (FP32 fused multiply-adds in index order); cmax = max |c| rounded up. One block.
@@ -337,89 +350,209 @@ __global__ void km_inertia_kernel(const float *F, int32_t n, int32_t d, const fl
     }
 }
 
-// key = label << 32 | row
-__global__ void km_keys_kernel(const int32_t *labels, int32_t n, uint64_t *keys) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) keys[i] = ((uint64_t)(uint32_t)labels[i] << 32) | (uint32_t)i;
+// Fixed-point scale of the centroid sums: every |F_ij| <= B = fmax_bits as a
+// float, and n < 2^nb, so with values rounded to integers of F_ij 2^sh every
+// partial sum stays below n 2^e 2^sh <= 2^62 (B < 2^e).
+__device__ __forceinline__ int km_fix_shift(int32_t fmax_bits, int32_t n) {
+    const float B = __int_as_float(fmax_bits);
+    if (!(B > 0.f)) return 0;
+    int e = 0;
+    frexpf(B, &e);
+    // at most 187: then every value is a multiple of 2^-sh (B < 2^-126 when
+    // the cap binds: all values subnormal, multiples of 2^-149)
+    return min(62 - (32 - __clz(n)) - e, 187);
 }
 
-// offs[c] = first sorted position with label >= c (c = 0..k); coffs = prefix of
-// ceil(count / kChunkRows) chunks per cluster. One block of 1024 threads, k <= 1023.
-__global__ void km_offsets_kernel(const uint64_t *keys, int32_t n, int32_t k, int32_t *offs, int32_t *coffs) {
-    __shared__ int32_t s_scan[1024];
-    const int c = threadIdx.x;
-    auto lower = [&](int32_t lab) {
-        int32_t lo = 0, hi = n;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi) >> 1;
-            if ((int32_t)(keys[mid] >> 32) < lab) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
+// Centroid sums of one tile of clusters [c0, c0 + kt) over one contiguous
+// range of rows, in batches of br rows. The sums live in shared memory as
+// 64-bit integers; column chunk q (128 columns) of cluster c belongs to warp
+// (c nch + q) mod kFixWarps alone, which adds it without atomics: lane l
+// takes columns 128 q + 4 l .. + 3, kept at cells 128 q + 32 u + l of the
+// cluster (u = 0..3), so every shared access of a warp is conflict free.
+// STAGED: each batch (a contiguous run of br d floats, d a multiple of 4) is
+// copied into one of kFixStages shared buffers by the TMA engine, three
+// batches ahead; otherwise rows are read from global memory. The block then
+// adds its sums into S and its counts into cnt with 64-bit integer atomics:
+// integer addition is associative, so S is the same in any order.
+constexpr int kFixWarps = 32;
+constexpr int kFixStages = 3;
+constexpr int kFixBatch = 128;  // rows per batch at most (4 label registers per lane)
+constexpr int64_t kFixSmemBytes = 227 * 1024 - 1024;  // dynamic shared memory of one block
+constexpr int64_t kFixAccBytes = 160 * 1024;          // of which at most this for the sums of a cluster tile
+
+// the first column chunk q of cluster c that warp w owns: (c nch + q) mod kFixWarps == w
+static_assert((kFixWarps & (kFixWarps - 1)) == 0, "kFixWarps must be a power of two");
+__device__ __forceinline__ int km_fix_first_chunk(int w, int32_t c, int nch) {
+    return (w - c * nch) & (kFixWarps - 1);
+}
+
+// The fixed-point value of the float x with bits u: floor(x 2^sh), by
+// integer operations alone (a 64-bit conversion would run on the FP64 pipe).
+// |x| = m 2^(e - 150) with m the 24-bit significand (e = 1 and no implicit
+// bit for subnormals); the signed significand placed at bit 39 and shifted
+// right arithmetically by 189 - sh - e (>= 1 because |x| 2^sh < 2^62,
+// clamped to 63) is floor(x 2^sh). base = 189 - sh.
+__device__ __forceinline__ long long km_fix_value(uint32_t u, int base) {
+    const int e = (int)((u >> 23) & 255u);
+    const int32_t s = (int32_t)u >> 31;  // 0 or -1
+    const int32_t hi = (int32_t)(((u << 7) & 0x3fffff80u) | (e ? 0x40000000u : 0u));  // (m << 39) >> 32
+    const uint32_t amt = (uint32_t)min(base - max(e, 1), 63);
+    long long r;
+    asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"((long long)((hi ^ s) - s) << 32), "r"(amt));
+    return r;
+}
+
+struct FixParams {
+    const float *F;
+    const int32_t *labels;
+    int32_t n, d, k, kc, nb, br, dpad;  // dpad: cells per cluster (128 per column chunk)
+    const int32_t *fmax_bits;
+    unsigned long long *S, *cnt;
+    int32_t *status;  // bit 0: a bounded wait gave up
+};
+
+template <bool STAGED>
+__global__ void __launch_bounds__(kFixWarps * 32, 1) km_fixsum_kernel(FixParams P) {
+    extern __shared__ __align__(16) unsigned char km_fix_smem[];
+    __shared__ int32_t s_done[kFixStages];   // warps done with the stage's current batch
+    __shared__ int32_t s_last[kFixStages];   // the last batch issued into the stage
+    __shared__ int32_t s_abort;
+    const int32_t d = P.d, br = P.br, dpad = P.dpad;
+    const int32_t tile = blockIdx.x / P.nb, blk = blockIdx.x % P.nb;
+    const int32_t c0 = tile * P.kc, kt = min(P.kc, P.k - c0);
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(km_fix_smem);             // [kFixStages]
+    float *s_f = reinterpret_cast<float *>(km_fix_smem + 16 * kFixStages);  // [kFixStages][br][d]
+    const int32_t stage_floats = STAGED ? br * d : 0;
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(s_f + kFixStages * stage_floats);  // [kt][dpad]
+    unsigned long long *s_cnt = s_acc + kt * dpad;                                                       // [kt]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int32_t t = tid; t < kt * dpad + kt; t += blockDim.x) s_acc[t] = 0ull;
+    const int base = 189 - km_fix_shift(*P.fmax_bits, P.n);
+    const int64_t r0 = (int64_t)P.n * blk / P.nb, r1 = (int64_t)P.n * (blk + 1) / P.nb;
+    const int32_t nbatch = (int32_t)((r1 - r0 + br - 1) / br);
+    const int nch = (d + 127) >> 7;
+
+    auto issue = [&](int32_t bt) {  // one thread: batch bt into stage bt mod kFixStages
+        const int st = bt % kFixStages;
+        const int64_t r = r0 + (int64_t)bt * br;
+        const uint32_t bytes = (uint32_t)(min((int64_t)br, r1 - r) * d * 4);
+        s_last[st] = bt;
+        mbar_arrive_expect_tx(&s_bar[st], bytes);
+        bulk_g2s(s_f + st * stage_floats, P.F + r * d, bytes, &s_bar[st]);
     };
-    int32_t nch = 0;
-    if (c <= k) {
-        const int32_t o = lower(c);
-        offs[c] = o;
-        if (c < k) {
-            const int32_t cnt = lower(c + 1) - o;
-            nch = (cnt + kChunkRows - 1) / kChunkRows;
+    if (tid == 0) {
+        s_abort = 0;
+        for (int st = 0; st < kFixStages; ++st) {
+            s_done[st] = 0;
+            s_last[st] = -1;
+        }
+        if (STAGED) {
+            for (int st = 0; st < kFixStages; ++st) mbar_init(&s_bar[st], 1);
+            fence_mbar_init();
+            for (int32_t bt = 0; bt < kFixStages && bt < nbatch; ++bt) issue(bt);
         }
     }
-    s_scan[c] = nch;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan (Hillis-Steele)
-        const int32_t v = (c >= off) ? s_scan[c - off] : 0;
-        __syncthreads();
-        s_scan[c] += v;
-        __syncthreads();
-    }
-    if (c <= k) coffs[c] = (c == 0) ? 0 : s_scan[c - 1];
-}
-
-// FP64 column sums of one chunk of one cluster, rows in sorted (row) order
-__global__ void km_chunk_sum_kernel(const float *F, int32_t d, int32_t k, const uint64_t *keys, const int32_t *offs,
-                                    const int32_t *coffs, double *part) {
-    const int32_t b = blockIdx.x;
-    if (b >= coffs[k]) return;
-    int32_t lo = 0, hi = k - 1;  // the cluster c with coffs[c] <= b < coffs[c + 1]
-    while (lo < hi) {
-        const int32_t mid = (lo + hi + 1) >> 1;
-        if (coffs[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const int32_t c = lo;
-    const int32_t q = b - coffs[c];
-    const int32_t r0 = offs[c] + q * kChunkRows;
-    const int32_t cnt = min(offs[c + 1], r0 + kChunkRows) - r0;
-    __shared__ int32_t s_rows[kChunkRows];
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) s_rows[t] = (int32_t)(uint32_t)(keys[r0 + t] & 0xffffffffu);
-    __syncthreads();
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        int32_t r = 0;
-        for (; r + 8 <= cnt; r += 8) {  // eight loads in flight, added in row order
-            float v[8];
+    // Warps move through the batches independently: the last warp done with
+    // a stage refills it, so a warp that owns more rows of one batch delays
+    // the others only when it falls a whole ring of stages behind.
+    int32_t lv[kFixBatch / 32], ln[kFixBatch / 32];  // labels of rows 32 g + lane of this batch and the next
+    auto load_labels = [&](int32_t bt, int32_t (&dst)[kFixBatch / 32]) {
+        const int64_t r = r0 + (int64_t)bt * br;
+        const int32_t rows = bt < nbatch ? (int32_t)min((int64_t)br, r1 - r) : 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = F[(int64_t)s_rows[r + u] * d + j];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s += (double)v[u];
+        for (int g = 0; g < kFixBatch / 32; ++g)
+            dst[g] = (32 * g + lane < rows) ? __ldg(P.labels + r + 32 * g + lane) : -1;
+    };
+    load_labels(0, lv);
+    for (int32_t bt = 0; bt < nbatch; ++bt) {
+        const int64_t r = r0 + (int64_t)bt * br;
+        load_labels(bt + 1, ln);  // in flight while this batch is added
+        const float *rowbase = P.F + r * d;
+        const int st = bt % kFixStages;
+        if (STAGED) {
+            const bool landed = mbar_wait_bounded(&s_bar[st], (uint32_t)(bt / kFixStages) & 1u);
+            if (!__all_sync(0xffffffffu, landed) || *(volatile int32_t *)&s_abort) {
+                if (lane == 0) s_abort = 1;
+                break;
+            }
+            rowbase = s_f + st * stage_floats;
         }
-        for (; r < cnt; ++r) s += (double)F[(int64_t)s_rows[r] * d + j];
-        part[(int64_t)b * d + j] = s;
+#pragma unroll
+        for (int g = 0; g < kFixBatch / 32; ++g) {
+            const int32_t c = lv[g] - c0;  // rows past the batch carry label -1
+            const bool own = lv[g] >= 0 && c >= 0 && c < kt && km_fix_first_chunk(warp, c, nch) < nch;
+            for (uint32_t m = __ballot_sync(0xffffffffu, own); m; m &= m - 1u) {
+                const int l = __ffs(m) - 1;
+                const int32_t cl = __shfl_sync(0xffffffffu, c, l);
+                const float *f = rowbase + (32 * g + l) * d;
+                unsigned long long *acc = s_acc + cl * dpad;
+                const int q0 = km_fix_first_chunk(warp, cl, nch);
+                for (int q = q0; q < nch; q += kFixWarps) {
+                    const int j0 = 128 * q + 4 * lane;
+                    float x[4];
+                    if (STAGED) {
+                        if (j0 >= d) continue;  // d is a multiple of 4: all four columns or none
+                        const float4 t = *reinterpret_cast<const float4 *>(f + j0);
+                        x[0] = t.x;
+                        x[1] = t.y;
+                        x[2] = t.z;
+                        x[3] = t.w;
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) x[u] = (j0 + u < d) ? __ldg(f + j0 + u) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        acc[128 * q + 32 * u + lane] += (unsigned long long)km_fix_value(__float_as_uint(x[u]), base);
+                }
+                if (q0 == 0 && lane == 0) s_cnt[cl] += 1ull;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kFixBatch / 32; ++g) lv[g] = ln[g];
+        if (STAGED) {
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&s_done[st], 1) == kFixWarps - 1) {  // the last warp done with this batch
+                    s_done[st] = 0;
+                    __threadfence_block();
+                    if (bt + kFixStages < nbatch) {
+                        fence_proxy_async();
+                        issue(bt + kFixStages);
+                    }
+                }
+            }
+        }
     }
+    __syncthreads();
+    if (STAGED && s_abort) {  // a copy never landed: report, wait (bounded) for the copies issued, leave
+        if (tid == 0) {
+            atomicOr(P.status, 1);
+            for (int st = 0; st < kFixStages; ++st)
+                if (s_last[st] >= 0) mbar_wait_bounded(&s_bar[st], (uint32_t)(s_last[st] / kFixStages) & 1u);
+        }
+        return;
+    }
+    for (int32_t t = tid; t < kt * d; t += blockDim.x) {  // cell of column j: 128 q + 32 u + l, j = 128 q + 4 l + u
+        const int32_t c = t / d, j = t - c * d;
+        const unsigned long long v = s_acc[c * dpad + (j & ~127) + 32 * (j & 3) + ((j & 127) >> 2)];
+        if (v) atomicAdd(P.S + (int64_t)(c0 + c) * d + j, v);
+    }
+    for (int t = tid; t < kt; t += blockDim.x)
+        if (s_cnt[t]) atomicAdd(P.cnt + c0 + t, s_cnt[t]);
 }
 
-// c_c = (sum of its chunks in order) / count, rounded to FP32; empty clusters keep c_c
-__global__ void km_centroid_kernel(int32_t d, const int32_t *offs, const int32_t *coffs, const double *part,
-                                   float *C) {
-    const int32_t c = blockIdx.x;
-    const int32_t cnt = offs[c + 1] - offs[c];
-    if (cnt == 0) return;
-    for (int j = threadIdx.x; j < d; j += blockDim.x) {
-        double s = 0.0;
-        for (int32_t q = coffs[c]; q < coffs[c + 1]; ++q) s += part[(int64_t)q * d + j];
-        C[(int64_t)c * d + j] = (float)(s / (double)cnt);
+// c_c = (float)((S_c 2^-sh) / count_c) in FP64; an empty cluster keeps c_c
+__global__ void km_fix_centroid_kernel(int32_t n, int32_t d, int32_t k, const int32_t *fmax_bits,
+                                       const unsigned long long *S, const unsigned long long *cnt, float *C) {
+    const int sh = km_fix_shift(*fmax_bits, n);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)k * d;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long m = cnt[t / d];
+        if (m == 0) continue;
+        C[t] = (float)(ldexp((double)(long long)S[t], -sh) / (double)m);
     }
 }
 
@@ -751,22 +884,20 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     Scratch sc(s);
     float *fn = nullptr, *cn2 = nullptr, *cmax = nullptr;
     uint32_t *cmask = nullptr;
-    int32_t *changed = nullptr, *bad = nullptr, *list = nullptr, *count = nullptr, *offs = nullptr, *coffs = nullptr;
-    uint64_t *keys = nullptr, *keys_alt = nullptr;
-    double *part = nullptr, *ipart = nullptr, *isum = nullptr;
-    const int64_t max_chunks = (int64_t)(n + kChunkRows - 1) / kChunkRows + k;
+    int32_t *changed = nullptr, *bad = nullptr, *list = nullptr, *count = nullptr, *fmax_bits = nullptr;
+    unsigned long long *S = nullptr;  // [k][d] fixed-point sums, then [k] counts
+    double *ipart = nullptr, *isum = nullptr;
     const int ig = 2 * sm_count();
     sf_status st;
     if ((st = sc.get(&fn, (size_t)n)) || (st = sc.get(&cn2, (size_t)k)) || (st = sc.get(&cmax, 1)) ||
         (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
-        (st = sc.get(&count, 2)) || (st = sc.get(&offs, (size_t)k + 1)) || (st = sc.get(&coffs, (size_t)k + 1)) ||
-        (st = sc.get(&keys, (size_t)n)) || (st = sc.get(&keys_alt, (size_t)n)) ||
-        (st = sc.get(&part, (size_t)max_chunks * d)) || (st = sc.get(&ipart, (size_t)ig)) ||
-        (st = sc.get(&isum, 1)))
+        (st = sc.get(&count, 2)) || (st = sc.get(&fmax_bits, 1)) || (st = sc.get(&S, (size_t)k * (d + 1))) ||
+        (st = sc.get(&ipart, (size_t)ig)) || (st = sc.get(&isum, 1)))
         return st;
     SF_CHECK_CUDA(cudaMemsetAsync(labels, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1: no label yet
     SF_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
-    km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad);
+    SF_CHECK_CUDA(cudaMemsetAsync(fmax_bits, 0, sizeof(int32_t), s));
+    km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad, fmax_bits);
     if ((st = check_launch("km_row_norm_kernel"))) return st;
 
     // tensor-core setup
@@ -830,6 +961,43 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         return check_launch("km_assign_kernel");
     };
 
+    // update layout: tiles of FP.kc clusters whose sums fit in shared memory beside the row stages
+    FixParams FP = {};
+    size_t fix_smem = 0;
+    unsigned fix_grid = 0;
+    const void *fix_fn = nullptr;
+    {
+        const bool staged = d % 4 == 0 && (uintptr_t)F % 16 == 0;
+        const int32_t dpad = (d + 127) / 128 * 128;
+        const int64_t cell = 8 * (int64_t)dpad + 8;
+        const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, kFixAccBytes / cell));
+        const int64_t ntile = (k + kc - 1) / kc;
+        FP.kc = (int32_t)((k + ntile - 1) / ntile);
+        const int64_t acc = (int64_t)FP.kc * cell;
+        const int64_t head = 16 * kFixStages;
+        int64_t br = kFixBatch;
+        if (staged) br = std::min<int64_t>(kFixBatch, (kFixSmemBytes - head - acc) / ((int64_t)kFixStages * 4 * d));
+        SF_ARG(br >= 1, "k-means: centroid sums do not fit in shared memory");
+        fix_smem = (size_t)(head + (staged ? (int64_t)kFixStages * br * 4 * d : 0) + acc);
+        fix_fn = staged ? (const void *)km_fixsum_kernel<true> : (const void *)km_fixsum_kernel<false>;
+        SF_CHECK_CUDA(cudaFuncSetAttribute(fix_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fix_smem));
+        int occ = 0;
+        SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fix_fn, kFixWarps * 32, fix_smem));
+        FP.nb = (int32_t)std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)std::max(occ, 1) * sm_count() / ntile));
+        fix_grid = (unsigned)(ntile * FP.nb);
+        FP.F = F;
+        FP.labels = labels;
+        FP.n = n;
+        FP.d = d;
+        FP.k = k;
+        FP.br = (int32_t)br;
+        FP.dpad = dpad;
+        FP.fmax_bits = fmax_bits;
+        FP.S = S;
+        FP.cnt = S + (size_t)k * d;
+        FP.status = device_status();
+        SF_ARG(FP.status, "device status word unavailable");
+    }
     int it = 0;
     while (it < max_iter) {
         SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
@@ -873,20 +1041,15 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
             SF_CHECK_CUDA(cudaStreamSynchronize(s));
         }
         if (it > 1 && !h_changed) break;
-        // update: rows sorted by (label, row), FP64 chunk sums, clusters add their chunks in order
-        km_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(labels, n, keys);
-        if ((st = check_launch("km_keys_kernel"))) return st;
-        int bits = 8;
-        while (bits < 32 && (1ll << bits) < k) bits += 8;
-        uint64_t *ka = keys, *kb = keys_alt;
-        float *nv = nullptr, *nv2 = nullptr;
-        if ((st = radix_sort(ka, nv, kb, nv2, n, 32, 32 + bits, s))) return st;
-        km_offsets_kernel<<<1, 1024, 0, s>>>(ka, n, k, offs, coffs);
-        if ((st = check_launch("km_offsets_kernel"))) return st;
-        km_chunk_sum_kernel<<<(unsigned)max_chunks, 128, 0, s>>>(F, d, k, ka, offs, coffs, part);
-        if ((st = check_launch("km_chunk_sum_kernel"))) return st;
-        km_centroid_kernel<<<k, 128, 0, s>>>(d, offs, coffs, part, C);
-        if ((st = check_launch("km_centroid_kernel"))) return st;
+        // update: exact fixed-point sums per cluster, then the FP64 means
+        SF_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * (size_t)k * (d + 1), s));
+        if (fix_fn == (const void *)km_fixsum_kernel<true>)
+            km_fixsum_kernel<true><<<fix_grid, kFixWarps * 32, fix_smem, s>>>(FP);
+        else
+            km_fixsum_kernel<false><<<fix_grid, kFixWarps * 32, fix_smem, s>>>(FP);
+        if ((st = check_launch("km_fixsum_kernel"))) return st;
+        km_fix_centroid_kernel<<<(k * d + 255) / 256, 256, 0, s>>>(n, d, k, fmax_bits, S, S + (size_t)k * d, C);
+        if ((st = check_launch("km_fix_centroid_kernel"))) return st;
     }
     *iters = it;
     return SF_OK;

@@ -3,9 +3,10 @@ FP32 rows and initial centroids.
 
 Labels are integers decided by floating point; both sides decide them with
 the FP32 fused-multiply-add sum in index order (ties to the lowest index), so
-labels and the number of assignments must be equal. Centroids are FP64 means
-rounded to FP32 on both sides, summed in different orders (chunks vs one
-pass): equal up to one FP32 ulp. Inertia: FP64 sums in different orders,
+labels and the number of assignments must be equal. Centroids are means
+rounded to FP32 on both sides, of sums taken differently (exact integer sums
+of values rounded down to a fixed point far below FP32 resolution on the GPU, FP64
+in row order in the oracle): equal up to one FP32 ulp. Inertia: FP64 sums in different orders,
 1e-12 relative.
 """
 import numpy as np
@@ -80,6 +81,18 @@ def test_kmeans_other_shapes_use_cuda_cores(sf, oracle_mod):
     check_same(sf, oracle_mod, F, C0, 4, sf.KMEANS_AUTO)
     with pytest.raises(sf.SpecFiltError):
         sf.kmeans(torch.as_tensor(F, device="cuda"), torch.as_tensor(C0, device="cuda"), 3, sf.KMEANS_TENSOR)
+
+
+def test_kmeans_cluster_tiles_and_scales(sf, oracle_mod):
+    # k d too large for one tile of shared-memory sums (300 x 100 cells of 8 bytes): two cluster tiles
+    F, C0 = mixture(2000, 300, 100, seed=8)
+    check_same(sf, oracle_mod, F, C0, 4, sf.KMEANS_AUTO)
+    # the fixed-point scale follows max |F_ij|: exact power-of-two rescalings far from unit rows
+    F, C0 = mixture(2500, 64, 16, seed=9)
+    for e in (40, -20):
+        Fs, Cs = np.ldexp(F, e).astype(np.float32), np.ldexp(C0, e).astype(np.float32)
+        for mode in (sf.KMEANS_TENSOR, sf.KMEANS_CUDA_CORES):
+            check_same(sf, oracle_mod, Fs, Cs, 8, mode)
 
 
 def test_kmeans_ties_go_to_lowest_index(sf, oracle_mod):
