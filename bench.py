@@ -373,11 +373,13 @@ def main():
                        blocks_per_sm=t.blocks_per_sm, carveout_pct=t.carveout_pct, l2_window=t.l2_window,
                        sweep_kernel=t.sweep_kernel)
 
-    def step(src, dst, Rc, Rt, st, collect=None, marks=None):
+    def step(src, dst, Rc, Rt, st, collect=None, marks=None, before_filter=None):
         """One pass of the path: the count's moments on the probe block Rc, the
         filter on R. `st` is the block storage of both sweeps (FP16 applies to
         the filter, whose moments then use BF16 blocks). `marks`, when given,
-        collects (stage, CUDA event) pairs after each stage."""
+        collects (stage, CUDA event) pairs after each stage. `before_filter` is
+        called once the step has made its last host round trip (after the
+        coefficients), just before the filter sweep is enqueued."""
         def mark(name):
             if marks is not None:
                 e = torch.cuda.Event(enable_timing=True)
@@ -401,6 +403,8 @@ def main():
         mark("dichotomy_and_coeffs")
         if st not in tuned:
             tuned[st] = sf.autotune(g, eta, st, 1)
+        if before_filter is not None:
+            before_filter()
         Y = sf.cheb_filter(g, lh, a, Rt, opts_for(st, filter_algo))[0]
         mark("cheb_filter")
         if dist:  # row norms run over every rank's columns
@@ -453,9 +457,12 @@ def main():
 
     def timed_e2e(st, steps, warmup):
         """Steps fed from pinned host buffers, features read back to pinned host
-        memory, all inside the timed region. The copies run on a second stream:
-        step i + 1's inputs are copied while step i computes (two device input
-        buffers), and step i's features are read back while step i + 1 runs."""
+        memory, all inside the timed region. The copies run on a second stream
+        and are enqueued while a step's filter sweep runs (after its last host
+        round trip, so that the step's own small reads never queue behind them):
+        the previous step's features go back to the host and the next step's
+        inputs come in (two device input buffers). Only the first step's inputs
+        and the last step's features are not overlapped."""
         cs = torch.cuda.Stream(device=dev)
         host = (src_h, dst_h, Rc_h, R_h)
         bufs = [tuple(torch.empty(h.shape, dtype=h.dtype, device=dev) for h in host) for _ in range(2)]
@@ -466,30 +473,41 @@ def main():
             start.record(stream)
             ev_in = [torch.cuda.Event(), torch.cuda.Event()]
             ev_done = [None, None]
+            prev = [None, None, 0]  # output, its event, its step index
             cs.wait_event(start)
             with torch.cuda.stream(cs):
                 for d_, h_ in zip(bufs[0], host):
                     d_.copy_(h_, non_blocking=True)
                 ev_in[0].record(cs)
+
+            def read_back(out, ev, i):
+                cs.wait_event(ev)
+                out.record_stream(cs)
+                host_out[i % 2].copy_(out, non_blocking=True)
+
             for i in range(total):
                 b = i % 2
-                if i + 1 < total:  # prefetch the next step's inputs once the step that used the buffer is done
-                    nb = (i + 1) % 2
+
+                def overlap():
                     with torch.cuda.stream(cs):
-                        if ev_done[nb] is not None:
-                            cs.wait_event(ev_done[nb])
-                        for d_, h_ in zip(bufs[nb], host):
-                            d_.copy_(h_, non_blocking=True)
-                        ev_in[nb].record(cs)
+                        if prev[0] is not None:
+                            read_back(*prev)
+                        if i + 1 < total:  # buffer (i + 1) % 2 was last read by step i - 1
+                            nb = (i + 1) % 2
+                            if ev_done[nb] is not None:
+                                cs.wait_event(ev_done[nb])
+                            for d_, h_ in zip(bufs[nb], host):
+                                d_.copy_(h_, non_blocking=True)
+                            ev_in[nb].record(cs)
+
                 stream.wait_event(ev_in[b])
-                out = step(*bufs[b], st)
+                out = step(*bufs[b], st, before_filter=overlap)
                 done = torch.cuda.Event()
                 done.record(stream)
                 ev_done[b] = done
-                with torch.cuda.stream(cs):  # read the features back while the next step runs
-                    cs.wait_event(done)
-                    out.record_stream(cs)
-                    host_out[i % 2].copy_(out, non_blocking=True)
+                prev[:] = [out, done, i]
+            with torch.cuda.stream(cs):
+                read_back(*prev)
             fin = torch.cuda.Event()
             fin.record(cs)
             stream.wait_event(fin)
@@ -547,7 +565,8 @@ def main():
     if not args.no_e2e:
         mse = timed_e2e(storage, max(3, args.steps // 2), 1)
         e2e = {"value": updates * world / (mse * 1e-3), "unit": "updates/s", "ms_per_step": mse,
-               "copies": "on a second stream, overlapped with the neighbouring steps (two input buffers)",
+               "copies": "on a second stream, enqueued during each step's filter sweep: the previous step's features "
+                         "out, the next step's inputs in (two input buffers)",
                "h2d_bytes_per_step": int(src_h.numel() * 4 + dst_h.numel() * 4 + R_h.numel() * 4 +
                                          Rc_h.numel() * 4),
                "d2h_bytes_per_step": int(n * eta * 4)}

@@ -41,25 +41,33 @@ namespace sf {
 constexpr int kTcRows = 128;  // rows of F per tensor-core tile (MMA M)
 
 // ------------------------------------------------------------ small kernels
-// |f_i| (FP32, rounded up by 2^-20 relative), one warp per row; fmax_bits:
-// the largest |F_ij| (float bits, atomicMax of non-negative floats as ints)
+// |f_i| (FP32, rounded up by 2^-20 relative), a warp per four rows (their
+// loads in flight together); fmax_bits: the largest |F_ij| (float bits,
+// atomicMax of non-negative floats as ints)
 __global__ void km_row_norm_kernel(const float *F, int32_t n, int32_t d, float *fn, int32_t *bad,
                                    int32_t *fmax_bits) {
     const int lane = threadIdx.x & 31;
     float mx = 0.f;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
-         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        float s = 0.f;
+    for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; i0 < n;
+         i0 += (((int64_t)gridDim.x * blockDim.x) >> 5) * 4) {
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
         for (int j = lane; j < d; j += 32) {
-            const float x = F[i * d + j];
-            s = fmaf(x, x, s);
-            mx = fmaxf(mx, fabsf(x));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float x = (i0 + u < n) ? F[(i0 + u) * d + j] : 0.f;
+                s[u] = fmaf(x, x, s[u]);
+                mx = fmaxf(mx, fabsf(x));
+            }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) {
-            fn[i] = sqrtf(s) * (1.0f + 1.0f / 1048576.0f);
-            if (!isfinite(s)) *bad = 1;
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], off);
+        }
+        if (lane < 4 && i0 + lane < n) {
+            const float v = lane == 0 ? s[0] : lane == 1 ? s[1] : lane == 2 ? s[2] : s[3];
+            fn[i0 + lane] = sqrtf(v) * (1.0f + 1.0f / 1048576.0f);
+            if (!isfinite(v)) *bad = 1;
         }
     }
 #pragma unroll
@@ -324,28 +332,69 @@ __global__ void km_assign_cands_kernel(const float *F, int32_t d, const float *C
     }
 }
 
-// inertia partials: part[b] = sum over this block's rows (block order) of d(f_i, c_label_i)
-__global__ void km_inertia_kernel(const float *F, int32_t n, int32_t d, const float *C, const int32_t *labels,
-                                  double *part) {
-    __shared__ double s_red[32];
+// inertia partials: part[b] = sum (FP64) over this block's rows of
+// d(f_i, c_label_i), the FP32 fused-multiply-add chain in index order. A
+// lane owns a row; when t_smem is set (d <= 128) each warp stages tiles of 32
+// rows in shared memory (row stride d + 1, eight rows' coalesced loads in
+// flight at a time), and
+// the centroids are staged once per block when c_smem is set. Rows are added in a fixed order
+// (lanes, warps, then tiles), so the result is deterministic.
+constexpr int kInWarps = 8;
+constexpr int kInRowVals = 4;  // values of a staged row per lane: tiles are staged when d <= 32 kInRowVals
+__global__ void __launch_bounds__(kInWarps * 32) km_inertia_kernel(const float *__restrict__ F, int32_t n, int32_t d,
+                                                                   const float *__restrict__ C, int32_t k,
+                                                                   const int32_t *__restrict__ labels, int32_t t_smem,
+                                                                   int32_t c_smem, double *part) {
+    extern __shared__ float km_in_smem[];
+    __shared__ double s_red[kInWarps];
+    const int ld = d + 1, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s_c = km_in_smem;
+    float *s_t = km_in_smem + (c_smem ? (int64_t)k * ld : 0) + (t_smem ? (int64_t)warp * 32 * ld : 0);
+    if (c_smem)
+        for (int64_t t = threadIdx.x; t < (int64_t)k * d; t += blockDim.x) s_c[(t / d) * ld + t % d] = C[t];
+    __syncthreads();
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float *f = F + i * d;
-        const float *c = C + (int64_t)labels[i] * d;
-        float s = 0.f;
-        for (int j = 0; j < d; ++j) {
-            const float t = __fsub_rn(f[j], c[j]);
-            s = __fmaf_rn(t, t, s);
+    for (int64_t r0 = ((int64_t)blockIdx.x * kInWarps + warp) * 32; r0 < n; r0 += (int64_t)gridDim.x * kInWarps * 32) {
+        const int rows = (int)min((int64_t)32, n - r0);
+        if (t_smem)
+            for (int r8 = 0; r8 < rows; r8 += 8) {  // eight rows' loads in flight
+                float v[8][kInRowVals];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+                    for (int u = 0; u < kInRowVals; ++u) {
+                        const int j = lane + 32 * u;
+                        v[rr][u] = (r8 + rr < rows && j < d) ? F[(r0 + r8 + rr) * d + j] : 0.f;
+                    }
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+                    for (int u = 0; u < kInRowVals; ++u) {
+                        const int j = lane + 32 * u;
+                        if (r8 + rr < rows && j < d) s_t[(r8 + rr) * ld + j] = v[rr][u];
+                    }
+            }
+        __syncwarp();
+        if (lane < rows) {
+            const int32_t c = labels[r0 + lane];
+            const float *f = t_smem ? s_t + lane * ld : F + (r0 + lane) * d;
+            const float *cc = c_smem ? s_c + (int64_t)c * ld : C + (int64_t)c * d;
+            float sum = 0.f;
+            for (int j = 0; j < d; ++j) {
+                const float t = __fsub_rn(f[j], cc[j]);
+                sum = __fmaf_rn(t, t, sum);
+            }
+            acc += (double)sum;
         }
-        acc += (double)s;
+        __syncwarp();
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    if (lane == 0) s_red[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[w];
+        for (int w = 0; w < kInWarps; ++w) a += s_red[w];
         part[blockIdx.x] = a;
     }
 }
@@ -998,6 +1047,19 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         FP.status = device_status();
         SF_ARG(FP.status, "device status word unavailable");
     }
+    // inertia: tiles of 32 rows per warp in shared memory, the centroids too when they fit
+    const int in_t_smem = d <= 32 * kInRowVals ? 1 : 0;
+    const size_t in_tiles = in_t_smem ? (size_t)kInWarps * 32 * (d + 1) * sizeof(float) : 0;
+    const size_t in_cent = (size_t)k * (d + 1) * sizeof(float);
+    const int in_c_smem = in_tiles + in_cent <= (size_t)kFixSmemBytes ? 1 : 0;
+    const size_t in_smem = in_tiles + (in_c_smem ? in_cent : 0);
+    int in_grid = 1;
+    if (inertia) {
+        SF_CHECK_CUDA(cudaFuncSetAttribute(km_inertia_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in_smem));
+        int occ = 0;
+        SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, km_inertia_kernel, kInWarps * 32, in_smem));
+        in_grid = std::min(ig, std::max(occ, 1) * sm_count());
+    }
     int it = 0;
     while (it < max_iter) {
         SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
@@ -1034,9 +1096,10 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         ++it;
         const bool last = (it > 1 && !h_changed) || it == max_iter;
         if (last && inertia) {
-            km_inertia_kernel<<<ig, 256, 0, s>>>(F, n, d, C, labels, ipart);
+            km_inertia_kernel<<<in_grid, kInWarps * 32, in_smem, s>>>(F, n, d, C, k, labels, in_t_smem, in_c_smem,
+                                                                    ipart);
             if ((st = check_launch("km_inertia_kernel"))) return st;
-            if ((st = reduce_sum_f64(ipart, ig, isum, s))) return st;
+            if ((st = reduce_sum_f64(ipart, in_grid, isum, s))) return st;
             SF_CHECK_CUDA(cudaMemcpyAsync(inertia, isum, sizeof(double), cudaMemcpyDeviceToHost, s));
             SF_CHECK_CUDA(cudaStreamSynchronize(s));
         }
