@@ -577,14 +577,19 @@ def main():
         kmeans = run_kmeans_leg(sf, info["Y"], k, wl["r_seed"] + 5, 20)
 
     # the method end to end on this graph (§4.1: count, filter, features, k-means; FP32 blocks) against the
-    # generating communities, and the stability measure of §4.3 where the graph is small enough
-    clustering = stability = None
+    # generating communities; where the graph is small enough also on the normalised Laplacian (footnote of
+    # §2.1) and the stability measure of §4.3
+    clustering = clustering_norm = stability = None
     if not args.no_kmeans and world == 1:
         gq = sf.csr_build(n, src_d, dst_d, None)
         _, lq = sf.lambda_max_estimate(gq, 40, None, seed=11)
         clustering = cluster_recovery(sf, gq, lq, R_d, k, p, gr.labels, seed=wl["r_seed"])
         if n <= 200_000:
             stability = stability_leg(sf, gq, lq, p, n, eta, k, seed=wl["r_seed"])
+            gn = gq.normalized()
+            _, ln = sf.lambda_max_estimate(gn, 40, None, seed=11)
+            clustering_norm = cluster_recovery(sf, gn, ln, R_d, k, p, gr.labels, seed=wl["r_seed"])
+            gn.free()
         gq.free()
 
     # accuracy of this step's features/filter against the FP64 oracle on one column
@@ -649,6 +654,7 @@ def main():
         "stages_ms": stages,
         "kmeans": kmeans,
         "clustering": clustering,
+        "clustering_normalized_laplacian": clustering_norm,
         "stability": stability,
         "roofline_by_variant": by_variant,
         "clocks": clocks,
