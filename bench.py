@@ -598,7 +598,8 @@ def main():
     def roof_of(name, n_l, ms_, by_):
         gbs = by_ / (ms_ * 1e-3) / 1e9 if ms_ > 0 else 0.0
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": traffic_from_profile(args.workload, name), "kernel": (f"sddmm_kernel ({name})" if name.startswith("adjoint") else f"cheb_step_kernel ({name})"),
+                "traffic": traffic_from_profile(args.workload, name),
+                "kernel": (f"sddmm_kernel ({name})" if name.startswith("adjoint") else f"cheb_step_kernel ({name})"),
                 "launches_timed": n_l, "avg_launch_ms": ms_ / max(n_l, 1), "bytes_per_launch": by_ / max(n_l, 1),
                 "share_of_sweep_time": ms_ / k_ms if k_ms > 0 else None, "peak_source": f"{peak_kind} hbm_gbs"}
 

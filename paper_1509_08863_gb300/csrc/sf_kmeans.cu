@@ -5,8 +5,9 @@
 // c, where d is the FP32 sum of fused multiply-adds (f_j - c_j)^2 in index
 // order: a floating-point decision, so it is stated in one precision and
 // order. Two ways to take it:
-//  * CUDA cores (kmeans_assign_kernel): a warp per row, a lane per centroid,
-//    exactly that sum;
+//  * CUDA cores: exactly that sum, in km_assign_blocked_kernel (32 rows x 128
+//    centroids per block, register tiles; k <= 128, d <= 256) or else
+//    km_assign_kernel (a warp per row, a lane per centroid);
 //  * tensor cores (kmeans_tc_kernel): G = F C^T for a 128-row tile on tcgen05
 //    (TF32 operands staged by TMA in 128-byte swizzled shared memory, FP32
 //    accumulators in TMEM), e_c = |c_c|^2 - 2 G_ic; the row takes the tensor
@@ -24,11 +25,11 @@
 //
 // Update. c_c = (sum of its rows / count) rounded to FP32, an empty cluster
 // keeping its centroid. The sums are exact integer sums of the values
-// rounded down to multiples of 2^-sh, with 2^sh as large as keeps n max|F_ij| 2^sh
-// below 2^62 (an absolute error below n 2^-sh <= 2^-60 n^2 max|F_ij| per
-// sum, under the bound of about 2^-53 n^2 max|F_ij| of an FP64 sum in row
-// order); integer addition is associative, so blocks and atomics may add
-// in any order and the centroids are deterministic.
+// rounded down to multiples of 2^-sh, with 2^sh as large as keeps
+// n max|F_ij| 2^sh below 2^62 (an absolute error below n 2^-sh <=
+// 2^-60 n^2 max|F_ij| per sum, under the bound of about 2^-53 n^2 max|F_ij|
+// of an FP64 sum in row order); integer addition is associative, so blocks
+// and atomics may add in any order and the centroids are deterministic.
 #include <cuda.h>
 
 #include <algorithm>
@@ -1055,7 +1056,8 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     const size_t in_smem = in_tiles + (in_c_smem ? in_cent : 0);
     int in_grid = 1;
     if (inertia) {
-        SF_CHECK_CUDA(cudaFuncSetAttribute(km_inertia_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in_smem));
+        SF_CHECK_CUDA(
+            cudaFuncSetAttribute(km_inertia_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in_smem));
         int occ = 0;
         SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, km_inertia_kernel, kInWarps * 32, in_smem));
         in_grid = std::min(ig, std::max(occ, 1) * sm_count());
