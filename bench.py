@@ -697,7 +697,9 @@ def run_kmeans_leg(sf, Fk, k, seed, max_iter):
     tc_ok = d % 32 == 0 and 32 <= d <= 128 and k <= 128
     out = {"rows": n, "d": d, "k": k, "max_iter": max_iter, "init": "k seeded random rows"}
     res = {}
-    for name, mode in (("tensor_cores", sf.KMEANS_TENSOR if tc_ok else None), ("cuda_cores", sf.KMEANS_CUDA_CORES)):
+    for name, mode in (("tensor_cores", sf.KMEANS_TENSOR if tc_ok else None),
+                       ("tensor_cores_single_product", sf.KMEANS_TENSOR_SINGLE if tc_ok else None),
+                       ("cuda_cores", sf.KMEANS_CUDA_CORES)):
         if mode is None:
             continue
         sf.kmeans(Fk, C0, 2, mode)  # warm-up
@@ -716,18 +718,20 @@ def run_kmeans_leg(sf, Fk, k, seed, max_iter):
         if "kmeans_tc_f32" in v:
             nl, kms, by = v["kmeans_tc_f32"]
             t = kms / nl * 1e-3
+            mma = 3 if mode == sf.KMEANS_TENSOR else 1  # split operands: hi.hi + hi.lo + lo.hi
             hbm, kind = peaks()
             tfp, tkind = tf32_peak()
             ent["distance_kernel"] = {
                 "avg_launch_ms": kms / nl, "launches": nl,
                 "hbm": {"achieved": by / nl / t / 1e9, "peak": hbm, "unit": "GB/s", "frac": by / nl / t / 1e9 / hbm,
                         "peak_source": f"{kind} hbm_gbs"},
-                "tensor": {"achieved": 2.0 * n * k * d / t / 1e12, "peak": tfp, "unit": "TFLOP/s",
-                           "frac": 2.0 * n * k * d / t / 1e12 / tfp, "peak_source": tkind},
+                "tensor": {"achieved": mma * 2.0 * n * k * d / t / 1e12, "peak": tfp, "unit": "TFLOP/s",
+                           "frac": mma * 2.0 * n * k * d / t / 1e12 / tfp, "peak_source": tkind,
+                           "products_per_pair": mma},
                 "bound": "hbm"}
         out[name] = ent
-    if len(res) == 2:
-        out["labels_equal"] = bool(torch.equal(res["tensor_cores"], res["cuda_cores"]))
+    if len(res) > 1:
+        out["labels_equal"] = all(bool(torch.equal(lab, res["cuda_cores"])) for lab in res.values())
     return out
 
 

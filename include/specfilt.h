@@ -465,9 +465,10 @@ SF_API sf_status sf_profile_variant(int32_t tag, int64_t *launches, double *ms, 
 /* ---------------------------------------------------------------------- */
 
 enum {
-    SF_KMEANS_AUTO = 0,       /* tensor cores when the shape allows (below), else CUDA cores */
-    SF_KMEANS_TENSOR = 1,     /* tensor cores (SF_ERR_ARG when the shape does not allow them) */
-    SF_KMEANS_CUDA_CORES = 2  /* CUDA cores only */
+    SF_KMEANS_AUTO = 0,         /* tensor cores when the shape allows (below), else CUDA cores */
+    SF_KMEANS_TENSOR = 1,       /* tensor cores (SF_ERR_ARG when the shape does not allow them) */
+    SF_KMEANS_CUDA_CORES = 2,   /* CUDA cores only */
+    SF_KMEANS_TENSOR_SINGLE = 3 /* tensor cores, one TF32 product per pair (no split operands) */
 };
 
 /*
@@ -487,13 +488,16 @@ enum {
  * stop when no label changed (from the second assignment on); otherwise
  * c_c = (sum of its rows / count) rounded to FP32, empty clusters keeping
  * their centroid, the sum exact over the values rounded down to multiples
- * of 2^-sh, with n max|F_ij| 2^sh just below 2^62. With tensor cores (d a multiple of 32 in [32, 128],
- * k <= 128, F and C 16-byte aligned) the products f_i.c_c come from tcgen05
- * TF32 MMAs and every row whose two best candidates lie within the products'
- * error bound is decided again with the exact FP32 sum on CUDA cores, so both
- * modes return the same labels. Deterministic. SF_ERR_NUMERIC when a row or
- * a centroid is not finite. Synchronises `stream` once per assignment (to
- * read whether labels changed).
+ * of 2^-sh, with n max|F_ij| 2^sh just below 2^62. With tensor cores (d a
+ * multiple of 32 in [32, 128], k <= 128, F and C 16-byte aligned) the
+ * products f_i.c_c come from tcgen05 TF32 MMAs: with F and C split into TF32
+ * high and low parts (three MMAs per product; 8 n d bytes of device memory
+ * more) for SF_KMEANS_AUTO and SF_KMEANS_TENSOR, one product per pair for
+ * SF_KMEANS_TENSOR_SINGLE. Every row whose two best candidates lie within
+ * the products' error bound is decided again with the exact FP32 sum on
+ * CUDA cores, so all modes return the same labels. Deterministic.
+ * SF_ERR_NUMERIC when a row or a centroid is not finite. Synchronises
+ * `stream` once per assignment (to read whether labels changed).
  */
 SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int32_t k, float *C, int32_t max_iter,
                            int32_t mode, int32_t *labels, int32_t *iters, double *inertia, void *stream);

@@ -526,7 +526,7 @@ def profile_end():
     return n.value, ms.value, by.value
 
 
-KMEANS_AUTO, KMEANS_TENSOR, KMEANS_CUDA_CORES = 0, 1, 2
+KMEANS_AUTO, KMEANS_TENSOR, KMEANS_CUDA_CORES, KMEANS_TENSOR_SINGLE = 0, 1, 2, 3
 
 
 def kmeans(F, C0, max_iter: int = 50, mode: int = KMEANS_AUTO):

@@ -16,12 +16,18 @@
 //    superset of the centroids within that margin of its best (no other
 //    centroid can win in FP32), which km_assign_cands_kernel then decides
 //    exactly. Both give the same labels.
-// Bound: TF32 keeps 10 mantissa bits (truncation error < 2^-10 per operand),
-// so |G_ic - f_i.c_c| <= (2^-9 + 2^-16) |f_i| |c_c| with FP32 accumulation
-// of 128 products; |c|^2 and the FP32 sum d carry <= 2^-16 (|f| + |c|)^2.
-// With the factor 2 on G and a safety margin: E_i = 2^-7 |f_i| c_max +
+// Bound, one product per pair (F and C as given, read as TF32): TF32 keeps
+// 10 mantissa bits (truncation error < 2^-10 per operand), so
+// |G_ic - f_i.c_c| <= (2^-9 + 2^-16) |f_i| |c_c| with FP32 accumulation of
+// 128 products; |c|^2 and the FP32 sum d carry <= 2^-16 (|f| + |c|)^2. With
+// the factor 2 on G and a safety margin: E_i = 2^-7 |f_i| c_max +
 // 2^-16 (|f_i| + c_max)^2, and a row is decided by the tensor cores when the
 // gap between its two best e exceeds 2 E_i.
+// Split operands (the default): x = hi + lo + r with hi, lo TF32 (round to
+// nearest) and |r| <= 2^-22 |x|; G = hi.hi + hi.lo + lo.hi drops terms of at
+// most 3.01 2^-22 |f||c| in all, and the FP32 accumulation of 3 d <= 384
+// exact TF32 products (1 ulp per addition) adds <= 2^-14.4 |f||c|: with the
+// factor 2 and a safety margin the first term of E_i becomes 2^-12 |f_i| c_max.
 //
 // Update. c_c = (sum of its rows / count) rounded to FP32, an empty cluster
 // keeping its centroid. The sums are exact integer sums of the values
@@ -637,8 +643,33 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32(int nmma) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
 }
 
+// x = hi + lo + r with hi = x rounded to TF32 (nearest, ties away from
+// zero), lo = (x - hi) rounded to TF32 (x - hi is exact in FP32), so
+// |r| <= 2^-11 |x - hi| <= 2^-22 |x|.
+__global__ void km_split_tf32_kernel(const float *x, int64_t count, float *hi, float *lo) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fsub_rn(v, __uint_as_float(h))));
+        hi[i] = __uint_as_float(h);
+        lo[i] = __uint_as_float(l);
+    }
+}
+
+// D (TMEM, FP32) (+)= A B^T for one K = 8 step of TF32 operands (A: 128 rows, B: N rows, both K-major)
+__device__ __forceinline__ void umma_tf32(uint32_t dcol, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 struct TcParams {
     int32_t n, d, k, nmma, ncols;  // ncols: TMEM columns per accumulator (power of two >= 32)
+    int32_t stages;                // split operands: A stages of one 32-column chunk (high and low parts)
     const float *cn2;              // [k]
     const float *cmax;             // [1]
     const float *fn;               // [n]
@@ -662,15 +693,26 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
 }
 
 // Warp roles: 0 = TMA producer, 1 = TMEM owner and MMA issuer, 2..5 = epilogue
-// (128 threads, one tile row each). A: two stages of 128 x d FP32; B: the
-// centroids (nmma x d, rows >= k zero-filled by the copy); two TMEM
-// accumulators of ncols columns so that tile t + 1 multiplies while tile t is
-// read.
+// (128 threads, one tile row each). B: the centroids (nmma x d, rows >= k
+// zero-filled by the copy), resident; two TMEM accumulators of ncols columns
+// so that tile t + 1 multiplies while tile t is read. A, single pass: two
+// stages of a whole 128 x d tile. A, SPLIT (F and C each given as TF32 high
+// and low parts, x = hi + lo + r with |r| <= 2^-22 |x|): P.stages stages of
+// one 32-column chunk of both parts, and three MMAs per K step, hi.hi +
+// hi.lo + lo.hi, into the same accumulator.
+constexpr int kTcMaxStages = 3;
+constexpr float kTcProdSingle = 0.0078125f;        // 2^-7: products of TF32-truncated operands
+constexpr float kTcProdSplit = 2.44140625e-04f;    // 2^-12: split operands
+constexpr uint32_t kTcChunk = (uint32_t)kTcRows * 128;  // bytes of one 32-column FP32 chunk of a tile
+constexpr int kTcSmemMax = 227 * 1024 - 2048;           // dynamic shared memory of the kernel, static beside it
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(192, 1)
     kmeans_tc_kernel(const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapC,
+                     const __grid_constant__ CUtensorMap mapFlo, const __grid_constant__ CUtensorMap mapClo,
                      const TcParams P) {
     extern __shared__ __align__(16) unsigned char km_smem[];
-    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tfull[2], s_tempty[2], s_bfull;
+    __shared__ __align__(8) uint64_t s_full[kTcMaxStages], s_empty[kTcMaxStages], s_tfull[2], s_tempty[2], s_bfull;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ float s_cn2[128];  // |c|^2, +inf for the padding columns
@@ -681,13 +723,18 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t a_bytes = (uint32_t)kTcRows * P.d * 4;
     const uint32_t b_atom = (uint32_t)P.nmma * 128;
     unsigned char *sB = base;
-    unsigned char *sA[2] = {base + (uint32_t)atoms * b_atom, base + (uint32_t)atoms * b_atom + a_bytes};
+    unsigned char *sBlo = base + (uint32_t)atoms * b_atom;  // SPLIT only
+    unsigned char *sA0 = base + (uint32_t)atoms * b_atom * (SPLIT ? 2u : 1u);
+    const int stages = SPLIT ? P.stages : 2;
+    const uint32_t stage_bytes = SPLIT ? 2u * kTcChunk : a_bytes;  // SPLIT: high chunk, then low chunk
     const int n_tiles = (P.n + kTcRows - 1) / kTcRows;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(&s_full[s], 1);
             mbar_init(&s_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
             mbar_init(&s_tfull[s], 1);
             mbar_init(&s_tempty[s], 4);  // one arrival per epilogue warp
         }
@@ -709,46 +756,71 @@ __global__ void __launch_bounds__(192, 1)
     volatile int *abort = &s_abort;
 
     if (warp == 0 && lane == 0) {
-        // producer: the centroids once, then the A tiles through two stages
-        mbar_arrive_expect_tx(&s_bfull, (uint32_t)atoms * b_atom);
-        for (int a = 0; a < atoms; ++a) tma_load_2d(sB + a * b_atom, &mapC, 32 * a, 0, &s_bfull);
-        int t = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
-            const int s = t & 1;
-            if (t >= 2 && !tc_wait(&s_empty[s], (uint32_t)((t >> 1) - 1) & 1u, abort)) break;
-            mbar_arrive_expect_tx(&s_full[s], a_bytes);
-            for (int a = 0; a < atoms; ++a)
-                tma_load_2d(sA[s] + (uint32_t)a * kTcRows * 128, &mapF, 32 * a, tile * kTcRows, &s_full[s]);
+        // producer: the centroids once, then the A tiles (or tile chunks) through the stages
+        mbar_arrive_expect_tx(&s_bfull, (uint32_t)atoms * b_atom * (SPLIT ? 2u : 1u));
+        for (int a = 0; a < atoms; ++a) {
+            tma_load_2d(sB + a * b_atom, &mapC, 32 * a, 0, &s_bfull);
+            if (SPLIT) tma_load_2d(sBlo + a * b_atom, &mapClo, 32 * a, 0, &s_bfull);
+        }
+        int t = 0;  // stage uses so far
+        bool go = true;
+        for (int tile = blockIdx.x; go && tile < n_tiles; tile += gridDim.x) {
+            for (int a = 0; a < (SPLIT ? atoms : 1); ++a, ++t) {
+                const int s = t % stages;
+                if (t >= stages && !tc_wait(&s_empty[s], (uint32_t)((t / stages) - 1) & 1u, abort)) {
+                    go = false;
+                    break;
+                }
+                unsigned char *dst = sA0 + (uint32_t)s * stage_bytes;
+                mbar_arrive_expect_tx(&s_full[s], stage_bytes);
+                if (SPLIT) {
+                    tma_load_2d(dst, &mapF, 32 * a, tile * kTcRows, &s_full[s]);
+                    tma_load_2d(dst + kTcChunk, &mapFlo, 32 * a, tile * kTcRows, &s_full[s]);
+                } else {
+                    for (int c = 0; c < atoms; ++c)
+                        tma_load_2d(dst + (uint32_t)c * kTcChunk, &mapF, 32 * c, tile * kTcRows, &s_full[s]);
+                }
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         const uint32_t idesc = umma_idesc_tf32(P.nmma);
         bool ok = tc_wait(&s_bfull, 0, abort);
-        int t = 0;
-        for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++t) {
-            const int s = t & 1;
-            if (!tc_wait(&s_full[s], (uint32_t)(t >> 1) & 1u, abort)) break;
-            if (t >= 2 && !tc_wait(&s_tempty[s], (uint32_t)((t >> 1) - 1) & 1u, abort)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dcol = tmem + (uint32_t)s * P.ncols;
-            for (int kk = 0; kk < P.d / 8; ++kk) {  // K = 8 TF32 per instruction: 32 bytes of a 128-byte row
-                const int a = kk >> 2;
-                const uint32_t off = (uint32_t)(kk & 3) * 32;
-                const uint64_t adesc = umma_desc_sw128(smem_u32(sA[s] + (uint32_t)a * kTcRows * 128) + off);
-                const uint64_t bdesc = umma_desc_sw128(smem_u32(sB + (uint32_t)a * b_atom) + off);
-                const uint32_t acc = kk > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-                    "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-                    : "memory");
+        int t = 0, tt = 0;  // stage uses, tiles
+        for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tt) {
+            const int sa = tt & 1;
+            if (tt >= 2 && !tc_wait(&s_tempty[sa], (uint32_t)((tt >> 1) - 1) & 1u, abort)) break;
+            const uint32_t dcol = tmem + (uint32_t)sa * P.ncols;
+            for (int a = 0; a < (SPLIT ? atoms : 1); ++a, ++t) {
+                const int s = t % stages;
+                if (!tc_wait(&s_full[s], (uint32_t)(t / stages) & 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned char *sA = sA0 + (uint32_t)s * stage_bytes;
+                // K = 8 TF32 per instruction: 32 bytes of a 128-byte row
+                for (int kk = (SPLIT ? 4 * a : 0); kk < (SPLIT ? 4 * a + 4 : P.d / 8); ++kk) {
+                    const int c = kk >> 2;  // the chunk of B (and of A in the single pass)
+                    const uint32_t off = (uint32_t)(kk & 3) * 32;
+                    const uint32_t a_hi = smem_u32(sA + (SPLIT ? 0u : (uint32_t)c * kTcChunk)) + off;
+                    const uint64_t bhi = umma_desc_sw128(smem_u32(sB + (uint32_t)c * b_atom) + off);
+                    umma_tf32(dcol, umma_desc_sw128(a_hi), bhi, idesc, kk > 0 ? 1u : 0u);
+                    if (SPLIT) {
+                        const uint64_t blo = umma_desc_sw128(smem_u32(sBlo + (uint32_t)c * b_atom) + off);
+                        umma_tf32(dcol, umma_desc_sw128(a_hi), blo, idesc, 1u);
+                        umma_tf32(dcol, umma_desc_sw128(a_hi + kTcChunk), bhi, idesc, 1u);
+                    }
+                }
+                // the stage is free once these MMAs complete
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&s_empty[s]))
+                             : "memory");
             }
-            // the stage is free and the accumulator ready once these MMAs complete
+            if (!ok) break;
+            // the accumulator is ready once every MMA of the tile completes
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&s_empty[s]))
-                         : "memory");
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&s_tfull[s]))
+                             smem_u32(&s_tfull[sa]))
                          : "memory");
         }
     } else if (warp >= 2) {
@@ -763,7 +835,8 @@ __global__ void __launch_bounds__(192, 1)
             const int64_t row = (int64_t)tile * kTcRows + q * 32 + lane;
             // the row's error margin first: the candidate test below needs it
             const float fi = row < P.n ? __ldg(P.fn + row) : 0.0f;
-            const float two_e = 2.0f * (0.0078125f * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax));
+            const float prod = SPLIT ? kTcProdSplit : kTcProdSingle;
+            const float two_e = 2.0f * (prod * fi * cmax + 1.52587890625e-05f * (fi + cmax) * (fi + cmax));
             // four interleaved best / second-best trackers (columns u % 4), branch-free; a column is a
             // candidate when e_c <= (its tracker's best so far) + 2 E_i: a superset of the centroids within
             // 2 E_i of the final best, since every tracker's best only decreases towards values >= it
@@ -924,12 +997,14 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     SF_ARG(n >= 1 && d >= 1 && d <= 4096, "need n >= 1 and 1 <= d <= 4096");
     SF_ARG(k >= 1 && k <= 1023, "k must be in [1, 1023]");
     SF_ARG(max_iter >= 1, "max_iter must be >= 1");
-    SF_ARG(mode == SF_KMEANS_AUTO || mode == SF_KMEANS_TENSOR || mode == SF_KMEANS_CUDA_CORES,
+    SF_ARG(mode == SF_KMEANS_AUTO || mode == SF_KMEANS_TENSOR || mode == SF_KMEANS_CUDA_CORES ||
+               mode == SF_KMEANS_TENSOR_SINGLE,
            "mode must be SF_KMEANS_*");
     const bool aligned = ((uintptr_t)F % 16 == 0) && ((uintptr_t)C % 16 == 0);
     const bool tc = mode != SF_KMEANS_CUDA_CORES && tc_shape_ok(d, k) && aligned;
-    SF_ARG(mode != SF_KMEANS_TENSOR || tc,
+    SF_ARG((mode != SF_KMEANS_TENSOR && mode != SF_KMEANS_TENSOR_SINGLE) || tc,
            "the tensor-core assignment needs d a multiple of 32 in [32, 128], k <= 128 and 16-byte aligned F and C");
+    const bool split = tc && mode != SF_KMEANS_TENSOR_SINGLE;
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
     float *fn = nullptr, *cn2 = nullptr, *cmax = nullptr;
@@ -950,17 +1025,36 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad, fmax_bits);
     if ((st = check_launch("km_row_norm_kernel"))) return st;
 
-    // tensor-core setup
-    CUtensorMap mapF, mapC;
+    // tensor-core setup (split: F and C as TF32 high and low parts, F once, C every assignment)
+    CUtensorMap mapF, mapC, mapFlo, mapClo;
     TcParams T = {};
     int tc_grid = 0, tc_smem = 0;
+    float *Fhi = nullptr, *Flo = nullptr, *Chi = nullptr, *Clo = nullptr;
     if (tc) {
         const int nmma = (k + 15) / 16 * 16;
         int ncols = 32;
         while (ncols < nmma) ncols *= 2;
-        if ((st = encode_rows(&mapF, F, n, d, kTcRows)) || (st = encode_rows(&mapC, C, k, d, nmma))) return st;
-        tc_smem = tc_smem_bytes(d, nmma);
-        SF_CHECK_CUDA(cudaFuncSetAttribute(kmeans_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
+        if (split) {
+            if ((st = sc.get(&Fhi, (size_t)n * d)) || (st = sc.get(&Flo, (size_t)n * d)) ||
+                (st = sc.get(&Chi, (size_t)k * d)) || (st = sc.get(&Clo, (size_t)k * d)))
+                return st;
+            km_split_tf32_kernel<<<4 * sm_count(), 256, 0, s>>>(F, (int64_t)n * d, Fhi, Flo);
+            if ((st = check_launch("km_split_tf32_kernel"))) return st;
+            if ((st = encode_rows(&mapF, Fhi, n, d, kTcRows)) || (st = encode_rows(&mapFlo, Flo, n, d, kTcRows)) ||
+                (st = encode_rows(&mapC, Chi, k, d, nmma)) || (st = encode_rows(&mapClo, Clo, k, d, nmma)))
+                return st;
+            const int fixed = 1024 + 2 * (d / 32) * nmma * 128;
+            T.stages = fixed + kTcMaxStages * 2 * (int)kTcChunk <= kTcSmemMax ? kTcMaxStages : 2;
+            tc_smem = fixed + T.stages * 2 * (int)kTcChunk;
+        } else {
+            if ((st = encode_rows(&mapF, F, n, d, kTcRows)) || (st = encode_rows(&mapC, C, k, d, nmma))) return st;
+            mapFlo = mapF;
+            mapClo = mapC;
+            tc_smem = tc_smem_bytes(d, nmma);
+        }
+        SF_CHECK_CUDA(cudaFuncSetAttribute(split ? (const void *)kmeans_tc_kernel<true>
+                                                 : (const void *)kmeans_tc_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem));
         SF_CHECK_CUDA(cudaFuncSetAttribute(km_assign_cands_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)((size_t)k * (d + 1) * sizeof(float))));
         const int n_tiles = (n + kTcRows - 1) / kTcRows;
@@ -1071,13 +1165,20 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
             SF_CHECK_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
             cudaEvent_t ea = nullptr, eb = nullptr;
             const bool prof = profiling_on() && profile_events(&ea, &eb);
+            if (split) {
+                km_split_tf32_kernel<<<sm_count(), 256, 0, s>>>(C, (int64_t)k * d, Chi, Clo);
+                if ((st = check_launch("km_split_tf32_kernel"))) return st;
+            }
             if (prof) cudaEventRecord(ea, s);
-            kmeans_tc_kernel<<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, T);
+            if (split) kmeans_tc_kernel<true><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, T);
+            else kmeans_tc_kernel<false><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, T);
             if ((st = check_launch("kmeans_tc_kernel"))) return st;
             if (prof) {
                 cudaEventRecord(eb, s);
-                // compulsory bytes: the rows once, the centroids per CTA, labels read and written
-                profile_record(ea, eb, (double)n * d * 4 + (double)tc_grid * k * d * 4 + (double)n * 8,
+                // compulsory bytes: the rows once, the centroids per CTA (each in two parts when split),
+                // labels read and written
+                const double parts = split ? 2.0 : 1.0;
+                profile_record(ea, eb, parts * ((double)n * d * 4 + (double)tc_grid * k * d * 4) + (double)n * 8,
                                kProfTagKmeansTc);
             }
             km_assign_cands_kernel<<<4 * sm_count(), 256, (size_t)k * (d + 1) * sizeof(float), s>>>(

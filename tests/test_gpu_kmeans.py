@@ -68,7 +68,7 @@ def check_same(sf, oracle_mod, F, C0, max_iter, mode):
 def test_kmeans_tensor_cores_match_oracle(sf, oracle_mod, d, k):
     # ragged row count: not a multiple of the 128-row tiles
     F, C0 = mixture(3001, d, k, seed=d + k)
-    for mode in (sf.KMEANS_TENSOR, sf.KMEANS_CUDA_CORES):
+    for mode in (sf.KMEANS_TENSOR, sf.KMEANS_TENSOR_SINGLE, sf.KMEANS_CUDA_CORES):
         check_same(sf, oracle_mod, F, C0, 12, mode)
 
 
@@ -91,8 +91,19 @@ def test_kmeans_cluster_tiles_and_scales(sf, oracle_mod):
     F, C0 = mixture(2500, 64, 16, seed=9)
     for e in (40, -20):
         Fs, Cs = np.ldexp(F, e).astype(np.float32), np.ldexp(C0, e).astype(np.float32)
-        for mode in (sf.KMEANS_TENSOR, sf.KMEANS_CUDA_CORES):
+        for mode in (sf.KMEANS_TENSOR, sf.KMEANS_TENSOR_SINGLE, sf.KMEANS_CUDA_CORES):
             check_same(sf, oracle_mod, Fs, Cs, 8, mode)
+
+
+def test_kmeans_structureless_rows_near_ties(sf, oracle_mod):
+    # random unit rows and centroids: every row has several centroids at nearly the same distance, so the
+    # tensor paths re-decide many rows; labels must still equal the FP32 decision of the oracle
+    rng = np.random.default_rng(12)
+    F = rng.standard_normal((20000, 128)).astype(np.float32)
+    F /= np.linalg.norm(F, axis=1, keepdims=True)
+    C0 = F[rng.choice(len(F), 100, replace=False)].copy()
+    for mode in (sf.KMEANS_TENSOR, sf.KMEANS_TENSOR_SINGLE):
+        check_same(sf, oracle_mod, F, C0, 4, mode)
 
 
 def test_kmeans_ties_go_to_lowest_index(sf, oracle_mod):
