@@ -532,7 +532,11 @@ KMEANS_AUTO, KMEANS_TENSOR, KMEANS_CUDA_CORES, KMEANS_TENSOR_SINGLE = 0, 1, 2, 3
 def kmeans(F, C0, max_iter: int = 50, mode: int = KMEANS_AUTO):
     """Lloyd's k-means on the rows of F (§4.1 step 6) from centroids C0 (k x d):
     returns (labels int32 tensor [n], centroids float32 tensor [k x d],
-    assignments performed, inertia of the last assignment)."""
+    assignments performed, inertia of the last assignment). mode:
+    KMEANS_AUTO (tensor cores when the shape allows), KMEANS_TENSOR (tcgen05
+    distances from split TF32 operands), KMEANS_TENSOR_SINGLE (one TF32
+    product per pair) or KMEANS_CUDA_CORES; every mode returns the labels of
+    the same FP32 decision."""
     torch = _torch()
     n, d = F.shape
     k = C0.shape[0]
