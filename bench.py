@@ -5,10 +5,21 @@ One step = one pass of the whole path over one batch of synthetic input
 (a seeded stochastic-block-model graph and a block of random signals already
 resident in device memory):
   CSR build from the edge list -> lambda_N by Lanczos (40 steps) ->
-  moment sweep (p orders, FP32 blocks) -> dichotomy for lambda_k ->
-  coefficients -> filter sweep (p orders, storage per workload) ->
-  row-normalised features.
+  moment sweep (p orders, on the count's own probe block) -> dichotomy for
+  lambda_k -> coefficients -> filter sweep (p orders, on R) ->
+  row-normalised features; both sweeps store their blocks as the workload
+  says (BF16 at the default) and accumulate in FP32.
 Updates counted per step: (nnz_off + N) * R * p for each of the two sweeps.
+
+Besides the contract's keys the JSON line carries: the roofline of the
+dominant sweep kernel (and of each variant) with its ncu DRAM traffic, the
+measured ceiling of its random-row gathers, where a step's device time goes,
+the same step with FP32 blocks, the end-to-end timing from pinned host
+buffers, k-means on the step's features (tensor cores with split and with
+single TF32 products, CUDA cores), the method end to end against the
+generating communities (and on the normalised Laplacian and the stability
+measure up to 200k nodes), the CPU oracle's rate, the filter's error against
+the FP64 oracle, and the SM clocks sampled during the timed region.
 
 Default workload ("sbm1m"): N = 1,000,000, k = 100 equal communities, mean
 degree 30, c_out/c_in = 0.08, unit weights, R = 128 signals, p = 200, filter
