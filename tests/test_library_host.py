@@ -77,6 +77,26 @@ def test_argument_errors_without_gpu(sflib):
     assert st == 1 and b"lam_max" in L.sf_last_error()
 
 
+def test_kmeans_argument_checks_without_gpu(sflib):
+    """sf_kmeans checks its arguments before any device work: bad sizes and modes, and a tensor-core request
+    for a shape the tensor cores do not take, return SF_ERR_ARG with a message (the pointers are never read)."""
+    L = sflib.lib()
+    fake = C.c_void_p(16)  # 16-byte aligned, never dereferenced
+    it = C.c_int32(0)
+    iner = C.c_double(0.0)
+
+    def call(n, d, k, max_iter, mode):
+        return L.sf_kmeans(fake, n, d, k, fake, max_iter, mode, fake, C.byref(it), C.byref(iner), None)
+
+    assert call(100, 32, 0, 10, 0) == 1 and b"k must be" in L.sf_last_error()
+    assert call(0, 32, 4, 10, 0) == 1
+    assert call(100, 32, 4, 0, 0) == 1 and b"max_iter" in L.sf_last_error()
+    assert call(100, 32, 4, 10, 7) == 1 and b"mode" in L.sf_last_error()
+    for mode in (sflib.KMEANS_TENSOR, sflib.KMEANS_TENSOR_SINGLE):
+        assert call(100, 30, 4, 10, mode) == 1 and b"tensor-core" in L.sf_last_error()  # d not a multiple of 32
+        assert call(100, 32, 129, 10, mode) == 1  # k > 128
+
+
 def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
     """The order table m* of §2.4 (host FP64, Clenshaw evaluation) equals the
     oracle's (direct cos(j arccos) evaluation) on a spread of cutoffs."""
