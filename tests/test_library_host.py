@@ -97,6 +97,29 @@ def test_kmeans_argument_checks_without_gpu(sflib):
         assert call(100, 32, 129, 10, mode) == 1  # k > 128
 
 
+def test_stability_and_rand_argument_checks_without_gpu(sflib):
+    """sf_adjusted_rand and sf_stability reject bad arguments before reading any pointer or launching work."""
+    L = sflib.lib()
+    fake = C.c_void_p(16)
+    ari = C.c_double(0.0)
+    assert L.sf_adjusted_rand(None, fake, 10, 2, 2, None, C.byref(ari)) == 1
+    assert L.sf_adjusted_rand(fake, fake, 0, 2, 2, None, C.byref(ari)) == 1
+    assert L.sf_adjusted_rand(fake, fake, 10, 5000, 5000, None, C.byref(ari)) == 1 and b"2^24" in L.sf_last_error()
+    gam = np.zeros(8)
+    lk = np.zeros(8)
+    dp = C.POINTER(C.c_double)
+
+    def stab(J, kmin, kmax, max_iter, starts):
+        return L.sf_stability(fake, 10.0, 20, fake, fake, J, 8, kmin, kmax, max_iter, starts, 1, None, None,
+                              gam.ctypes.data_as(dp), lk.ctypes.data_as(dp))
+
+    assert stab(1, 2, 4, 10, 2) == 1 and b"J >= 2" in L.sf_last_error()
+    assert stab(3, 5, 4, 10, 2) == 1 and b"kmin" in L.sf_last_error()
+    assert stab(3, 2, 4, 0, 2) == 1 and b"max_iter" in L.sf_last_error()
+    assert stab(3, 2, 4, 10, 0) == 1 and b"starts" in L.sf_last_error()
+    assert np.all(gam == 0) and np.all(lk == 0)  # outputs untouched
+
+
 def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
     """The order table m* of §2.4 (host FP64, Clenshaw evaluation) equals the
     oracle's (direct cos(j arccos) evaluation) on a spread of cutoffs."""
