@@ -120,6 +120,32 @@ def test_stability_and_rand_argument_checks_without_gpu(sflib):
     assert np.all(gam == 0) and np.all(lk == 0)  # outputs untouched
 
 
+def test_filter_and_moment_argument_checks_without_gpu(sflib):
+    """The sweeps' entry points reject a missing graph or block, a bad lam_max, order, width or dtype before
+    they look at the graph or the device; the host outputs stay untouched."""
+    L = sflib.lib()
+    fake = C.c_void_p(16)
+    dp = C.POINTER(C.c_double)
+    coef = np.ones(3)
+    mom = np.zeros(5)
+
+    def filt(g, lam, p, R, dtype, n_sig):
+        return L.sf_cheb_filter(g, lam, coef.ctypes.data_as(dp), 1, p, R, dtype, n_sig, fake, None, None)
+
+    def moments(g, lam, p, R, dtype, n_sig):
+        return L.sf_cheb_moments(g, lam, R, dtype, n_sig, p, mom.ctypes.data_as(dp), None, None)
+
+    for call in (filt, moments):
+        assert call(None, 10.0, 2, fake, 0, 4) == 1 and b"graph" in L.sf_last_error()
+        assert call(fake, -1.0, 2, fake, 0, 4) == 1 and b"lam_max" in L.sf_last_error()
+        assert call(fake, float("nan"), 2, fake, 0, 4) == 1
+        assert call(fake, 10.0, -1, fake, 0, 4) == 1 and b"p must" in L.sf_last_error()
+        assert call(fake, 10.0, 2, fake, 0, 0) == 1 and b"n_sig" in L.sf_last_error()
+        assert call(fake, 10.0, 2, None, 0, 4) == 1 and b"R is NULL" in L.sf_last_error()
+        assert call(fake, 10.0, 2, fake, 2, 4) == 1 and b"dtype" in L.sf_last_error()  # FP16 input blocks
+    assert np.all(mom == 0)
+
+
 def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
     """The order table m* of §2.4 (host FP64, Clenshaw evaluation) equals the
     oracle's (direct cos(j arccos) evaluation) on a spread of cutoffs."""
