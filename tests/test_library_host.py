@@ -146,6 +146,22 @@ def test_filter_and_moment_argument_checks_without_gpu(sflib):
     assert np.all(mom == 0)
 
 
+def test_graph_and_feature_argument_checks_without_gpu(sflib):
+    """sf_csr_build and sf_features reject bad sizes and missing buffers before any device work; the
+    graph handle is cleared on failure, and an empty feature block is a no-op."""
+    L = sflib.lib()
+    fake = C.c_void_p(16)
+    out = C.c_void_p(12345)
+    assert L.sf_csr_build(0, 10, fake, fake, None, None, C.byref(out)) == 1 and out.value is None
+    assert L.sf_csr_build(10, -1, fake, fake, None, None, C.byref(out)) == 1
+    assert L.sf_csr_build(10, 1 << 30, fake, fake, None, None, C.byref(out)) == 1 and b"2^31" in L.sf_last_error()
+    assert L.sf_csr_build(10, 5, None, fake, None, None, C.byref(out)) == 1 and b"src/dst" in L.sf_last_error()
+    assert L.sf_csr_build(10, 5, fake, fake, None, None, None) == 1 and b"out is NULL" in L.sf_last_error()
+    assert L.sf_features(None, 10, 4, 1, fake, None) == 1
+    assert L.sf_features(fake, 10, 0, 1, fake, None) == 1 and b"n_sig" in L.sf_last_error()
+    assert L.sf_features(fake, 0, 4, 1, fake, None) == 0  # nothing to do, no launch
+
+
 def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
     """The order table m* of §2.4 (host FP64, Clenshaw evaluation) equals the
     oracle's (direct cos(j arccos) evaluation) on a spread of cutoffs."""
