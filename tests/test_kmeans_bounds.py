@@ -7,7 +7,10 @@ with TF32 rounding emulated bit for bit in numpy (10 explicit mantissa bits):
   from zero): |r| <= 2^-22 |x| and |f.c - (hi.hi + hi.lo + lo.hi)| <= 3.01
   2^-22 sum |f_j c_j|;
 * the margins the kernel uses cover twice these terms plus the FP32
-  accumulation of the products (one ulp per addition)."""
+  accumulation of the products (one ulp per addition);
+* the centroid update's fixed point: the integer recipe gives floor(x 2^sh)
+  exactly across binades and for subnormals, and the scale keeps n partial
+  sums below 2^62."""
 import numpy as np
 
 TF32_DROP = 13  # mantissa bits FP32 has beyond TF32
@@ -75,3 +78,40 @@ def test_margins_cover_the_bounds():
     acc_split = 3 * d * 2.0 ** -23    # three products per K step
     assert 2.0 * (2.0 ** -9 + 2.0 ** -20 + acc_single) <= 2.0 ** -7
     assert 2.0 * (3.01 * 2.0 ** -22 + acc_split) <= 2.0 ** -12
+
+
+def fix_shift(bmax, n):
+    """The centroid sums' scale: n < 2^nb, max |F_ij| < 2^e (frexp), sh = 62 - nb - e, at most 187."""
+    if not bmax > 0:
+        return 0
+    e = int(np.frexp(np.float32(bmax))[1])
+    return min(62 - int(n).bit_length() - e, 187)
+
+
+def fix_value(x, sh):
+    """floor(x 2^sh) by the integer recipe of the update: the signed significand placed at bit 39 and shifted
+    right arithmetically by 189 - sh - e (e = 1 and no implicit bit for subnormals), shifts clamped to 63."""
+    u = int(np.array([x], np.float32).view(np.uint32)[0])
+    e = (u >> 23) & 255
+    hi = ((u << 7) & 0x3FFFFF80) | (0x40000000 if e else 0)
+    amt = min(189 - sh - max(e, 1), 63)
+    assert amt >= 1
+    v = -hi if u >> 31 else hi
+    return (v << 32) >> amt
+
+
+def test_fixed_point_centroid_sums():
+    from fractions import Fraction
+
+    rng = np.random.default_rng(5)
+    for n, lo, hi_exp in ((1000, -30, 0), (3, -140, -125), (1 << 20, -10, 10)):
+        x = (rng.standard_normal(min(n, 3000)) * np.exp2(rng.uniform(lo, hi_exp, min(n, 3000)))).astype(np.float32)
+        sh = fix_shift(np.abs(x).max(), n)
+        q = [fix_value(v, sh) for v in x]
+        exact = [Fraction(float(v)) * Fraction(2) ** sh for v in x]
+        assert all(e - 1 < qi <= e for qi, e in zip(q, exact))  # floor: error below one unit of 2^-sh
+        # n values of magnitude up to max|x| keep every partial sum below 2^62
+        assert int(n) * max(abs(qi) for qi in q) < 2 ** 62
+    # subnormal data: the cap keeps the shift at or below 187, where every subnormal is a whole number of units
+    assert fix_shift(np.float32(1e-44), 10) == 187
+    assert fix_value(np.float32(1e-44), 187) == int(Fraction(float(np.float32(1e-44))) * Fraction(2) ** 187)
