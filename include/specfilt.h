@@ -66,6 +66,19 @@ enum {
     SF_ALGO_CLENSHAW = 2  /* backward Clenshaw sum, one cutoff at a time */
 };
 
+/*
+ * Memory-system hints of the sweep kernels (sf_opts.sweep_hints: 0 = the
+ * library default, SF_HINT_IDX_EVICT_FIRST | SF_HINT_OUT_STREAMING |
+ * SF_HINT_MIXED_ADD; SF_HINTS_NONE; or any OR of these). They change where
+ * data is cached or how a sum is issued, never the value of a result.
+ */
+enum {
+    SF_HINTS_NONE = -1,
+    SF_HINT_IDX_EVICT_FIRST = 1, /* staged index copies read with an L2 evict-first policy */
+    SF_HINT_OUT_STREAMING = 2,   /* T_j / b_j stores marked streaming (evict-first) */
+    SF_HINT_MIXED_ADD = 8        /* unit weights, 16-bit blocks: FP32 += 16-bit adds in one instruction */
+};
+
 /* Sweep kernel variants (sf_opts.sweep_kernel). */
 enum {
     SF_SWEEP_AUTO = 0,   /* the staged tiles (SF_SWEEP_TILED) unless sf_autotune chose otherwise */
@@ -110,6 +123,7 @@ enum {
  *                   are bit-identical; the FP64 moment sums may differ in the
  *                   last bits (rows reach the block partial sums in another
  *                   order).
+ *   sweep_hints     SF_HINT_* mask, SF_HINTS_NONE, or 0 for the default.
  */
 typedef struct sf_opts {
     int32_t storage;
@@ -122,6 +136,7 @@ typedef struct sf_opts {
     int32_t carveout_pct;
     int32_t l2_window;
     int32_t sweep_kernel;
+    int32_t sweep_hints;
 } sf_opts;
 
 typedef struct sf_graph sf_graph; /* device-resident CSR of W, owned by the library */

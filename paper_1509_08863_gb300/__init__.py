@@ -58,6 +58,7 @@ __all__ = [
 F32, BF16, F16 = 0, 1, 2
 ALGO_AUTO, ALGO_FORWARD, ALGO_CLENSHAW = 0, 1, 2
 SWEEP_AUTO, SWEEP_TILED, SWEEP_DIRECT = 0, 1, 2
+HINTS_NONE, HINT_IDX_EVICT_FIRST, HINT_OUT_STREAMING, HINT_MIXED_ADD = -1, 1, 2, 8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspecfilt.so")
@@ -82,6 +83,7 @@ class _Opts(C.Structure):
         ("carveout_pct", C.c_int32),
         ("l2_window", C.c_int32),
         ("sweep_kernel", C.c_int32),
+        ("sweep_hints", C.c_int32),
     ]
 
 
@@ -99,10 +101,12 @@ class Opts:
     carveout_pct: int = 0
     l2_window: int = 0
     sweep_kernel: int = 0
+    sweep_hints: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.storage, self.algo, self.slab_cols, self.block_warps, self.blocks_per_sm,
-                      self.ckpt_every, self.mem_cap_mb, self.carveout_pct, self.l2_window, self.sweep_kernel)
+                      self.ckpt_every, self.mem_cap_mb, self.carveout_pct, self.l2_window, self.sweep_kernel,
+                      self.sweep_hints)
 
 
 _vp = C.c_void_p
@@ -512,7 +516,7 @@ def autotune(g: Graph, n_sig: int, storage: int = F32, n_cut: int = 1, base: Opt
     _check(lib().sf_autotune(g.handle, int(n_sig), int(storage), int(n_cut), bp, _stream(), C.byref(best)),
            "sf_autotune")
     return Opts(best.storage, best.algo, best.slab_cols, best.block_warps, best.blocks_per_sm, best.ckpt_every,
-                best.mem_cap_mb, best.carveout_pct, best.l2_window, best.sweep_kernel)
+                best.mem_cap_mb, best.carveout_pct, best.l2_window, best.sweep_kernel, best.sweep_hints)
 
 
 def profile_begin():

@@ -19,11 +19,12 @@
 
 namespace sf {
 
+// Blocks are in slice-row order (row t of a block is graph row perm[t], see
+// SellMatrix); sell_idx holds the column indices as slice rows.
 struct SddmmParams {
     int32_t n;
     int64_t sell_slices;
     const int32_t *sell_ptr;
-    const int32_t *sell_perm;
     const int32_t *sell_idx;
     int32_t ld;
     const float *Gb;   // Gb_j, own rows
@@ -32,7 +33,7 @@ struct SddmmParams {
     const float *Tj;   // T_j own rows, for <G, T_j>
     float csd;         // 1 for j == 1, 2 for j >= 2
     float *Msell;      // [entries] accumulated edge products, sliced-ELL order
-    float *Mdiag;      // [n] accumulated diagonal products
+    float *Mdiag;      // [rows] accumulated diagonal products, slice-row order
     double *part;      // [gridDim.x] partial <G, T_j>
     int32_t *status;
 };
@@ -58,8 +59,9 @@ __global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
     int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
-    unsigned char *s_buf0 = smem_raw + 64;
+    unsigned char *s_buf0 = smem_raw + C::header;
     constexpr int buf_bytes = C::buf_bytes(false);
+    static_assert(C::stages >= 2, "two stage buffers");
     __shared__ double s_red[8];
 
     const int tid = threadIdx.x;
@@ -74,19 +76,17 @@ __global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
     auto issue = [&](int tile, int b) {
         unsigned char *base = s_buf0 + b * buf_bytes;
         int32_t *sp = reinterpret_cast<int32_t *>(base);
-        int32_t *pm = sp + C::sp_ints;
-        int32_t *ix = pm + C::rows;
+        int32_t *ix = sp + C::sp_ints;
         const int32_t s0 = tile * C::slices;
         const int32_t e0 = P.sell_ptr[s0], e1 = P.sell_ptr[s0 + C::slices];
         const int32_t cnt = e1 - e0;
         const bool fits = (P.Tm1 != nullptr) && cnt <= C::entries;
-        const uint32_t bytes = (C::sp_ints + C::rows) * 4 + (fits ? (uint32_t)cnt * 4u : 0u);
+        const uint32_t bytes = C::sp_ints * 4 + (fits ? (uint32_t)cnt * 4u : 0u);
         s_meta[2 * b] = e0;
         s_meta[2 * b + 1] = fits ? 1 : 0;
         fence_proxy_async();
         mbar_arrive_expect_tx(&s_bar[b], bytes);
         bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
-        bulk_g2s(pm, P.sell_perm + (int64_t)s0 * kSliceRows, C::rows * 4, &s_bar[b]);
         if (fits && cnt > 0) bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
     };
 
@@ -110,14 +110,13 @@ __global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
             return;
         }
         const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
-        const int32_t *s_pm = s_sp + C::sp_ints;
-        const int32_t *s_ix = s_pm + C::rows;
+        const int32_t *s_ix = s_sp + C::sp_ints;
         const int32_t e0 = s_meta[2 * b];
         const bool fits = s_meta[2 * b + 1] != 0;
 
         for (int tr = grp; tr < C::rows; tr += ngrp) {
-            const int32_t i = s_pm[tr];
-            if (i < 0) continue;
+            const int32_t i = tile * C::rows + tr;  // slice row: the row of every block
+            if (i >= P.n) continue;
             const int sl = tr / kSliceRows, pos = tr % kSliceRows;
             const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
             const int32_t eo = so - e0 + pos * ls;
@@ -180,7 +179,8 @@ __device__ __forceinline__ int64_t sell_pos(const int32_t *sptr, const int32_t *
 }
 
 // grad[e] = (2/lam)(Md[u] + Md[v] - M_uv - M_vu) for CSR entry e = (u, v); the
-// entry (v, u) is found by binary search in the sorted row v.
+// entry (v, u) is found by binary search in the sorted row v. Md is in
+// slice-row order.
 __global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t *colidx, const int32_t *sptr,
                                  const int32_t *iperm, const float *Msell, const float *Mdiag, float two_over_lam,
                                  float *grad) {
@@ -201,7 +201,7 @@ __global__ void edge_grad_kernel(int32_t n, const int32_t *rowptr, const int32_t
                 else hi = mid - 1;
             }
             const float muv = Msell[sell_pos(sptr, iperm, u, e - beg)];
-            grad[e] = two_over_lam * ((Mdiag[u] + Mdiag[v]) - (muv + mvu));
+            grad[e] = two_over_lam * ((Mdiag[iperm[u]] + Mdiag[iperm[v]]) - (muv + mvu));
         }
     }
 }
@@ -267,13 +267,15 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->n;
     const int ld = sh.ld;
-    // one block = n + 1 rows: row n stays zero (padding of the sliced-ELL layout)
-    const size_t blk = (size_t)(n + 1) * ld;
-    SF_ARG((int64_t)(n + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
     {
         std::lock_guard<std::mutex> lk(g->sell_mu);
         if ((st = sell_build(&g->sell, g->n, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, s))) return st;
     }
+    // one block = rows + 1 rows in slice-row order: row `rows` stays zero (padding of the sliced-ELL layout)
+    const int64_t rows = g->sell.rows;
+    const int32_t *perm = g->sell.perm;
+    const size_t blk = (size_t)(rows + 1) * ld;
+    SF_ARG((int64_t)(rows + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
     const int64_t cap_mb = o.mem_cap_mb > 0 ? o.mem_cap_mb : 16384;
     int k = o.ckpt_every;
     if (k <= 0) k = ((double)(p + 1) * blk * 4 <= (double)cap_mb * (1 << 20)) ? 1 : (int)ceil(sqrt((double)p));
@@ -294,8 +296,8 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         if ((st = sc.get(&work[q], blk))) return st;
         if ((st = sc.get(&bb[q], blk))) return st;
     }
-    if ((st = sc.get(&gq, blk)) || (st = sc.get(&coef, (size_t)p + 1)) || (st = sc.get(&dtil, (size_t)n)) ||
-        (st = sc.get(&mdiag, (size_t)n)) || (st = sc.get(&part, (size_t)sm_count() * 4 + 1)) ||
+    if ((st = sc.get(&gq, blk)) || (st = sc.get(&coef, (size_t)p + 1)) || (st = sc.get(&dtil, (size_t)rows)) ||
+        (st = sc.get(&mdiag, (size_t)rows)) || (st = sc.get(&part, (size_t)sm_count() * 4 + 1)) ||
         (st = sc.get(&ga, (size_t)p + 1)))
         return st;
     if ((st = sc.get(&msell, (size_t)g->sell.entries + kCsrPad))) return st;
@@ -312,41 +314,42 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         SF_CHECK_CUDA(cudaMemcpyAsync(coef, cf.data(), sizeof(float) * (p + 1), cudaMemcpyHostToDevice, s));
     }
     SF_CHECK_CUDA(cudaMemsetAsync(msell, 0, sizeof(float) * ((size_t)g->sell.entries + kCsrPad), s));
-    SF_CHECK_CUDA(cudaMemsetAsync(mdiag, 0, sizeof(float) * n, s));
+    SF_CHECK_CUDA(cudaMemsetAsync(mdiag, 0, sizeof(float) * rows, s));
     SF_CHECK_CUDA(cudaMemsetAsync(ga, 0, sizeof(double) * (p + 1), s));
-    if (n > 0) {
-        dtil_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->strength, (int32_t)n, 2.0 / lam_max, nullptr, nullptr,
-                                                                dtil, nullptr);
+    if (rows > 0) {
+        dtil_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(g->strength, (int32_t)rows, 2.0 / lam_max, nullptr,
+                                                                   nullptr, dtil, nullptr, perm, nullptr);
         if ((st = check_launch("dtil_kernel"))) return st;
     }
     const float *val = g->unit_weights ? nullptr : g->val;
     const int pack_grid = 2 * sm_count();
     const double two_over_lam = 2.0 / lam_max;
+    const int n_slabs = (n_sig + ld - 1) / ld;
 
     for (int c0 = 0; c0 < n_sig; c0 += ld) {
         const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;
         auto T_at = [&](int j) { return store + (size_t)slot[j] * blk; };
         // ---- forward: T_0..T_p, keeping the checkpoint slots
         pack_kernel<float><<<pack_grid, 256, 0, s>>>(R, SF_F32, (int32_t)n, n_sig, c0, w, ld, work[0], nullptr, 0, 0,
-                                                     nullptr, 1, 0, nullptr, nullptr, nullptr);
+                                                     nullptr, 1, 0, nullptr, nullptr, nullptr, nullptr, perm,
+                                                     (int32_t)rows);
         if ((st = check_launch("pack_kernel"))) return st;
         SF_CHECK_CUDA(cudaMemcpyAsync(T_at(0), work[0], blk * 4, cudaMemcpyDeviceToDevice, s));
         StepParams P = {};
         P.n = (int32_t)n;
-        P.rowptr = g->rowptr;
-        P.colidx = g->colidx;
-        P.val = val;
         P.sell_ptr = g->sell.sptr;
-        P.sell_perm = g->sell.perm;
-        P.sell_idx = g->sell.idx;
+        P.sell_idx = g->sell.ridx;
         P.sell_val = g->sell.val;
         P.dtil = dtil;
         P.wscale_u = (float)two_over_lam;
         P.ld = ld;
+        P.flags = step_flags(o);
         P.n_cut = 0;
         P.status = device_status();
-        // compulsory bytes: CSR once, gathered block once, T_{j-2} read, T_j written
-        const double csr_b = (double)(n + 1) * 4 + (double)n * 4 + (double)g->nnz * (val ? 8 : 4);
+        // compulsory bytes: the order's CSR once (shared over its slabs), gathered block once,
+        // T_{j-2} read, T_j written
+        const double csr_b =
+            ((double)(n + 1) * 4 + (double)n * 4 + (double)g->nnz * (val ? 8 : 4)) / (double)n_slabs;
         const double blk_b = (double)n * w * 4;
         auto fwd_step = [&](const float *Xp, const float *Zp, float *outp, int j) {
             P.X = Xp;
@@ -389,7 +392,8 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         };
         // Gb_p = a_p G (pack with b-start), packed G
         pack_kernel<float><<<pack_grid, 256, 0, s>>>(G, SF_F32, (int32_t)n, n_sig, c0, w, ld, gq, nullptr, 0, 1, coef,
-                                                     p + 1, p, nullptr, bb[p % 3], nullptr);
+                                                     p + 1, p, nullptr, bb[p % 3], nullptr, nullptr, perm,
+                                                     (int32_t)rows);
         if ((st = check_launch("pack_kernel"))) return st;
         // the Clenshaw sweep on G: Gb_j = a_j G + m Lt Gb_{j+1} - Gb_{j+2}
         StepParams C = P;
@@ -401,8 +405,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         D.n = (int32_t)n;
         D.sell_slices = g->sell.n_slices;
         D.sell_ptr = g->sell.sptr;
-        D.sell_perm = g->sell.perm;
-        D.sell_idx = g->sell.idx;
+        D.sell_idx = g->sell.ridx;
         D.ld = ld;
         D.Gq = gq;
         D.Msell = msell;
@@ -428,14 +431,15 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
             D.csd = (j == 1) ? 1.0f : 2.0f;
             // index stream once, G and T_j rows, Gb_j rows and T_{j-1} gathered once (when products
             // are taken), edge and diagonal accumulators read and written
-            const double db = (double)g->sell.entries * 4 + blk_b * 2 +
+            const double db = (double)g->sell.entries * 4 / (double)n_slabs + blk_b * 2 +
                               (D.Tm1 ? blk_b * 2 + 8.0 * ((double)g->nnz + n) : 0.0);
             if ((st = sddmm_launch(sh.lpr, D, sddmm_grid, 256, s, db))) return st;
             pair_sum_kernel<<<1, 256, 0, s>>>(part, sddmm_grid, 1, ga + j);
             if ((st = check_launch("pair_sum_kernel"))) return st;
         }
         if (grad_R) {
-            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(gR, (int32_t)n, ld, w, 1, grad_R, n_sig, c0);
+            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(gR, (int32_t)n, ld, w, 1, grad_R, n_sig, c0, nullptr, perm,
+                                                        (int32_t)rows);
             if ((st = check_launch("unpack_kernel"))) return st;
         }
     }

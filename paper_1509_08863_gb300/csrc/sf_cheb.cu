@@ -151,13 +151,18 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     return st;
 }
 
-// Compulsory bytes of one sweep launch: CSR streamed once, the gathered slab
-// read once, the streamed slabs, the accumulators read and written.
+// Algorithmic (compulsory) bytes of one sweep launch over a slab of w of the
+// block's columns: per order the CSR is read once (rowptr, d~, the indices and,
+// for weighted graphs, the weights), the gathered block once, the streamed
+// blocks once and the accumulators read and written. The order's CSR bytes are
+// shared out over its n_slabs launches, so that the launches of one order add
+// up to one CSR read however many slabs the block is cut into.
 static double step_bytes(int64_t n, int64_t nnz, bool unit, bool batched, int w, int storage, int mode,
-                         bool has_z, int n_cut, bool final_f32) {
+                         bool has_z, int n_cut, bool final_f32, int n_slabs) {
     const double b = bytes_of(storage);
-    double by = (double)(n + 1) * 4 + (double)n * 4 + (double)nnz * (unit ? 4 : 8);
-    if (batched) by += (double)n * 8;
+    double csr = (double)(n + 1) * 4 + (double)n * 4 + (double)nnz * (unit ? 4 : 8);
+    if (batched) csr += (double)n * 8;
+    double by = csr / (double)(n_slabs > 0 ? n_slabs : 1);
     const double blk = (double)n * w * b;
     by += blk;                              // gathered T_{j-1}
     if (has_z) by += blk;                   // T_{j-2}
@@ -190,6 +195,13 @@ static sf_status view_of(const sf_graph *g, cudaStream_t s, GraphView *v) {
     *v = GraphView{g->n, g->nnz, g->rowptr, g->colidx, g->unit_weights ? nullptr : g->val, g->strength, nullptr, 1,
                    &g->sell};
     return SF_OK;
+}
+
+// Kernel hints of a call: the library default, none, or the caller's SF_HINT_* mask.
+int32_t step_flags(const sf_opts &o) {
+    if (o.sweep_hints == 0) return kStepFlagsDefault;
+    if (o.sweep_hints < 0) return 0;
+    return o.sweep_hints & (STEP_IDX_EVICT_FIRST | STEP_OUT_STREAMING | STEP_MIXED_ADD);
 }
 
 static sf_status resolve_opts(const sf_opts *o, int64_t n, int n_sig, sf_opts *r) {
@@ -244,17 +256,19 @@ static sf_status release_l2_window(cudaStream_t s) {
 static sf_status launch_pack(int storage, int grid, cudaStream_t s, const void *R, int r_dtype, int32_t n,
                              int32_t n_sig, int32_t c0, int32_t w, int32_t ld, void *T0, float *Y, int64_t ystride,
                              int32_t n_cut, const float *coef, int32_t coef_ld, int32_t jcoef, const int32_t *gid,
-                             void *bstart, double *part, const uint32_t *maxbits) {
+                             void *bstart, double *part, const uint32_t *maxbits, const int32_t *perm,
+                             int32_t rows) {
     if (storage == SF_F32)
         pack_kernel<float><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (float *)T0, Y, ystride, n_cut, coef,
-                                                coef_ld, jcoef, gid, (float *)bstart, part, maxbits);
+                                                coef_ld, jcoef, gid, (float *)bstart, part, maxbits, perm, rows);
     else if (storage == SF_BF16)
         pack_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (__nv_bfloat16 *)T0, Y,
                                                         ystride, n_cut, coef, coef_ld, jcoef, gid,
-                                                        (__nv_bfloat16 *)bstart, part, maxbits);
+                                                        (__nv_bfloat16 *)bstart, part, maxbits, perm, rows);
     else
         pack_kernel<__half><<<grid, 256, 0, s>>>(R, r_dtype, n, n_sig, c0, w, ld, (__half *)T0, Y, ystride, n_cut,
-                                                 coef, coef_ld, jcoef, gid, (__half *)bstart, part, maxbits);
+                                                 coef, coef_ld, jcoef, gid, (__half *)bstart, part, maxbits, perm,
+                                                 rows);
     return check_launch("pack_kernel");
 }
 
@@ -275,31 +289,35 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     SF_ARG(status, "device status word unavailable");
     const int ld = sh.ld;
     if (o.l2_window > 0) {
-        if ((st = setup_l2_window(&sh, (size_t)(G.n + 1) * ld * bytes_of(o.storage)))) return st;
+        if ((st = setup_l2_window(&sh, (size_t)(G.sell->rows + 1) * ld * bytes_of(o.storage)))) return st;
     }
     const int64_t n = G.n;
+    // blocks are in slice-row order: rows + 1 rows, the last one the zero row
+    const int64_t rows = G.sell->rows;
+    const int32_t *perm = G.sell->perm;
     const size_t eb = bytes_of(o.storage);
     Scratch sc(s);
     void *buf[3] = {nullptr, nullptr, nullptr};
     void *qbuf = nullptr;
     float *yacc = nullptr, *coef = nullptr, *dtil = nullptr, *wscale = nullptr;
     double *part = nullptr, *tol = nullptr;
+    int32_t *gid_t = nullptr;
     const int nbuf = 3;
-    SF_ARG((int64_t)(n + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
+    SF_ARG((int64_t)(rows + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets: use narrower slabs");
     for (int k = 0; k < nbuf; ++k) {
-        // row n stays zero: padding entries of the sliced-ELL layout gather it
-        if ((st = sc.get((char **)&buf[k], (size_t)(n + 1) * ld * eb))) return st;
-        SF_CHECK_CUDA(cudaMemsetAsync((char *)buf[k] + (size_t)n * ld * eb, 0, (size_t)ld * eb, s));
+        // row `rows` stays zero: padding entries of the sliced-ELL layout gather it
+        if ((st = sc.get((char **)&buf[k], (size_t)(rows + 1) * ld * eb))) return st;
+        SF_CHECK_CUDA(cudaMemsetAsync((char *)buf[k] + (size_t)rows * ld * eb, 0, (size_t)ld * eb, s));
     }
-    if (mode == MODE_CLEN && (st = sc.get((char **)&qbuf, (size_t)n * ld * eb))) return st;
+    if (mode == MODE_CLEN && (st = sc.get((char **)&qbuf, (size_t)(rows + 1) * ld * eb))) return st;
     const int ncy = (mode == MODE_FWD) ? n_cut : (mode == MODE_CLEN ? 1 : 0);
-    if (ncy && (st = sc.get(&yacc, (size_t)ncy * n * ld))) return st;
+    if (ncy && (st = sc.get(&yacc, (size_t)ncy * rows * ld))) return st;
     const int ncoef = (mode == MODE_MOM || coef_dev) ? 0 : G.n_graphs * n_cut * (p + 1);
     if (ncoef && (st = sc.get(&coef, (size_t)ncoef))) return st;
     if (coef_dev) coef = const_cast<float *>(coef_dev);
-    if ((st = sc.get(&dtil, (size_t)n))) return st;
+    if ((st = sc.get(&dtil, (size_t)rows))) return st;
     if (G.gid) {
-        if ((st = sc.get(&wscale, (size_t)n))) return st;
+        if ((st = sc.get(&wscale, (size_t)rows)) || (st = sc.get(&gid_t, (size_t)rows))) return st;
         if (tol_dev) tol = const_cast<double *>(tol_dev);
         else if ((st = sc.get(&tol, (size_t)G.n_graphs))) return st;
     }
@@ -326,33 +344,31 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     if (G.gid && !tol_dev) {
         SF_CHECK_CUDA(cudaMemcpyAsync(tol, two_over_lam_g, sizeof(double) * G.n_graphs, cudaMemcpyHostToDevice, s));
     }
-    if (n > 0) {
-        dtil_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G.strength, (int32_t)n, two_over_lam, G.gid, tol,
-                                                                dtil, wscale);
+    if (rows > 0) {
+        dtil_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(G.strength, (int32_t)rows, two_over_lam, G.gid,
+                                                                   tol, dtil, wscale, perm, gid_t);
         if ((st = check_launch("dtil_kernel"))) return st;
     }
     const int pack_grid = 2 * sm_count();
+    const int n_slabs = (n_sig + ld - 1) / ld;
     for (int c0 = 0; c0 < n_sig; c0 += ld) {
         const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;
         StepParams P = {};
         P.n = (int32_t)n;
-        P.rowptr = G.rowptr;
-        P.colidx = G.colidx;
-        P.val = G.val;
         P.sell_ptr = G.sell->sptr;
-        P.sell_perm = G.sell->perm;
-        P.sell_idx = G.sell->idx;
+        P.sell_idx = G.sell->ridx;
         P.sell_val = G.sell->val;
         P.dtil = dtil;
         P.wscale = wscale;
         P.wscale_u = (float)two_over_lam;
-        P.gid = G.gid;
+        P.gid = gid_t;
         P.ld = ld;
+        P.flags = step_flags(o);
         P.coef = coef;
         P.coef_ld = p + 1;
         P.n_cut = n_cut;
         P.Y = yacc;
-        P.ystride = n * ld;
+        P.ystride = rows * ld;
         P.part = part;
         P.status = status;
         const bool unit = G.val == nullptr;
@@ -365,8 +381,8 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
         if (mode == MODE_FWD || mode == MODE_MOM) {
             // T_0 = R (and Y_c = a_c0 T_0, or <T0,T0>)
             if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, buf[0], yacc,
-                                  n * ld, n_cut, coef, p + 1, 0, G.gid, nullptr, mode == MODE_MOM ? part : nullptr,
-                                  maxbits)))
+                                  rows * ld, n_cut, coef, p + 1, 0, G.gid, nullptr, mode == MODE_MOM ? part : nullptr,
+                                  maxbits, perm, (int32_t)rows)))
                 return st;
             if (mode == MODE_MOM) {
                 pair_sum_kernel<<<1, 256, 0, s>>>(part, pack_grid, 1, mom);
@@ -380,7 +396,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 P.out = buf[j % 3];
                 P.m = (j == 1) ? 1.0f : 2.0f;
                 P.j = j;
-                double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false);
+                double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false, n_slabs);
                 if (mode == MODE_MOM) {  // the kernel's last block adds <T_j,T_j>, <T_j,T_{j-1}> into mom
                     P.dots = mom + 2 * j;
                     P.done = done;
@@ -392,7 +408,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
             // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};
             // Y = a_0 R + Lt b_1 - b_2.
             if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, nullptr,
-                                  0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr, maxbits)))
+                                  0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr, maxbits, perm, (int32_t)rows)))
                 return st;
             P.Q = qbuf;
             ProfSpan span(s, MODE_CLEN * 3 + o.storage);
@@ -410,19 +426,22 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                     P.out = buf[j % 3];
                     P.outf = nullptr;
                 }
-                double by = step_bytes(n, G.nnz, unit, batched, w, o.storage, MODE_CLEN, j + 2 <= p, 1, j == 0);
+                double by =
+                    step_bytes(n, G.nnz, unit, batched, w, o.storage, MODE_CLEN, j + 2 <= p, 1, j == 0, n_slabs);
                 if ((st = launch_step(sh, MODE_CLEN, P, s, by))) return st;
                 span.add(by);
             }
             if (p == 0) {
                 // Y = a_0 R: b_0 computed by the pack as a_p R with p = 0, widen to fp32
                 if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, yacc,
-                                      n * ld, 1, coef, 1, 0, G.gid, nullptr, nullptr, maxbits)))
+                                      rows * ld, 1, coef, 1, 0, G.gid, nullptr, nullptr, maxbits, perm,
+                                      (int32_t)rows)))
                     return st;
             }
         }
         if (ncy) {
-            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0, maxbits);
+            unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0, maxbits, perm,
+                                                        (int32_t)rows);
             if ((st = check_launch("unpack_kernel"))) return st;
         }
     }
@@ -439,6 +458,29 @@ static sf_status check_common(const sf_graph *g, double lam_max, int p, const vo
     SF_ARG(r_dtype == SF_F32 || r_dtype == SF_BF16, "R dtype must be SF_F32 or SF_BF16");
     SF_ARG(g->device == current_device(), "graph lives on device %d, current device is %d", g->device,
            current_device());
+    return SF_OK;
+}
+
+// Checks the per-order dot products before they become moments: every
+// D_j = <T_j,T_j> and E_j = <T_j,T_{j-1}> finite, and D_j <= 16 D_0. Since
+// |T_j(x)| <= 1 on [-1, 1], ||T_j R||^2 <= ||R||^2 when lam_max bounds the
+// spectrum, while eigencomponents beyond it grow like cosh(j acosh x).
+// dots[2j] = D_j for j <= p, dots[2j + 1] = E_j for 1 <= j < p, and E_p is
+// `e_last` (so that a caller may hold the first 2p + 1 values in place).
+sf_status check_moment_dots(const double *dots, double e_last, int p, double lam_max) {
+    for (int j = 0; j <= p; ++j) {
+        const double d = dots[2 * j];
+        const double e = (j == 0) ? 0.0 : (j == p ? e_last : dots[2 * j + 1]);
+        if (!isfinite(d) || !isfinite(e)) {
+            set_error("non-finite moment at order %d (non-finite input or lam_max below the spectrum)", j);
+            return SF_ERR_NUMERIC;
+        }
+        if (d > 16.0 * dots[0] + 1e-300) {
+            set_error("||T_%d R||^2 = %g exceeds 16 ||R||^2 = %g: lam_max %g is below the Laplacian's spectrum", j, d,
+                      16.0 * dots[0], lam_max);
+            return SF_ERR_NUMERIC;
+        }
+    }
     return SF_OK;
 }
 
@@ -525,19 +567,7 @@ SF_API sf_status sf_cheb_moments(const sf_graph *g, double lam_max, const void *
     SF_CHECK_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * 2 * (p + 1), cudaMemcpyDeviceToHost, s));
     SF_CHECK_CUDA(cudaStreamSynchronize(s));
     if ((st = sf_device_check(stream))) return st;
-    // |T_j(x)| <= 1 on [-1, 1], so ||T_j R||^2 <= ||R||^2 when lam_max bounds the
-    // spectrum; eigencomponents beyond it grow like cosh(j acosh x)
-    for (int j = 0; j <= p; ++j) {
-        if (!isfinite(hd[2 * j]) || !isfinite(hd[2 * j + 1])) {
-            set_error("non-finite moment at order %d (non-finite input or lam_max below the spectrum)", j);
-            return SF_ERR_NUMERIC;
-        }
-        if (hd[2 * j] > 16.0 * hd[0] + 1e-300) {
-            set_error("||T_%d R||^2 = %g exceeds 16 ||R||^2 = %g: lam_max %g is below the Laplacian's spectrum", j,
-                      hd[2 * j], 16.0 * hd[0], lam_max);
-            return SF_ERR_NUMERIC;
-        }
-    }
+    if ((st = check_moment_dots(hd.data(), hd[2 * p + 1], p, lam_max))) return st;
     moments_from_dots(hd.data(), p, moments);
     return SF_OK;
 }

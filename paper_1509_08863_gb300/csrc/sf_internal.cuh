@@ -130,13 +130,20 @@ constexpr int kCsrPad = 4;
 namespace sf {
 constexpr int kSliceRows = 8;  // rows per slice
 }  // namespace sf
+// The sweeps keep their signal blocks in slice-row order: block row t holds
+// original row perm[t], so the rows of a tile are consecutive in memory, and
+// `ridx` holds the column indices renumbered into that order. Rows t >= n are
+// padding; row `rows` of every block is the zero row that padding entries
+// gather.
 struct SellMatrix {
     int32_t n = 0;
     int32_t n_slices = 0;
+    int32_t rows = 0;         // n_slices * 8: a block has rows + 1 rows
     int64_t entries = 0;
     int32_t *sptr = nullptr;  // [n_slices + 1 + pad] entry offset of each slice
     int32_t *perm = nullptr;  // [n_slices * 8] original row of each slice row, -1 for none
-    int32_t *idx = nullptr;   // [entries + pad] column index, n for padding
+    int32_t *idx = nullptr;   // [entries + pad] column index (original numbering), n for padding
+    int32_t *ridx = nullptr;  // [entries + pad] column index as a slice row, `rows` for padding
     float *val = nullptr;     // [entries + pad] weight, 0 for padding; nullptr for unit weights
     int32_t *iperm = nullptr; // [n] slice row (slice * 8 + position) of each original row
     bool built = false;

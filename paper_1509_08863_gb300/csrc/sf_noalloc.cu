@@ -1,21 +1,21 @@
 // Allocation-free variant of the moment sweep (sf_cheb_moments).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// eigenvalue-count moments: code that runs while a stream is being captured
-// into a CUDA graph (a stream-ordered allocation would become a node of the
-// graph), frameworks that own the whole device memory through their own
-// caching allocator and forbid foreign allocations, and latency-bound loops
-// that cannot afford an allocator call. This entry point serves them: all of
-// its working memory is carved from one fixed array that lives in this
-// library's device image, so the call itself never allocates.
+// eigenvalue-count moments: frameworks that hand the whole device memory to
+// their own caching allocator and forbid foreign allocations, and
+// latency-bound loops for which an allocator call (which may block, or, for
+// cudaFree, synchronise the device) costs too much. This entry point serves
+// them: all of its working memory is carved from one fixed array that lives
+// in this library's device image, so the call itself never allocates.
 //
 // The array is a file-scope __device__ object of kNoAllocBytes; every GPU
-// that loads the library keeps it until the process exits. Its address is
-// looked up once per device (cudaGetSymbolAddress) by the first call made on
-// that device. All calls share the array and it keeps the previous call's
-// contents, so everything that must start at zero is cleared on each call,
-// and calls whose GPU work overlaps (different streams without ordering)
-// race on it.
+// that loads the library keeps it until the process exits. Host code cannot
+// use its name as a device address: the address is looked up once per device
+// (cudaGetSymbolAddress, with that device current) by the first call made on
+// that device, so that first call should come before any stream capture. All
+// calls share the array and it keeps the previous call's contents, so
+// everything that must start at zero is cleared on each call, and calls whose
+// GPU work overlaps (different streams without ordering) race on it.
 #include <math.h>
 
 #include "sf_step.cuh"
@@ -45,6 +45,22 @@ static sf_status noalloc_base(unsigned char **out) {
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Working memory of one call: 3 slab blocks of rows + 1 rows, d~ per slice
+// row, partial sums, the per-order dot products and the sweep's block counter.
+struct NoAllocPlan {
+    size_t blk, dtil, part, dots, done, total;
+};
+static NoAllocPlan noalloc_plan(int64_t rows, int ld, int grid, int pack_grid, int p) {
+    NoAllocPlan q;
+    q.blk = round256((size_t)(rows + 1) * ld * sizeof(float));
+    q.dtil = round256((size_t)rows * sizeof(float));
+    q.part = round256((size_t)(2 * grid + 2 * pack_grid + 2) * sizeof(double));
+    q.dots = round256((size_t)2 * (p + 1) * sizeof(double));
+    q.done = 256;
+    q.total = 3 * q.blk + q.dtil + q.part + q.dots + q.done;
+    return q;
+}
+
 }  // namespace sf
 
 using namespace sf;
@@ -70,41 +86,49 @@ extern "C" SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double la
     if (st) return st;
 
     const int64_t n = g->n;
-    const int ld = auto_slab_cols(n, n_sig, SF_F32, 32ll << 20);
+    const int64_t rows = g->sell.rows;
+    const int32_t *perm = g->sell.perm;
     const bool weighted = !g->unit_weights;
-    SweepShape sh;
-    if ((st = make_shape(SF_F32, ld, 0, 0, MODE_MOM, weighted, &sh, 0))) return st;
-    SF_ARG((int64_t)(n + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets");
     const int pack_grid = 2 * sm_count();
-
-    // carve the array: 3 slab blocks of n + 1 rows, d~, partial sums, dot products
-    const size_t blk_bytes = round256((size_t)(n + 1) * ld * sizeof(float));
-    const size_t dtil_bytes = round256((size_t)n * sizeof(float));
-    const size_t part_bytes = round256((size_t)(2 * sh.grid + 2 * pack_grid + 2) * sizeof(double));
-    const size_t dots_bytes = round256((size_t)2 * (p + 1) * sizeof(double));
-    const size_t need = 3 * blk_bytes + dtil_bytes + part_bytes + dots_bytes;
-    SF_ARG(need <= kNoAllocBytes,
+    // The slab sf_cheb_moments picks by default, halved (down to 8 columns) until
+    // the working memory fits the array: the size limit is monotone in N.
+    int ld = auto_slab_cols(n, n_sig, SF_F32, 32ll << 20);
+    SweepShape sh;
+    NoAllocPlan plan;
+    for (;;) {
+        if ((st = make_shape(SF_F32, ld, 0, 0, MODE_MOM, weighted, &sh, 0))) return st;
+        plan = noalloc_plan(rows, ld, sh.grid, pack_grid, p);
+        if (plan.total <= kNoAllocBytes || ld <= 8) break;
+        ld /= 2;
+    }
+    SF_ARG(plan.total <= kNoAllocBytes,
            "this graph and signal count need %zu bytes of working memory; the allocation-free variant has %zu",
-           need, kNoAllocBytes);
+           plan.total, kNoAllocBytes);
+    SF_ARG((int64_t)(rows + 1) * ld < (1ll << 32), "graph too large for 32-bit slab offsets");
+
     float *buf[3];
     size_t off = 0;
     for (int k = 0; k < 3; ++k) {
         buf[k] = reinterpret_cast<float *>(base + off);
-        off += blk_bytes;
+        off += plan.blk;
     }
     float *dtil = reinterpret_cast<float *>(base + off);
-    off += dtil_bytes;
+    off += plan.dtil;
     double *part = reinterpret_cast<double *>(base + off);
-    off += part_bytes;
+    off += plan.part;
     double *dots = reinterpret_cast<double *>(base + off);
+    off += plan.dots;
+    uint32_t *done = reinterpret_cast<uint32_t *>(base + off);
 
-    // the array keeps the last call's contents: clear the accumulators and the zero rows
-    SF_CHECK_CUDA(cudaMemsetAsync(dots, 0, dots_bytes, s));
+    // the array keeps the last call's contents: clear the accumulators, the block
+    // counter and the zero rows
+    SF_CHECK_CUDA(cudaMemsetAsync(dots, 0, plan.dots, s));
+    SF_CHECK_CUDA(cudaMemsetAsync(done, 0, sizeof(uint32_t), s));
     for (int k = 0; k < 3; ++k)
-        SF_CHECK_CUDA(cudaMemsetAsync(buf[k] + (size_t)n * ld, 0, (size_t)ld * sizeof(float), s));
-    if (n > 0) {
-        dtil_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->strength, (int32_t)n, 2.0 / lam_max, nullptr,
-                                                                nullptr, dtil, nullptr);
+        SF_CHECK_CUDA(cudaMemsetAsync(buf[k] + (size_t)rows * ld, 0, (size_t)ld * sizeof(float), s));
+    if (rows > 0) {
+        dtil_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(g->strength, (int32_t)rows, 2.0 / lam_max,
+                                                                   nullptr, nullptr, dtil, nullptr, perm, nullptr);
         if ((st = check_launch("dtil_kernel"))) return st;
     }
     int32_t *status = device_status();
@@ -112,23 +136,22 @@ extern "C" SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double la
     for (int c0 = 0; c0 < n_sig; c0 += ld) {
         const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;
         pack_kernel<float><<<pack_grid, 256, 0, s>>>(R, SF_F32, (int32_t)n, n_sig, c0, w, ld, buf[0], nullptr, 0, 0,
-                                                     nullptr, 1, 0, nullptr, nullptr, part);
+                                                     nullptr, 1, 0, nullptr, nullptr, part, nullptr, perm,
+                                                     (int32_t)rows);
         if ((st = check_launch("pack_kernel"))) return st;
         pair_sum_kernel<<<1, 256, 0, s>>>(part, pack_grid, 1, dots);
         if ((st = check_launch("pair_sum_kernel"))) return st;
         StepParams P = {};
         P.n = (int32_t)n;
-        P.rowptr = g->rowptr;
-        P.colidx = g->colidx;
-        P.val = weighted ? g->val : nullptr;
         P.sell_ptr = g->sell.sptr;
-        P.sell_perm = g->sell.perm;
-        P.sell_idx = g->sell.idx;
+        P.sell_idx = g->sell.ridx;
         P.sell_val = g->sell.val;
         P.dtil = dtil;
         P.wscale_u = (float)(2.0 / lam_max);
         P.ld = ld;
+        P.flags = kStepFlagsDefault;
         P.part = part;
+        P.done = done;
         P.status = status;
         for (int j = 1; j <= p; ++j) {
             P.X = buf[(j - 1) % 3];
@@ -136,19 +159,20 @@ extern "C" SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double la
             P.out = buf[j % 3];
             P.m = (j == 1) ? 1.0f : 2.0f;
             P.j = j;
+            P.dots = dots + 2 * j;  // the kernel's last block adds <T_j,T_j>, <T_j,T_{j-1}>
             if ((st = launch_step(sh, MODE_MOM, P, s, 0.0))) return st;
-            pair_sum_kernel<<<1, 256, 0, s>>>(part, sh.grid, 2, dots + 2 * j);
-            if ((st = check_launch("pair_sum_kernel"))) return st;
         }
     }
     // dots = [D_0, E_0, D_1, E_1, ..., D_p, E_p] with D_j = <T_j, T_j>, E_j = <T_j, T_{j-1}>;
-    // copy the first 2p + 1 straight into the caller's array and convert in place:
+    // copy the first 2p + 1 straight into the caller's array, check them as
+    // sf_cheb_moments does, and convert in place:
     // mu_0 = D_0, mu_1 = E_1, mu_2j = 2 D_j - mu_0, mu_{2j-1} = 2 E_j - mu_1 (j >= 2)
     double last = 0.0;
     SF_CHECK_CUDA(cudaMemcpyAsync(moments, dots, sizeof(double) * (size_t)(2 * p + 1), cudaMemcpyDeviceToHost, s));
     SF_CHECK_CUDA(cudaMemcpyAsync(&last, dots + 2 * p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     SF_CHECK_CUDA(cudaStreamSynchronize(s));
     if ((st = sf_device_check(stream))) return st;
+    if ((st = check_moment_dots(moments, last, p, lam_max))) return st;
     if (p >= 1) {
         const double mu0 = moments[0];
         const double mu1 = (p == 1) ? last : moments[3];

@@ -72,6 +72,15 @@ __global__ void sell_iperm_kernel(int64_t count, const int32_t *perm, int32_t *i
     if (t < count && perm[t] >= 0) iperm[perm[t]] = (int32_t)t;
 }
 
+// ridx[e] = slice row of idx[e] (padding index n becomes the zero row `rows`)
+__global__ void sell_renumber_kernel(int64_t count, int32_t n, int32_t rows, const int32_t *idx,
+                                     const int32_t *iperm, int32_t *ridx) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const int32_t k = idx[e];
+    ridx[e] = (k >= 0 && k < n) ? iperm[k] : rows;
+}
+
 __global__ void sell_fill_pad_kernel(int32_t *p, int count, int32_t v) {
     if ((int)threadIdx.x < count) p[threadIdx.x] = v;
 }
@@ -81,6 +90,7 @@ void sell_release(SellMatrix *S) {
     cudaFree(S->iperm);
     cudaFree(S->perm);
     cudaFree(S->idx);
+    cudaFree(S->ridx);
     cudaFree(S->val);
     *S = SellMatrix();
 }
@@ -137,8 +147,19 @@ sf_status sell_build(SellMatrix *S, int32_t n, const int32_t *rowptr, const int3
     if (cudaMalloc(&S->iperm, sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) return oom();
     sell_iperm_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(threads, S->perm, S->iperm);
     if ((st = check_launch("sell_iperm_kernel"))) return st;
+    // the sweeps' copy of the indices, renumbered into slice-row order
+    const int32_t rows = n_slices * kSliceRows;
+    if (cudaMalloc(&S->ridx, sizeof(int32_t) * (size_t)(total + kCsrPad)) != cudaSuccess) return oom();
+    if (total > 0) {
+        sell_renumber_kernel<<<(unsigned)(((int64_t)total + 255) / 256), 256, 0, s>>>(total, n, rows, S->idx,
+                                                                                        S->iperm, S->ridx);
+        if ((st = check_launch("sell_renumber_kernel"))) return st;
+    }
+    sell_fill_pad_kernel<<<1, 32, 0, s>>>(S->ridx + total, kCsrPad, rows);
+    if ((st = check_launch("sell_fill_pad_kernel"))) return st;
     S->n = n;
     S->n_slices = n_slices;
+    S->rows = rows;
     S->entries = total;
     S->built = true;
     return SF_OK;

@@ -30,6 +30,10 @@ struct VT<float> {
     __device__ __forceinline__ static void st(float *p, const float (&x)[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
     }
+    __device__ __forceinline__ static void st_cs(float *p, const float (&x)[4]) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(x[0], x[1], x[2], x[3]));
+    }
+    __device__ __forceinline__ static void add_raw_mixed(float (&acc)[4], float4 x) { add_raw(acc, x); }
     // value as it is stored (identity for fp32)
     __device__ __forceinline__ static float rt(float x) { return x; }
     __device__ __forceinline__ static float cvt(float x) { return x; }
@@ -75,12 +79,18 @@ struct VT<__nv_bfloat16> {
     __device__ __forceinline__ static void ld_stream(const __nv_bfloat16 *p, float (&x)[8]) {
         unpack(__ldcs(reinterpret_cast<const uint4 *>(p)), x);
     }
-    __device__ __forceinline__ static void st(__nv_bfloat16 *p, const float (&x)[8]) {
+    __device__ __forceinline__ static uint4 pack(const float (&x)[8]) {
         uint4 v;
         __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
-        *reinterpret_cast<uint4 *>(p) = v;
+        return v;
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, const float (&x)[8]) {
+        *reinterpret_cast<uint4 *>(p) = pack(x);
+    }
+    __device__ __forceinline__ static void st_cs(__nv_bfloat16 *p, const float (&x)[8]) {
+        __stcs(reinterpret_cast<uint4 *>(p), pack(x));
     }
     __device__ __forceinline__ static float rt(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
     __device__ __forceinline__ static __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
@@ -119,17 +129,37 @@ struct VT<__nv_bfloat16> {
         fma_pair(acc[4], acc[5], w, x.z);
         fma_pair(acc[6], acc[7], w, x.w);
     }
+    // acc += x with the mixed-precision add (FP32 + BF16 operand, one rounding):
+    // the same sums as widening first, without the shift and mask
+    __device__ __forceinline__ static void add_pair_mixed(float &a0, float &a1, uint32_t h) {
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tadd.rn.f32.bf16 %0, lo, %0;\n\t"
+            "add.rn.f32.bf16 %1, hi, %1;\n}"
+            : "+f"(a0), "+f"(a1)
+            : "r"(h));
+    }
+    __device__ __forceinline__ static void add_raw_mixed(float (&acc)[8], raw_t x) {
+        add_pair_mixed(acc[0], acc[1], x.x);
+        add_pair_mixed(acc[2], acc[3], x.y);
+        add_pair_mixed(acc[4], acc[5], x.z);
+        add_pair_mixed(acc[6], acc[7], x.w);
+    }
 };
 
 template <>
 struct VT<__half> {
     static constexpr int V = 8;
-    __device__ __forceinline__ static void st(__half *p, const float (&x)[8]) {
+    __device__ __forceinline__ static uint4 pack(const float (&x)[8]) {
         uint4 v;
         __half2 *h = reinterpret_cast<__half2 *>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(x[2 * k], x[2 * k + 1]);
-        *reinterpret_cast<uint4 *>(p) = v;
+        return v;
+    }
+    __device__ __forceinline__ static void st(__half *p, const float (&x)[8]) {
+        *reinterpret_cast<uint4 *>(p) = pack(x);
+    }
+    __device__ __forceinline__ static void st_cs(__half *p, const float (&x)[8]) {
+        __stcs(reinterpret_cast<uint4 *>(p), pack(x));
     }
     __device__ __forceinline__ static float rt(float x) { return __half2float(__float2half_rn(x)); }
     __device__ __forceinline__ static __half cvt(float x) { return __float2half_rn(x); }
@@ -169,6 +199,18 @@ struct VT<__half> {
             acc[2 * k + 1] = fmaf(w, v.y, acc[2 * k + 1]);
         }
     }
+    __device__ __forceinline__ static void add_pair_mixed(float &a0, float &a1, uint32_t h) {
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tadd.rn.f32.f16 %0, lo, %0;\n\t"
+            "add.rn.f32.f16 %1, hi, %1;\n}"
+            : "+f"(a0), "+f"(a1)
+            : "r"(h));
+    }
+    __device__ __forceinline__ static void add_raw_mixed(float (&acc)[8], raw_t x) {
+        add_pair_mixed(acc[0], acc[1], x.x);
+        add_pair_mixed(acc[2], acc[3], x.y);
+        add_pair_mixed(acc[4], acc[5], x.z);
+        add_pair_mixed(acc[6], acc[7], x.w);
+    }
 };
 
 // Power-of-two scale that brings the largest magnitude of a block into
@@ -205,20 +247,29 @@ static __global__ void absmax_kernel(const void *R, int r_dtype, int32_t n, int3
 // ------------------------------------------------------------ parameters
 enum StepMode { MODE_FWD = 0, MODE_MOM = 1, MODE_CLEN = 2 };
 
+// StepParams::flags (uniform per launch)
+enum StepFlags {
+    STEP_IDX_EVICT_FIRST = 1,  // index copies marked evict-first in L2 (read once per launch)
+    STEP_OUT_STREAMING = 2,    // T_j / b_j stores marked streaming (evict-first) instead of write-back
+    STEP_MIXED_ADD = 8,        // unit weights, 16-bit blocks: FP32 += 16-bit operand in one instruction
+};
+constexpr int32_t kStepFlagsDefault = STEP_IDX_EVICT_FIRST | STEP_OUT_STREAMING | STEP_MIXED_ADD;
+
+// Every block (X, Z, Q, out, outf, Y) is row-major in slice-row order
+// (sliced-ELL position t = slice * 8 + position, see SellMatrix); rows
+// t < n hold graph rows, row `rows` of a gathered block is zero. The per-row
+// tables (dtil, wscale, gid) are in the same order.
 struct StepParams {
-    int32_t n;
-    const int32_t *rowptr;
-    const int32_t *colidx;
-    const float *val;       // nullptr: all weights 1
+    int32_t n;                 // graph rows: slice rows t >= n are padding and skipped
     const int32_t *sell_ptr;   // sliced-ELL: entry offset of each slice
-    const int32_t *sell_perm;  // original row of each slice row (-1: none)
-    const int32_t *sell_idx;   // column indices (n for padding)
+    const int32_t *sell_idx;   // column indices as slice rows (padding: the zero row)
     const float *sell_val;     // weights (0 for padding), nullptr for unit weights
     const float *dtil;      // per row: 2 s_i / lam - 1
     const float *wscale;    // per row 2 / lam (batches) or nullptr
     float wscale_u;         // uniform 2 / lam
     const int32_t *gid;     // per-row graph id (batches) or nullptr
     int32_t ld;             // slab row stride in elements
+    int32_t flags;          // StepFlags
     const void *X;          // T_{j-1} (forward) or b_{j+1} (Clenshaw): gathered
     const void *Z;          // T_{j-2} or b_{j+2}: subtracted (nullptr: none)
     const void *Q;          // Clenshaw addend block (packed R or G)
@@ -226,8 +277,8 @@ struct StepParams {
     float *outf;            // Clenshaw final: fp32 output instead of `out`
     float m;                // 2 (general order) or 1 (first order / final Clenshaw step)
     // forward accumulation
-    float *Y;               // n_cut accumulators [n_cut][N][ld] fp32
-    int64_t ystride;        // N * ld
+    float *Y;               // n_cut accumulators [n_cut][rows][ld] fp32
+    int64_t ystride;        // rows * ld
     int32_t n_cut;
     const float *coef;      // [graphs][n_cut][coef_ld]
     int32_t coef_ld;        // p + 1
@@ -266,6 +317,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// The same with an L2 cache policy (createpolicy) attached to the reads.
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -278,21 +343,39 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// 32-byte FP32 accesses (one 256-bit load or store per lane): with rows in
+// slice order, the lanes of a warp cover consecutive 128-byte lines.
+__device__ __forceinline__ void ld8_stream(const float *p, float (&x)[8]) {
+    asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p));
+}
+__device__ __forceinline__ void st8_stream(float *p, const float (&x)[8]) {
+    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x[0]), "f"(x[1]),
+                 "f"(x[2]), "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+                 : "memory");
+}
+
 // ------------------------------------------------------------ the sweep
 // The sweep reads the graph in a sliced-ELL layout (built from the CSR by
 // the library, see sell_build): rows are sorted by length inside windows of
 // 32768 rows and grouped into slices of 8 rows padded to a common length (a
-// multiple of 4); padding entries point at the zero row n appended to every
+// multiple of 4); padding entries point at the zero row appended to every
 // gathered block. Each slice is stored row after row, so a row's indices
-// are 16-byte aligned and read four at a time.
+// are 16-byte aligned and read four at a time. The signal blocks are kept in
+// the same (slice-row) order, so the rows a tile streams (its own rows of
+// T_{j-1}, T_{j-2}, the output and the accumulators) are consecutive.
 //
 // A CTA walks tiles of consecutive slices (tile k of the CTA is
-// blockIdx.x + k * gridDim.x). A tile's slice offsets, row permutation and
-// index (and weight) range are staged in shared memory by TMA bulk copies
-// into one of two buffers; the copy for tile k + 1 is issued before tile k is
-// processed. Tiles whose entries do not fit read the indices from global
-// memory. Lane group g (LPR lanes, 16 bytes each) owns tile rows g, g + G,
-// ...; the groups of one warp share a slice, so their trip counts match.
+// blockIdx.x + k * gridDim.x). A tile's slice offsets and index (and weight)
+// range are staged in shared memory by TMA bulk copies into one of NST
+// stages. Warps run through the tiles independently: each waits for its
+// stage's copy on the stage's mbarrier, and the last warp done with a stage
+// (a shared counter) issues the copy of the stage's next tile, so no block
+// barrier separates tiles. Tiles whose entries do not fit read the indices
+// from global memory. Lane group g (LPR lanes, 16 bytes each) owns tile rows
+// g, g + G, ...; the groups of one warp share a slice, so their trip counts
+// match.
 
 template <int LPR>
 struct TileCfg {
@@ -300,11 +383,16 @@ struct TileCfg {
     static constexpr int slices = rows / kSliceRows;
     static constexpr int sp_ints = slices + 4;  // slices + 1 offsets, rounded up to 16 bytes
     static constexpr int entries = rows * 44;  // 4 blocks of 256 threads fit a 100 KB shared carveout
-    // per buffer: slice offsets, permutation, indices, weights (weighted graphs only)
+    static constexpr int stages = 2;
+    static constexpr int header = 128;  // mbarriers, per-stage entry base / fits / consumer count / copies issued
+    // per stage: slice offsets of the tile and of the stage's next tile (the
+    // refill's entry range), indices, weights (weighted graphs only)
     __host__ __device__ static constexpr int buf_bytes(bool weighted) {
-        return (sp_ints + rows) * 4 + entries * 4 * (weighted ? 2 : 1);
+        return 2 * sp_ints * 4 + entries * 4 * (weighted ? 2 : 1);
     }
-    __host__ __device__ static constexpr int smem_bytes(bool weighted) { return 64 + 2 * buf_bytes(weighted); }
+    __host__ __device__ static constexpr int smem_bytes(bool weighted) {
+        return header + stages * buf_bytes(weighted);
+    }
 };
 
 __device__ __forceinline__ int4 lds_int4(const int32_t *p) {
@@ -334,7 +422,7 @@ __device__ __forceinline__ float4 ld_val4(const float *p) {
 }
 
 // acc += sum over the row's ls entries of w_e * X[idx_e] (this lane's 16 bytes)
-template <typename TS, bool W, bool SMEM>
+template <typename TS, bool W, bool SMEM, bool MIX>
 __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rstride, const int32_t *ip,
                                            const float *wp, int32_t ls, float (&acc)[VT<TS>::V]) {
     using V = VT<TS>;
@@ -350,6 +438,9 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
             const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
             for (int u = 0; u < 8; ++u) V::fma_raw(acc, w[u], x[u]);
+        } else if constexpr (MIX) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) V::add_raw_mixed(acc, x[u]);
         } else {
 #pragma unroll
             for (int u = 0; u < 8; ++u) V::add_raw(acc, x[u]);
@@ -366,6 +457,9 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
             const float w[4] = {wa.x, wa.y, wa.z, wa.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) V::fma_raw(acc, w[u], x[u]);
+        } else if constexpr (MIX) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) V::add_raw_mixed(acc, x[u]);
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) V::add_raw(acc, x[u]);
@@ -374,10 +468,11 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
 }
 
 // One row of one order: acc = sum_e w_e X[idx_e] over the row's ls entries,
-// then t = m (d_i X_i - (2/lam) acc) - Z_i [+ a_j Q_i], stored; the forward
-// mode adds a_cj t to each accumulator, the moment mode sums t.t and t.X_i.
+// then v = m (d_t X_t - (2/lam) acc) - Z_t [+ a_j Q_t], stored; the forward
+// mode adds a_cj v to each accumulator, the moment mode sums v.v and v.X_t.
+// t is the row's slice-row position, which is also its row in every block.
 template <typename TS, int MODE, bool W, bool SMEM>
-__device__ __forceinline__ void sweep_row(const StepParams &P, int32_t i, int q, const int32_t *ip, const float *wp,
+__device__ __forceinline__ void sweep_row(const StepParams &P, int32_t t, int q, const int32_t *ip, const float *wp,
                                           int32_t ls, double &mtt, double &mtx) {
     using V = VT<TS>;
     constexpr int VEC = V::V;
@@ -386,56 +481,66 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t i, int q,
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
     TS *__restrict__ out = static_cast<TS *>(P.out);
     const int32_t ld = P.ld;
-    const int64_t ro = (int64_t)i * ld + q * VEC;
+    const int64_t ro = (int64_t)t * ld + q * VEC;
     // epilogue operands first (kept packed): their latency overlaps the gathers
     const typename V::raw_t xi_r = V::ld_raw(X + ro);
     const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
     typename V::raw_t q_r = V::zero_raw();
     if (MODE == MODE_CLEN) q_r = V::ld_raw_stream(Qb + ro);
-    const float d = __ldcs(P.dtil + i);
-    const float sc = P.wscale ? __ldcs(P.wscale + i) : P.wscale_u;
-    const int g = P.gid ? __ldcs(P.gid + i) : 0;
+    const float d = __ldcs(P.dtil + t);
+    const float sc = P.wscale ? __ldcs(P.wscale + t) : P.wscale_u;
+    const int g = P.gid ? __ldcs(P.gid + t) : 0;
 
     float acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-    gather_row<TS, W, SMEM>(X + q * VEC, ld, ip, wp, ls, acc);
+    if (!W && VEC == 8 && (P.flags & STEP_MIXED_ADD)) gather_row<TS, W, SMEM, true>(X + q * VEC, ld, ip, wp, ls, acc);
+    else gather_row<TS, W, SMEM, false>(X + q * VEC, ld, ip, wp, ls, acc);
 
-    float t[VEC], xi[VEC];
+    float tv[VEC], xi[VEC];
     {
         float z[VEC];
         V::to_float(xi_r, xi);
         V::to_float(z_r, z);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) t[v] = P.m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
+        for (int v = 0; v < VEC; ++v) tv[v] = P.m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
     }
     if (MODE == MODE_CLEN) {
         const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
         float qv[VEC];
         V::to_float(q_r, qv);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) t[v] = fmaf(alpha, qv[v], t[v]);
+        for (int v = 0; v < VEC; ++v) tv[v] = fmaf(alpha, qv[v], tv[v]);
     }
     if (MODE == MODE_CLEN && P.outf) {
         float *o = P.outf + ro;
-#pragma unroll
-        for (int v = 0; v < VEC; v += 4)
-            __stcs(reinterpret_cast<float4 *>(o + v), make_float4(t[v], t[v + 1], t[v + 2], t[v + 3]));
+        if constexpr (VEC == 8) {
+            st8_stream(o, tv);
+        } else {
+            __stcs(reinterpret_cast<float4 *>(o), make_float4(tv[0], tv[1], tv[2], tv[3]));
+        }
+    } else if (P.flags & STEP_OUT_STREAMING) {
+        V::st_cs(out + ro, tv);
     } else {
-        V::st(out + ro, t);
+        V::st(out + ro, tv);
     }
     if (MODE == MODE_FWD) {
         for (int c = 0; c < P.n_cut; ++c) {
             const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + P.j);
             float *y = P.Y + c * P.ystride + ro;
+            if constexpr (VEC == 8) {
+                float yy[8];
+                ld8_stream(y, yy);
 #pragma unroll
-            for (int v = 0; v < VEC; v += 4) {
-                float4 yy = __ldcs(reinterpret_cast<const float4 *>(y + v));
-                yy.x = fmaf(a, t[v], yy.x);
-                yy.y = fmaf(a, t[v + 1], yy.y);
-                yy.z = fmaf(a, t[v + 2], yy.z);
-                yy.w = fmaf(a, t[v + 3], yy.w);
-                __stcs(reinterpret_cast<float4 *>(y + v), yy);
+                for (int v = 0; v < 8; ++v) yy[v] = fmaf(a, tv[v], yy[v]);
+                st8_stream(y, yy);
+            } else {
+                float4 yy = __ldcs(reinterpret_cast<const float4 *>(y));
+                yy.x = fmaf(a, tv[0], yy.x);
+                yy.y = fmaf(a, tv[1], yy.y);
+                yy.z = fmaf(a, tv[2], yy.z);
+                yy.w = fmaf(a, tv[3], yy.w);
+                __stcs(reinterpret_cast<float4 *>(y), yy);
             }
         }
     }
@@ -443,7 +548,7 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t i, int q,
         float tt = 0.f, tx = 0.f;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-            const float ts = V::rt(t[v]);  // the value the next order reads
+            const float ts = V::rt(tv[v]);  // the value the next order reads
             tt = fmaf(ts, ts, tt);
             tx = fmaf(ts, xi[v], tx);
         }
@@ -513,91 +618,123 @@ __device__ __forceinline__ void block_moments(const StepParams &P, double mtt, d
 template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
     using C = TileCfg<LPR>;
+    constexpr int NST = C::stages;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [2]
-    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 16);  // [2][2]: entry base, fits
-    unsigned char *s_buf0 = smem_raw + 64;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [NST] copy landed
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 32);  // [NST][2]: entry base, fits
+    int32_t *s_cnt = s_meta + 2 * NST;                              // [NST] warps done with the stage's tile
+    int32_t *s_iss = s_cnt + NST;                                   // [NST] copies issued into the stage
+    unsigned char *s_buf0 = smem_raw + C::header;
     constexpr int buf_bytes = C::buf_bytes(W);
+    static_assert(32 + 4 * NST * 4 <= C::header, "stage header");
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int q = tid % LPR, grp = tid / LPR;
     const int ngrp = blockDim.x / LPR;
+    const int nwarps = blockDim.x >> 5;
     const int n_tiles = (P.n + C::rows - 1) / C::rows;
     double mtt = 0.0, mtx = 0.0;
 
-    // thread 0: stage tile `tile` into buffer `b`
-    auto issue = [&](int tile, int b) {
+    // one thread: stage tile `tile` (entries [e0, e1)) into stage b
+    auto issue = [&](int tile, int b, int32_t e0, int32_t e1) {
         unsigned char *base = s_buf0 + b * buf_bytes;
         int32_t *sp = reinterpret_cast<int32_t *>(base);
-        int32_t *pm = sp + C::sp_ints;
-        int32_t *ix = pm + C::rows;
+        int32_t *spn = sp + C::sp_ints;
+        int32_t *ix = spn + C::sp_ints;
         float *wv = reinterpret_cast<float *>(ix + C::entries);
         const int32_t s0 = tile * C::slices;
-        const int32_t e0 = P.sell_ptr[s0], e1 = P.sell_ptr[s0 + C::slices];
+        const int next = tile + NST * (int)gridDim.x;  // the stage's tile after this one
         const int32_t cnt = e1 - e0;  // multiple of 32
         const bool fits = cnt <= C::entries;
-        const uint32_t bytes = (C::sp_ints + C::rows) * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
+        const uint32_t bytes = C::sp_ints * 4 * (next < n_tiles ? 2u : 1u) +
+                               (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
         s_meta[2 * b] = e0;
         s_meta[2 * b + 1] = fits ? 1 : 0;
+        s_iss[b] += 1;
         fence_proxy_async();
         mbar_arrive_expect_tx(&s_bar[b], bytes);
         bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
-        bulk_g2s(pm, P.sell_perm + (int64_t)s0 * kSliceRows, C::rows * 4, &s_bar[b]);
+        if (next < n_tiles) bulk_g2s(spn, P.sell_ptr + (int64_t)next * C::slices, C::sp_ints * 4, &s_bar[b]);
         if (fits && cnt > 0) {
-            bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
-            if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
+            if (P.flags & STEP_IDX_EVICT_FIRST) {
+                const uint64_t pol = l2_policy_evict_first();
+                bulk_g2s_hint(ix, P.sell_idx + e0, cnt * 4, &s_bar[b], pol);
+                if (W) bulk_g2s_hint(wv, P.sell_val + e0, cnt * 4, &s_bar[b], pol);
+            } else {
+                bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
+                if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
+            }
         }
     };
 
     if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+        for (int b = 0; b < NST; ++b) {
+            mbar_init(&s_bar[b], 1);
+            s_cnt[b] = 0;
+            s_iss[b] = 0;
+        }
         fence_mbar_init();
-        if ((int)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+        for (int b = 0; b < NST; ++b) {
+            const int tile = blockIdx.x + b * gridDim.x;
+            if (tile < n_tiles) issue(tile, b, P.sell_ptr[tile * C::slices], P.sell_ptr[(tile + 1) * C::slices]);
+        }
     }
     __syncthreads();
     for (int k = 0;; ++k) {
         const int tile = blockIdx.x + k * gridDim.x;
         if (tile >= n_tiles) break;
-        const int b = k & 1;
-        // buffer b^1 was released by the barrier that ended the previous tile
-        if (tid == 0 && tile + (int)gridDim.x < n_tiles) issue(tile + gridDim.x, b ^ 1);
-        const bool landed = mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
-        if (__syncthreads_or(!landed)) {
-            if (tid == 0) atomicOr(P.status, 1);
-            // one more bounded chance for copies still in flight before leaving
-            mbar_wait_bounded(&s_bar[b], (uint32_t)(k >> 1) & 1u);
-            if (tile + (int)gridDim.x < n_tiles) mbar_wait_bounded(&s_bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u);
-            return;
+        const int b = k % NST;
+        const uint32_t par = (uint32_t)(k / NST) & 1u;
+        if (!mbar_wait_bounded(&s_bar[b], par)) {
+            if (lane == 0) atomicOr(P.status, 1);
+            break;  // the other warps give up on their own waits; copies in flight are awaited below
         }
         const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
-        const int32_t *s_pm = s_sp + C::sp_ints;
-        const int32_t *s_ix = s_pm + C::rows;
+        const int32_t *s_ix = s_sp + 2 * C::sp_ints;
         const float *s_wv = reinterpret_cast<const float *>(s_ix + C::entries);
         const int32_t e0 = s_meta[2 * b];
         const bool fits = s_meta[2 * b + 1] != 0;
 
         for (int tr = grp; tr < C::rows; tr += ngrp) {
-            const int32_t i = s_pm[tr];
-            if (i < 0) continue;
+            const int32_t t = tile * C::rows + tr;
+            if (t >= P.n) continue;  // padding rows of the last tile
             const int sl = tr / kSliceRows, pos = tr % kSliceRows;
             const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
             const int32_t eo = so - e0 + pos * ls;  // offset of the row's first entry in the tile
-            if (fits) sweep_row<TS, MODE, W, true>(P, i, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
-            else sweep_row<TS, MODE, W, false>(P, i, q, P.sell_idx + e0 + eo, W ? P.sell_val + e0 + eo : nullptr,
+            if (fits) sweep_row<TS, MODE, W, true>(P, t, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
+            else sweep_row<TS, MODE, W, false>(P, t, q, P.sell_idx + e0 + eo, W ? P.sell_val + e0 + eo : nullptr,
                                                ls, mtt, mtx);
         }
-        __syncthreads();  // buffer b fully consumed before it is refilled
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();  // this warp's reads of the stage come before its release
+            if (atomicAdd(&s_cnt[b], 1) == nwarps - 1) {
+                // the last warp done with the stage refills it with the stage's next tile,
+                // whose entry range came with this tile's copy
+                __threadfence_block();  // every warp's reads of the stage come before the refill
+                s_cnt[b] = 0;
+                const int next = tile + NST * (int)gridDim.x;
+                if (next < n_tiles) {
+                    const int32_t *spn = s_sp + C::sp_ints;
+                    issue(next, b, spn[0], spn[C::slices]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // after a wait gave up, copies may still be in flight: wait (bounded) for the last one of each stage
+        for (int b = 0; b < NST; ++b)
+            if (s_iss[b] > 0) mbar_wait_bounded(&s_bar[b], (uint32_t)(s_iss[b] - 1) & 1u);
     }
     if (MODE == MODE_MOM) block_moments(P, mtt, mtx);
 }
 
 // Direct variant: no staging and no block barriers. Warp c of the grid walks
 // chunks of 32 / LPR consecutive slice rows (chunk c, c + W, ... for W warps
-// in the grid); each lane group reads its row's slice offsets, original row
-// and indices straight from global memory (16-byte vector loads, broadcast
-// within the group). With no shared memory the whole L1 holds gathers in
-// flight.
+// in the grid); each lane group reads its row's slice offsets and indices
+// straight from global memory (16-byte vector loads, broadcast within the
+// group). With no shared memory the whole L1 holds gathers in flight.
 template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepParams P) {
     constexpr int RPW = 32 / LPR;
@@ -608,37 +745,41 @@ __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepPara
     double mtt = 0.0, mtx = 0.0;
     for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += warps) {
         const int64_t t = c * RPW + g;
-        const int32_t i = (t < P.n) ? __ldg(P.sell_perm + t) : -1;
-        if (i < 0) continue;
+        if (t >= P.n) continue;
         const int32_t sl = (int32_t)(t / kSliceRows), pos = (int32_t)(t % kSliceRows);
         const int32_t so = __ldg(P.sell_ptr + sl);
         const int32_t ls = (__ldg(P.sell_ptr + sl + 1) - so) / kSliceRows;
         const int64_t eo = (int64_t)so + (int64_t)pos * ls;
-        sweep_row<TS, MODE, W, false>(P, i, q, P.sell_idx + eo, W ? P.sell_val + eo : nullptr, ls, mtt, mtx);
+        sweep_row<TS, MODE, W, false>(P, (int32_t)t, q, P.sell_idx + eo, W ? P.sell_val + eo : nullptr, ls, mtt,
+                                      mtx);
     }
     if (MODE == MODE_MOM) block_moments(P, mtt, mtx);
 }
 
 // ------------------------------------------------------------ pack / unpack
-// T0 = R slab converted to the storage type (zero padded to ld columns).
-// Optionally: Y_c = a_c0 * T0 (forward), b_p = a_p * T0 (Clenshaw start,
-// written to `bstart`), and per-block partial sum of T0.T0 (moments).
+// Blocks hold rows in slice-row order: block row t is graph row perm[t]
+// (perm[t] < 0 and t >= rows: zero rows). pack_kernel fills rows
+// [0, rows] of T0 with the R slab converted to the storage type (zero padded
+// to ld columns). Optionally: Y_c = a_c0 * T0 (forward, rows [0, rows)),
+// b_p = a_p * T0 (Clenshaw start, written to `bstart`), and per-block
+// partial sum of T0.T0 (moments). gid is indexed by graph row.
 template <typename TS>
 __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0, int32_t w,
                             int32_t ld, TS *T0, float *Y, int64_t ystride, int32_t n_cut, const float *coef,
                             int32_t coef_ld, int32_t jcoef, const int32_t *gid, TS *bstart, double *part,
-                            const uint32_t *maxbits = nullptr) {
+                            const uint32_t *maxbits, const int32_t *perm, int32_t rows) {
     __shared__ double red[256];
-    const int64_t total = (int64_t)n * ld;
+    const int64_t total = (int64_t)(rows + 1) * ld;
     const float scale = block_scale(maxbits);
     double acc = 0.0;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / ld;
-        const int32_t c = (int32_t)(idx - i * ld);
+        const int64_t t = idx / ld;
+        const int32_t c = (int32_t)(idx - t * ld);
+        const int32_t i = (t < rows) ? perm[t] : -1;
         float x = 0.f;
-        if (c < w) {
-            const int64_t src = i * n_sig + c0 + c;
+        if (i >= 0 && c < w) {
+            const int64_t src = (int64_t)i * n_sig + c0 + c;
             x = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
                                      : static_cast<const float *>(R)[src];
             x *= scale;
@@ -646,7 +787,8 @@ __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig
         T0[idx] = VT<TS>::cvt(x);
         const float xr = VT<TS>::rt(x);
         acc += (double)xr * (double)xr;
-        const int g = gid ? gid[i] : 0;
+        if (t == rows) continue;  // the zero row of the gathered block
+        const int g = (gid && i >= 0) ? gid[i] : 0;
         if (Y) {
             for (int k = 0; k < n_cut; ++k) {
                 const float a = coef[((int64_t)g * n_cut + k) * coef_ld + jcoef];
@@ -669,30 +811,44 @@ __global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig
     }
 }
 
-// Y_out[c][i][c0 + col] = Yslab[c][i][col] for col < w.
+// Y_out[c][perm[t]][c0 + col] = Yslab[c][t][col] for col < w and graph rows t.
 static __global__ void unpack_kernel(const float *Yslab, int32_t n, int32_t ld, int32_t w, int32_t n_cut,
-                              float *Y, int32_t n_sig, int32_t c0, const uint32_t *maxbits = nullptr) {
-    const int64_t total = (int64_t)n_cut * n * w;
+                                     float *Y, int32_t n_sig, int32_t c0, const uint32_t *maxbits,
+                                     const int32_t *perm, int32_t rows) {
+    const int64_t total = (int64_t)n_cut * rows * w;
     const float inv = 1.0f / block_scale(maxbits);  // exact: a power of two
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t cc = idx / ((int64_t)n * w);
-        const int64_t rem = idx - cc * n * w;
-        const int64_t i = rem / w;
-        const int32_t col = (int32_t)(rem - i * w);
-        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * n + i) * ld + col) * inv;
+        const int64_t cc = idx / ((int64_t)rows * w);
+        const int64_t rem = idx - cc * rows * w;
+        const int64_t t = rem / w;
+        const int32_t col = (int32_t)(rem - t * w);
+        const int32_t i = perm[t];
+        if (i < 0) continue;
+        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * rows + t) * ld + col) * inv;
     }
 }
 
-// d~_i = 2 s_i / lam - 1 (uniform lam) or per-graph lam (batches); also
-// writes 2 / lam per row for batches.
-static __global__ void dtil_kernel(const double *s, int32_t n, double two_over_lam, const int32_t *gid,
-                            const double *two_over_lam_g, float *dtil, float *wscale) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double tl = gid ? two_over_lam_g[gid[i]] : two_over_lam;
-    dtil[i] = (float)(tl * s[i] - 1.0);
-    if (wscale) wscale[i] = (float)tl;
+// Per slice row t (graph row i = perm[t]): d~_t = 2 s_i / lam - 1 (uniform lam)
+// or with the graph's own lam (batches), 2 / lam per row for batches, and the
+// graph id per row; padding rows get zeros.
+static __global__ void dtil_kernel(const double *s, int32_t rows, double two_over_lam, const int32_t *gid,
+                                   const double *two_over_lam_g, float *dtil, float *wscale, const int32_t *perm,
+                                   int32_t *gid_t) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows) return;
+    const int32_t i = perm[t];
+    if (i < 0) {
+        dtil[t] = 0.0f;
+        if (wscale) wscale[t] = 0.0f;
+        if (gid_t) gid_t[t] = 0;
+        return;
+    }
+    const int g = gid ? gid[i] : 0;
+    double tl = gid ? two_over_lam_g[g] : two_over_lam;
+    dtil[t] = (float)(tl * s[i] - 1.0);
+    if (wscale) wscale[t] = (float)tl;
+    if (gid_t) gid_t[t] = g;
 }
 
 // Sum the [count][2] partials in a fixed order and add into out[0..1].
@@ -743,5 +899,9 @@ StepFn direct_step_fn(int storage, int lpr, int mode, bool weighted);
 // Device error word written by the sweep kernels (bounded waits).
 int32_t *device_status();
 sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaStream_t s, double bytes);
+// StepParams::flags for a call's options (sf_opts.sweep_hints).
+int32_t step_flags(const sf_opts &o);
+// Finiteness and growth checks of a moment sweep's dot products (SF_ERR_NUMERIC).
+sf_status check_moment_dots(const double *dots, double e_last, int p, double lam_max);
 
 }  // namespace sf
