@@ -32,7 +32,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_LIB_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_omp_lib = None
 _lock = threading.Lock()
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -40,23 +42,39 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 
 
+def _compile(path: str, extra, force: bool) -> str:
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math"] + extra + ["-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, path)
+    return path
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so next to it (gcc, -O2, IEEE semantics)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-        )
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, [], force)
 
 
-def _load():
-    global _lib
+def build_parallel(force: bool = False) -> str:
+    """The same source built with -fopenmp (liboracle_omp.so): the filter's
+    loops over rows and elements run on all the threads OpenMP is given, each
+    element computed exactly as in the plain build. For the timed CPU
+    baseline only."""
+    return _compile(_OMP_LIB_PATH, ["-fopenmp"], force)
+
+
+def _load(parallel: bool = False):
+    global _lib, _omp_lib
     with _lock:
-        if _lib is not None:
+        if parallel and _omp_lib is not None:
+            return _omp_lib
+        if not parallel and _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(build_parallel() if parallel else build())
+        lib.oracle_threads.restype = C.c_int32
+        lib.oracle_threads.argtypes = []
         lib.oracle_csr_build.restype = C.c_int64
         lib.oracle_csr_build.argtypes = [C.c_int32, C.c_int64, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p]
         lib.oracle_strength.restype = None
@@ -105,7 +123,10 @@ def _load():
         lib.oracle_cheb_filter_backward.restype = None
         lib.oracle_cheb_filter_backward.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32,
                                                     _f64p, C.c_int64, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
-        _lib = lib
+        if parallel:
+            _omp_lib = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -204,8 +225,9 @@ def cheb_coeffs(lam_max: float, cutoffs, p: int, jackson: bool = True) -> np.nda
     return out
 
 
-def cheb_filter(g: CSR, lam_max: float, coeffs, R) -> np.ndarray:
-    """Y_q = sum_j a_qj T_j(Lt) R for every coefficient row q (3)/(6)/(11)."""
+def cheb_filter(g: CSR, lam_max: float, coeffs, R, parallel: bool = False) -> np.ndarray:
+    """Y_q = sum_j a_qj T_j(Lt) R for every coefficient row q (3)/(6)/(11).
+    parallel=True runs the same loops from the OpenMP build (identical results)."""
     a = np.atleast_2d(_c(coeffs, np.float64))
     a = _c(a, np.float64)
     R = _c(R, np.float64)
@@ -213,11 +235,16 @@ def cheb_filter(g: CSR, lam_max: float, coeffs, R) -> np.ndarray:
     n, n_sig = R.shape
     Y = np.zeros((n_cut, n, n_sig))
     if g.diag is None:
-        _load().oracle_cheb_filter(g.n, g.rowptr, g.colidx, g.val, lam_max, n_cut, p1 - 1, a, n_sig, R, Y)
+        _load(parallel).oracle_cheb_filter(g.n, g.rowptr, g.colidx, g.val, lam_max, n_cut, p1 - 1, a, n_sig, R, Y)
     else:
         _load().oracle_cheb_filter_diag(g.n, g.rowptr, g.colidx, g.val, _c(g.diag, np.float64), lam_max, n_cut,
                                         p1 - 1, a, n_sig, R, Y)
     return Y
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the filter's loops use in the plain (1) or the OpenMP build."""
+    return int(_load(parallel).oracle_threads())
 
 
 def normalize(g: CSR) -> CSR:

@@ -7,7 +7,11 @@
  * header or helper with it.
  *
  * Every function is a direct loop over the definition it cites, in double
- * precision, single-threaded, with no blocking, fusion or reordering.
+ * precision, single-threaded, with no blocking, fusion or reordering. A
+ * second build of this file (with -fopenmp) spreads the filter's loops over
+ * rows and elements on several threads, for the timed CPU baseline only;
+ * each row or element is still computed by the same operations in the same
+ * order, so both builds return identical results.
  * Citations name the paper's sections and equations (Tremblay, Puy, Borgnat,
  * Gribonval, Vandergheynst, "Accelerated spectral clustering using graph
  * filtering of random signals"); equations are numbered in order of
@@ -38,6 +42,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <string.h>
 
 #ifndef M_PI
@@ -277,6 +284,7 @@ void oracle_cheb_coeffs(double lam_max, double lc, int32_t p, int32_t jackson, d
  * L = S - W; the diagonal S is the row sums of W unless `diag` gives it. */
 static void lt_apply_d(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                        const double *diag, double lam_max, int64_t c, const double *X, double *Y) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
         if (diag) s = diag[i];
@@ -318,13 +326,25 @@ void oracle_cheb_filter(int32_t n, const int32_t *rowptr, const int32_t *colidx,
     for (int32_t j = 1; j <= p; ++j) {
         lt_apply(n, rowptr, colidx, val, lam_max, n_sig, Tm1, Tj); /* Lt T_{j-1} */
         if (j >= 2) {
+#pragma omp parallel for schedule(static)
             for (int64_t t = 0; t < sz; ++t) Tj[t] = 2.0 * Tj[t] - Tm2[t];
         }
-        for (int32_t q = 0; q < n_cut; ++q)
+        for (int32_t q = 0; q < n_cut; ++q) {
+#pragma omp parallel for schedule(static)
             for (int64_t t = 0; t < sz; ++t) Y[q * sz + t] += a[q * (p + 1) + j] * Tj[t];
+        }
         double *tmp = Tm2; Tm2 = Tm1; Tm1 = Tj; Tj = tmp;
     }
     free(Tm2); free(Tm1); free(Tj);
+}
+
+/* Threads the filter's loops run on: 1 in the plain build. */
+int32_t oracle_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /*

@@ -703,3 +703,23 @@ def test_cheb_order_matches_chebval_search(oracle_mod):
     # first overshoot, delta = 0.05 is out of reach; the damped series (a positive kernel) never overshoots
     assert oracle_mod.cheb_order(0.4, 0.05, 1e-4, False, 300) == -1
     assert oracle_mod.cheb_order(0.4, 0.05, 0.01, True, 2000) > 0
+
+
+def test_parallel_build_equals_plain_build(oracle_mod):
+    """The OpenMP build of the oracle (the timed CPU baseline on all host cores)
+    computes every element with the same operations in the same order as the
+    plain build: identical filter outputs, for any number of threads."""
+    from helpers import random_graph
+
+    oracle_mod.build_parallel()
+    n = 700
+    src, dst, w = random_graph(n, 6000, seed=21)
+    g = oracle_mod.csr_build(n, src, dst, w)
+    lam = 2.0 * float(oracle_mod.strength(g).max())
+    a = oracle_mod.cheb_coeffs(lam, [0.1 * lam, 0.3 * lam], 17, True)
+    R = np.random.default_rng(3).standard_normal((n, 5))
+    Y1 = oracle_mod.cheb_filter(g, lam, a, R)
+    Yp = oracle_mod.cheb_filter(g, lam, a, R, parallel=True)
+    assert oracle_mod.threads() == 1
+    assert oracle_mod.threads(parallel=True) >= 1
+    np.testing.assert_array_equal(Y1, Yp)
