@@ -50,3 +50,10 @@ def cliques_edges(k, m, seed=0):
                 src.append(base + i)
                 dst.append(base + j)
     return np.array(src, np.int32), np.array(dst, np.int32)
+
+
+def oracle_lambda_hat(oracle_mod, go, iters=60, seed=0):
+    """lam_hat for a comparison, computed by the oracle (its Lanczos from a seeded
+    start, then the reading of §4.1 step 1); both sides are given this value."""
+    v0 = np.random.default_rng(seed).standard_normal(go.n)
+    return oracle_mod.lambda_hat(oracle_mod.lanczos_max(go, iters, v0), oracle_mod.strength(go))

@@ -128,8 +128,9 @@ def test_kmeans_small_and_degenerate(sf, oracle_mod):
 
 def test_kmeans_on_filtered_features(sf, oracle_mod):
     """The path end to end on a small SBM: filter at the k-th eigenvalue,
-    row-normalised features, k-means: labels equal the oracle's on the GPU's
-    own features, and the communities are recovered."""
+    row-normalised features, k-means: the communities are recovered, and on
+    the oracle's own features (cast to FP32) the GPU's labels equal the
+    oracle's."""
     from paper_1509_08863_gb300 import synth
 
     n, k, eta, p = 1200, 6, 24, 60
@@ -145,8 +146,20 @@ def test_kmeans_on_filtered_features(sf, oracle_mod):
     Y = sf.cheb_filter(g, lh, a, R)[0]
     Fe = sf.features(Y, True).cpu().numpy()
     C0 = farthest_point_init(Fe, k, seed=2)
-    lab, _ = check_same(sf, oracle_mod, Fe, C0, 30, sf.KMEANS_AUTO)
-    # purity of the recovered communities (labels up to permutation)
+    lab, _, _, _ = sf.kmeans(torch.as_tensor(Fe, device=dev), torch.as_tensor(C0, device=dev), 30)
+    lab = lab.cpu().numpy()
+    # purity of the communities the GPU path recovers (labels up to permutation)
     truth = gr.labels
     purity = sum(np.bincount(truth[lab == c]).max() for c in range(k) if (lab == c).any()) / n
     assert purity > 0.9, purity
+    # labels equal the oracle's on the same FP32 features: the oracle's own (FP64 filter at its own
+    # lam_hat and the cutoff between the k-th and (k+1)-th eigenvalues of the dense Laplacian)
+    from helpers import dense_laplacian, dense_w, oracle_lambda_hat
+
+    go = oracle_mod.csr_build(n, gr.src, gr.dst, gr.w)
+    lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, gr.src, gr.dst)))
+    lh_o = oracle_lambda_hat(oracle_mod, go, 60, seed=3)
+    a_o = oracle_mod.cheb_coeffs(lh_o, 0.5 * (lam[k - 1] + lam[k]), p, True)
+    Fo = oracle_mod.features(oracle_mod.cheb_filter(go, lh_o, a_o, synth.gaussian_block(n, eta, 21))[0], True)
+    Fo32 = np.ascontiguousarray(Fo.astype(np.float32))
+    check_same(sf, oracle_mod, Fo32, farthest_point_init(Fo32, k, seed=2), 30, sf.KMEANS_AUTO)

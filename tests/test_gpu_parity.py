@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-from helpers import cliques_edges, dense_laplacian, dense_w, random_graph  # noqa: E402
+from helpers import cliques_edges, dense_laplacian, dense_w, oracle_lambda_hat, random_graph  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -149,7 +149,7 @@ def _setup_config1(sf, oracle_mod):
     from paper_1509_08863_gb300 import synth
 
     R = synth.gaussian_block(gr.n, 14, seed=2001)
-    th, lh = sf.lambda_max_estimate(g, 60, None, seed=1)
+    lh = oracle_lambda_hat(oracle_mod, go, 60, seed=1)
     return gr, g, go, lam, R, lh
 
 
@@ -170,7 +170,7 @@ def test_filter_multi_cutoff_ragged(sf, oracle_mod):
     n, n_sig, p = 3001, 37, 23
     src, dst, w = random_graph(n, 20000, 9)
     g, go = build_both(sf, oracle_mod, n, src, dst, w)
-    _, lh = sf.lambda_max_estimate(g, 40, None, seed=2)
+    lh = oracle_lambda_hat(oracle_mod, go, 40, seed=2)
     R = np.random.default_rng(4).standard_normal((n, n_sig)) / math.sqrt(n_sig)
     a = oracle_mod.cheb_coeffs(lh, [0.05 * lh, 0.2 * lh, 0.7 * lh], p, True)
     Yo = oracle_mod.cheb_filter(go, lh, a, R)
@@ -206,8 +206,9 @@ def test_filter_empty_rows_and_bf16_input(sf, oracle_mod):
     g, go = build_both(sf, oracle_mod, n, src, dst, w)
     lh = 2.0 * oracle_mod.strength(go).max()
     R = np.random.default_rng(3).standard_normal((n, 16)).astype(np.float32)
-    Rb = torch.as_tensor(R, device="cuda").to(torch.bfloat16)
-    Rr = Rb.float().cpu().numpy().astype(np.float64)  # the values the GPU sees
+    Rb_h = torch.as_tensor(R).to(torch.bfloat16)  # rounded on the host
+    Rr = Rb_h.double().numpy()  # the values the GPU sees
+    Rb = Rb_h.to("cuda")
     a = oracle_mod.cheb_coeffs(lh, 0.3 * lh, 30, True)
     Yo = oracle_mod.cheb_filter(go, lh, a, Rr)[0]
     Y = sf.cheb_filter(g, lh, a, Rb)[0].cpu().numpy()
@@ -218,7 +219,7 @@ def test_filter_empty_rows_and_bf16_input(sf, oracle_mod):
     np.testing.assert_allclose(Y[iso], fac * Rr[iso], rtol=1e-5, atol=1e-6)
 
 
-def test_filter_bf16_storage_error(sf, oracle_mod):
+def test_filter_bf16_storage_error(sf, oracle_mod, record_property):
     """BF16 blocks, FP32 accumulation: error against the oracle fed the
     BF16-rounded R stays below the bound 2^-8 * sqrt(p) (one BF16 rounding
     per order, accumulated as independent errors), and against the FP64 R."""
@@ -226,16 +227,17 @@ def test_filter_bf16_storage_error(sf, oracle_mod):
     p = 50
     a = oracle_mod.cheb_coeffs(lh, 0.5 * (lam[9] + lam[10]), p, True)
     Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
-    Rr = Rt.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    Rr = torch.as_tensor(R.astype(np.float32)).to(torch.bfloat16).double().numpy()  # rounded on the host
     Yo_r = oracle_mod.cheb_filter(go, lh, a, Rr)[0]
     for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
         Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.BF16, algo=algo))[0].cpu().numpy()
         err = rel(Y, Yo_r)
+        record_property(f"err_bf16_{algo}", err)
         assert err <= 2.0 ** -8 * math.sqrt(p), (algo, err)
 
 
 @pytest.mark.parametrize("algo", ["forward", "clenshaw"])
-def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo):
+def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo, record_property):
     """FP16 blocks (10-bit mantissa) with the per-slab power-of-two prescale:
     error against the FP64 oracle below 2^-11 * p (one FP16 rounding per
     order, growing at most linearly through the recurrence); inputs far
@@ -250,6 +252,7 @@ def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo):
         Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.F16, algo=A))[0].cpu().numpy() / scale
         assert np.all(np.isfinite(Y))
         err = rel(Y, Yo)
+        record_property(f"err_f16_{algo}_scale{scale:g}", err)
         assert err <= 2.0 ** -11 * p, (scale, err)
 
 
@@ -263,7 +266,7 @@ def test_direct_kernel_matches_tiled_and_oracle(sf, oracle_mod, weighted):
     n, n_sig, p = 3001, 37, 23
     src, dst, w = random_graph(n, 20000, 31)
     g, go = build_both(sf, oracle_mod, n, src, dst, w if weighted else None)
-    _, lh = sf.lambda_max_estimate(g, 40, None, seed=2)
+    lh = oracle_lambda_hat(oracle_mod, go, 40, seed=2)
     R = np.random.default_rng(5).standard_normal((n, n_sig)) / math.sqrt(n_sig)
     a = oracle_mod.cheb_coeffs(lh, [0.05 * lh, 0.3 * lh], p, True)
     Yo = oracle_mod.cheb_filter(go, lh, a, R)
@@ -304,7 +307,7 @@ def test_moments_and_counts_match_oracle(sf, oracle_mod):
     sizes = synth.community_sizes_uniform(n, 8, 100, 400, seed=1)
     gr = synth.sbm_edges(n, sizes, 12.0, 0.1, seed=2)
     g, go = build_both(sf, oracle_mod, n, gr.src, gr.dst, gr.w)
-    _, lh = sf.lambda_max_estimate(g, 50, None, seed=1)
+    lh = oracle_lambda_hat(oracle_mod, go, 50, seed=1)
     R = synth.gaussian_block(n, eta, seed=3)
     Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
     mu = sf.cheb_moments(g, lh, Rt, p)
@@ -341,7 +344,7 @@ def test_dichotomy_finds_gap_on_cliques(sf, oracle_mod):
     n = k * m
     g, go = build_both(sf, oracle_mod, n, src, dst)
     lam = np.linalg.eigvalsh(dense_laplacian(dense_w(n, src, dst)))
-    _, lh = sf.lambda_max_estimate(g, n, None, seed=1)
+    lh = oracle_lambda_hat(oracle_mod, go, n, seed=1)
     R = np.random.default_rng(1).standard_normal((n, eta)) / math.sqrt(eta)
     Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
     mu = sf.cheb_moments(g, lh, Rt, p)
@@ -449,7 +452,7 @@ def test_batched_matches_oracle_and_single_launches(sf, oracle_mod):
         g, go = build_both(sf, oracle_mod, gr.n, gr.src, gr.dst, gr.w)
         gs.append(g)
         gos.append(go)
-        lams.append(sf.lambda_max_estimate(g, 40, None, seed=1)[1])
+        lams.append(oracle_lambda_hat(oracle_mod, go, 40, seed=1))
     b = sf.batch_build(gs)
     n_tot, nnz_tot, ng, offs = b.info()
     assert ng == 5 and n_tot == sum(gr.n for gr in graphs)
@@ -581,8 +584,9 @@ def test_normalized_laplacian_matches_oracle(sf, oracle_mod):
     rp, ci, va, st = gn.csr()
     np.testing.assert_array_equal(va.cpu().numpy(), gno.val.astype(np.float32))
     np.testing.assert_array_equal(st.cpu().numpy(), gno.diag)
-    th, lh = sf.lambda_max_estimate(gn, 80, None, seed=4)
-    assert th <= 2.0 + 1e-9 and lh <= 2.0
+    th, lh_gpu = sf.lambda_max_estimate(gn, 80, None, seed=4)
+    assert th <= 2.0 + 1e-9 and lh_gpu <= 2.0
+    lh = 2.0  # the normalised spectrum lies in [0, 2]: the closed-form bound, given to both sides
     R = np.random.default_rng(8).standard_normal((n, n_sig)) / math.sqrt(n_sig)
     Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
     a = oracle_mod.cheb_coeffs(lh, [0.2 * lh, 0.5 * lh], p, True)
