@@ -7,7 +7,13 @@ and the GPU result's matching columns must agree.
 Bounds (relative Frobenius error per column against FP64):
 * FP32 blocks: 1e-5 (p / 50)^1.5 (FP32 rounding growing through the
   recurrence; 1e-5 is the stated bound at p = 50);
-* BF16 blocks, forward recurrence: 2^-8 sqrt(p); FP16: 2^-11 p.
+* BF16 blocks, forward recurrence, 1M-node SBM at p = 200: 2^-8 sqrt(p) =
+  0.055, 1.7-1.9x the errors measured on GB300 (0.030 and 0.032 on the two
+  columns);
+* BF16 blocks on the batch: the smallest graph against the stored-block
+  rounding model of helpers.stored_block_error_model (its dense spectrum);
+  the two large graphs, whose spectra are out of reach, against 5e-3, 2x the
+  errors measured on GB300 (2.5e-3).
 """
 import math
 
@@ -121,10 +127,22 @@ def test_batch256_sampled_graphs(sf, oracle_mod, record_property):
                        for i in range(ng)])
     Y = sf.cheb_filter_batched(b, lams, coeffs, torch.as_tensor(R, dtype=torch.float32, device=dev),
                                sf.Opts(storage=sf.BF16))
+    from helpers import dense_laplacian, dense_w, stored_block_error_model
+
     sizes = np.diff(offs)
-    for i in (int(np.argmin(sizes)), int(np.argmax(sizes)), 128):
+    smallest = int(np.argmin(sizes))
+    for i in (smallest, int(np.argmax(sizes)), 128):
         sl = slice(int(offs[i]), int(offs[i + 1]))
         Yo = oracle_mod.cheb_filter(gos[i], lams[i], coeffs[i], np.ascontiguousarray(R[sl][:, :2]))[0]
+        if i == smallest:
+            gr = graphs[i]
+            lam = np.linalg.eigvalsh(dense_laplacian(dense_w(gr.n, gr.src, gr.dst)))
+            # the GPU rounds R to BF16 as it packs it: the model includes that rounding
+            bound = stored_block_error_model(2.0 * lam / lams[i] - 1.0, coeffs[i], 2.0 ** -8, "forward", True)
+        else:
+            bound = 5e-3
         for c in range(2):
-            record_property(f"err_bf16_graph{i}_col{c}", rel(Y[sl][:, c].cpu().numpy(), Yo[:, c]))
-            assert rel(Y[sl][:, c].cpu().numpy(), Yo[:, c]) <= 2.0 ** -8 * math.sqrt(p)
+            err = rel(Y[sl][:, c].cpu().numpy(), Yo[:, c])
+            record_property(f"err_bf16_graph{i}_col{c}", err)
+            record_property(f"bound_bf16_graph{i}", bound)
+            assert err <= bound, (i, c, err, bound)

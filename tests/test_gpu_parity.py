@@ -20,7 +20,8 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-from helpers import cliques_edges, dense_laplacian, dense_w, oracle_lambda_hat, random_graph  # noqa: E402
+from helpers import (cliques_edges, dense_laplacian, dense_w, oracle_lambda_hat, random_graph,  # noqa: E402
+                     stored_block_error_model)
 
 
 @pytest.fixture(scope="module")
@@ -220,40 +221,48 @@ def test_filter_empty_rows_and_bf16_input(sf, oracle_mod):
 
 
 def test_filter_bf16_storage_error(sf, oracle_mod, record_property):
-    """BF16 blocks, FP32 accumulation: error against the oracle fed the
-    BF16-rounded R stays below the bound 2^-8 * sqrt(p) (one BF16 rounding
-    per order, accumulated as independent errors), and against the FP64 R."""
+    """BF16 blocks, FP32 accumulation: the error against the oracle fed the
+    BF16-rounded R stays below the stored-block rounding model of
+    helpers.stored_block_error_model (u = 2^-8, from the graph's dense
+    spectrum); measured on GB300 at about half of it (forward 4.4e-3 against
+    7.8e-3, Clenshaw 7.9e-3 against 1.6e-2)."""
     gr, g, go, lam, R, lh = _setup_config1(sf, oracle_mod)
     p = 50
     a = oracle_mod.cheb_coeffs(lh, 0.5 * (lam[9] + lam[10]), p, True)
     Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
     Rr = torch.as_tensor(R.astype(np.float32)).to(torch.bfloat16).double().numpy()  # rounded on the host
     Yo_r = oracle_mod.cheb_filter(go, lh, a, Rr)[0]
-    for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+    for algo, name in ((sf.ALGO_FORWARD, "forward"), (sf.ALGO_CLENSHAW, "clenshaw")):
         Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.BF16, algo=algo))[0].cpu().numpy()
         err = rel(Y, Yo_r)
-        record_property(f"err_bf16_{algo}", err)
-        assert err <= 2.0 ** -8 * math.sqrt(p), (algo, err)
+        bound = stored_block_error_model(2.0 * lam / lh - 1.0, a[0], 2.0 ** -8, name, False)
+        record_property(f"err_bf16_{name}", err)
+        record_property(f"bound_bf16_{name}", bound)
+        assert err <= bound, (name, err, bound)
 
 
 @pytest.mark.parametrize("algo", ["forward", "clenshaw"])
 def test_filter_f16_storage_error_and_range(sf, oracle_mod, algo, record_property):
-    """FP16 blocks (10-bit mantissa) with the per-slab power-of-two prescale:
-    error against the FP64 oracle below 2^-11 * p (one FP16 rounding per
-    order, growing at most linearly through the recurrence); inputs far
-    outside the FP16 range give the same relative error."""
+    """FP16 blocks (11-bit significand) with the per-slab power-of-two
+    prescale: the error against the FP64 oracle (R rounded too) stays below
+    the stored-block rounding model (u = 2^-11, input rounding included);
+    measured at about half of it (forward 5.8e-4 against 1.0e-3, Clenshaw
+    1.0e-3 against 2.1e-3); inputs far outside the FP16 range give the same
+    relative error."""
     gr, g, go, lam, R, lh = _setup_config1(sf, oracle_mod)
     p = 50
     a = oracle_mod.cheb_coeffs(lh, 0.5 * (lam[9] + lam[10]), p, True)
     Yo = oracle_mod.cheb_filter(go, lh, a, R)[0]
     A = sf.ALGO_FORWARD if algo == "forward" else sf.ALGO_CLENSHAW
+    bound = stored_block_error_model(2.0 * lam / lh - 1.0, a[0], 2.0 ** -11, algo, True)
+    record_property(f"bound_f16_{algo}", bound)
     for scale in (1.0, 1e5, 1e-6):
         Rt = torch.as_tensor(R * scale, dtype=torch.float32, device="cuda")
         Y = sf.cheb_filter(g, lh, a, Rt, sf.Opts(storage=sf.F16, algo=A))[0].cpu().numpy() / scale
         assert np.all(np.isfinite(Y))
         err = rel(Y, Yo)
         record_property(f"err_f16_{algo}_scale{scale:g}", err)
-        assert err <= 2.0 ** -11 * p, (scale, err)
+        assert err <= bound, (scale, err, bound)
 
 
 @pytest.mark.parametrize("weighted", [False, True])
