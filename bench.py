@@ -80,6 +80,8 @@ def parse():
                          "kmeans|batched, STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
+    ap.add_argument("--case-graphs", type=int, default=0,
+                    help="kernel case 'batched': only the first K graphs of the batch (0: all), for small captures")
     ap.add_argument("--filter-algo", default="auto", choices=["auto", "clenshaw", "forward"],
                     help="algorithm of the filter sweep (auto: Clenshaw for FP32 blocks, forward otherwise); "
                          "the moment sweep is always the forward recurrence")
@@ -138,6 +140,8 @@ def run_kernel_case(args, wl):
         from paper_1509_08863_gb300 import synth
 
         graphs, _ = synth.batched_sbm(wl["n_graphs"], wl["graph_seed"])
+        if args.case_graphs > 0:
+            graphs = graphs[:args.case_graphs]
         gs = [sf.csr_build(gr.n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
               for gr in graphs]
         lams = np.array([sf.lambda_max_estimate(g, 40, None, seed=11)[1] for g in gs])
