@@ -1022,6 +1022,24 @@ def run_batch(args, wl):
         sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Yg, opts)
     ms_g, launches_g, _, _ = _clock_timed(cg.replay, args.steps, 1, sf)
     graph_same = bool(torch.equal(Yg, Y))
+    # the same batch in one persistent launch for all orders (per-graph arrival counters), eager and captured
+    opts_p = sf.Opts(storage=st, slab_cols=tuned.slab_cols, block_warps=tuned.block_warps,
+                     carveout_pct=tuned.carveout_pct, sweep_kernel=sf.SWEEP_PERSISTENT)
+    Yp = torch.empty_like(Y)
+
+    def persistent():
+        sf.cheb_filter_batched(b, np.array(lams), coeffs, R, opts_p, out=Yp)
+
+    ms_p, launches_p, variants_p, _ = _clock_timed(persistent, args.steps, 1, sf)
+    Ypg = torch.empty_like(Y)
+    with torch.cuda.stream(side):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Ypg, opts_p)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    cgp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cgp):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Ypg, opts_p)
+    ms_pg, _, _, _ = _clock_timed(cgp.replay, args.steps, 1, sf)
     ms_s, launches_s, _, _ = _clock_timed(sequential, max(1, args.steps // 2), 1, sf)
     nnz_sum = sum(g.nnz for g in gs)
     updates = (nnz_sum + n_tot) * eta * p
@@ -1046,6 +1064,12 @@ def run_batch(args, wl):
         "batched_equals_sequential": bool(same),
         "cuda_graph": {"value": updates / (ms_g * 1e-3), "ms_per_step": ms_g, "equals_eager": graph_same,
                        "note": "one capture of the device-table batched call, replayed"},
+        "persistent": {"value": updates / (ms_p * 1e-3), "ms_per_step": ms_p, "gpu_launches": launches_p,
+                       "equals_per_order": bool(torch.equal(Yp, Y)),
+                       "cuda_graph_ms_per_step": ms_pg, "cuda_graph_equals": bool(torch.equal(Ypg, Y)),
+                       "roofline_by_variant": _roof_variants(variants_p, args.workload)[1],
+                       "note": "one launch per column slab runs all orders: blocks claim (order, 8-tile chunk) items "
+                               "and wait on per-graph arrival counters"},
     }
     out.update(batch_fp32_and_accuracy(sf, b, gs, lams, coeffs, R, Rs, Y, offs, opts, updates, ms_b, args, graphs,
                                        ks, R_host))

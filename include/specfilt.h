@@ -83,7 +83,9 @@ enum {
 enum {
     SF_SWEEP_AUTO = 0,   /* the staged tiles (SF_SWEEP_TILED) unless sf_autotune chose otherwise */
     SF_SWEEP_TILED = 1,  /* CTA tiles whose indices are staged in shared memory by TMA bulk copies */
-    SF_SWEEP_DIRECT = 2  /* no staging: each warp reads its rows' indices from global memory */
+    SF_SWEEP_DIRECT = 2, /* no staging: each warp reads its rows' indices from global memory */
+    SF_SWEEP_PERSISTENT = 3 /* batches: one persistent launch runs every order (per-graph arrival
+                               counters); single graphs and the moment sweep use the staged tiles */
 };
 
 /*
@@ -378,8 +380,18 @@ SF_API sf_status sf_batch_info(const sf_batch *b, int32_t *n_total, int64_t *nnz
 SF_API void sf_batch_free(sf_batch *b);
 
 /*
- * Filter every graph of the batch with its own lam_max and coefficients in
- * one sweep per order (one kernel launch per order covers all graphs).
+ * Filter every graph of the batch with its own lam_max and coefficients
+ * (the fast filtering of §2.4 on each graph). With opts->sweep_kernel =
+ * SF_SWEEP_PERSISTENT one kernel launch runs all p orders of a column slab:
+ * blocks take (order, tile) items from a queue, and a tile starts an order as
+ * soon as every graph its rows belong to has finished the previous order on
+ * all of its tiles (per-graph arrival counters), so small graphs do not wait
+ * for the batch's largest graph at every order. Every such wait is bounded:
+ * one that runs out sets the device status word (sf_device_check then returns
+ * SF_ERR_TIMEOUT) and makes the launch's other waits give up. Otherwise
+ * (SF_SWEEP_AUTO, SF_SWEEP_TILED, SF_SWEEP_DIRECT) one launch per order
+ * covers all graphs. Both forms compute every row with the same operations:
+ * their outputs are bit-identical.
  *   lam_max  host double[n_graphs]
  *   coeffs   host double[n_graphs][p + 1]
  *   R, Y     device blocks of sum(N_g) rows x n_sig, graph g's rows at its
@@ -389,6 +401,18 @@ SF_API void sf_batch_free(sf_batch *b);
 SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
                                         int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
                                         const sf_opts *opts, void *stream);
+
+/*
+ * sf_cheb_filter_batched with n_cut coefficient rows per graph (several
+ * cutoffs lambda_c per graph, accumulated in one forward sweep; Clenshaw,
+ * when asked for, runs one cutoff at a time).
+ *   coeffs   host double[n_graphs][n_cut][p + 1], 1 <= n_cut <= 64
+ *   Y        device float[n_cut][sum(N_g)][n_sig]
+ * Asynchronous on `stream`.
+ */
+SF_API sf_status sf_cheb_filter_batched_multi(const sf_batch *b, const double *lam_max, const double *coeffs,
+                                              int32_t n_cut, int32_t p, const void *R, int32_t r_dtype,
+                                              int32_t n_sig, float *Y, const sf_opts *opts, void *stream);
 
 /*
  * sf_cheb_moments without any device allocation. The paper has no
@@ -564,6 +588,16 @@ SF_API sf_status sf_stability(const sf_graph *g, double lam_max, int32_t p, cons
  * usable. Asynchronous on `stream`.
  */
 SF_API sf_status sf_selftest_bounded_wait(int32_t polls, void *stream);
+
+/*
+ * Self-test of the persistent batch sweep's failure path (no counterpart in
+ * the paper): one thread waits, with the batch kernel's own wait, for a graph
+ * whose arrival counter nothing increments, gives up after `polls` polls
+ * (1..2^16, 128 ns apart) and sets the device status word and the launch's
+ * abort flag as the batch kernel does; the next sf_device_check returns
+ * SF_ERR_TIMEOUT and clears the word. Nothing faults. Synchronises `stream`.
+ */
+SF_API sf_status sf_selftest_arrival_wait(int32_t polls, void *stream);
 
 /*
  * Measured ceiling of the sweep's gather pattern. A diagnostic with no

@@ -57,7 +57,7 @@ __all__ = [
 
 F32, BF16, F16 = 0, 1, 2
 ALGO_AUTO, ALGO_FORWARD, ALGO_CLENSHAW = 0, 1, 2
-SWEEP_AUTO, SWEEP_TILED, SWEEP_DIRECT = 0, 1, 2
+SWEEP_AUTO, SWEEP_TILED, SWEEP_DIRECT, SWEEP_PERSISTENT = 0, 1, 2, 3
 HINTS_NONE, HINT_IDX_EVICT_FIRST, HINT_OUT_STREAMING, HINT_MIXED_ADD = -1, 1, 2, 8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -152,6 +152,8 @@ def lib():
         "sf_batch_free": (None, [_vp]),
         "sf_cheb_filter_batched": (_i32, [_vp, _dp, _dp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
         "sf_cheb_filter_batched_dev": (_i32, [_vp, _vp, _vp, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts), _vp]),
+        "sf_cheb_filter_batched_multi": (_i32, [_vp, _dp, _dp, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_Opts),
+                                                _vp]),
         "sf_autotune": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(_Opts), _vp, C.POINTER(_Opts)]),
         "sf_profile_begin": (_i32, []),
         "sf_device_check": (_i32, [_vp]),
@@ -165,6 +167,7 @@ def lib():
                                 _dp, _dp]),
         "sf_cheb_order": (_i32, [_f64, _f64, _f64, _i32, _i32, C.POINTER(_i32)]),
         "sf_selftest_bounded_wait": (_i32, [_i32, _vp]),
+        "sf_selftest_arrival_wait": (_i32, [_i32, _vp]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -483,7 +486,8 @@ def batch_build(graphs) -> Batch:
 
 
 def cheb_filter_batched(b: Batch, lam_max, coeffs, R, opts: Opts | None = None, out=None):
-    """Every graph of the batch filtered with its own lam_max and coefficient row, one sweep per order."""
+    """Every graph of the batch filtered with its own lam_max and coefficient row (one launch per order, or one
+    persistent launch for all orders with opts.sweep_kernel = SWEEP_PERSISTENT)."""
     torch = _torch()
     lm, lp = _f64arr(np.ravel(lam_max))
     a, ap = _f64arr(np.atleast_2d(coeffs))
@@ -493,6 +497,24 @@ def cheb_filter_batched(b: Batch, lam_max, coeffs, R, opts: Opts | None = None, 
     o, op = _opts_ptr(opts)
     _check(lib().sf_cheb_filter_batched(b.handle, lp, ap, a.shape[1] - 1, _dev_ptr(R, None, "R"), _rdtype(R), n_sig,
                                         _dev_ptr(out, torch.float32, "Y"), op, _stream()), "sf_cheb_filter_batched")
+    return out
+
+
+def cheb_filter_batched_multi(b: Batch, lam_max, coeffs, R, opts: Opts | None = None, out=None):
+    """Every graph filtered at n_cut cutoffs: coeffs [n_graphs, n_cut, p + 1]; returns [n_cut, N, n_sig]."""
+    torch = _torch()
+    lm, lp = _f64arr(np.ravel(lam_max))
+    a, ap = _f64arr(np.asarray(coeffs, np.float64))
+    if a.ndim != 3:
+        raise ValueError("coeffs must be [n_graphs, n_cut, p + 1]")
+    n, n_sig = R.shape
+    n_cut = a.shape[1]
+    if out is None:
+        out = torch.empty((n_cut, n, n_sig), dtype=torch.float32, device=R.device)
+    o, op = _opts_ptr(opts)
+    _check(lib().sf_cheb_filter_batched_multi(b.handle, lp, ap, n_cut, a.shape[2] - 1, _dev_ptr(R, None, "R"),
+                                              _rdtype(R), n_sig, _dev_ptr(out, torch.float32, "Y"), op, _stream()),
+           "sf_cheb_filter_batched_multi")
     return out
 
 
@@ -597,6 +619,12 @@ def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> flo
     _check(lib().sf_gather_ceiling(int(n_rows), int(row_bytes), int(deg), int(reps), _stream(), C.byref(r)),
            "sf_gather_ceiling")
     return r.value
+
+
+def selftest_arrival_wait(polls: int = 1000):
+    """Make the persistent batch sweep's arrival wait give up (nothing faults); the next device_check raises
+    SF_ERR_TIMEOUT."""
+    _check(lib().sf_selftest_arrival_wait(int(polls), _stream()), "sf_selftest_arrival_wait")
 
 
 def selftest_bounded_wait(polls: int = 1000):

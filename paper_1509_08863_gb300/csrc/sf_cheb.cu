@@ -86,7 +86,7 @@ sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per
                      SweepShape *sh, int carveout_pct, int sweep_kernel) {
     SF_ARG(storage == SF_F32 || storage == SF_BF16 || storage == SF_F16, "storage type %d is not supported",
            storage);
-    SF_ARG(sweep_kernel >= SF_SWEEP_AUTO && sweep_kernel <= SF_SWEEP_DIRECT, "sweep_kernel must be SF_SWEEP_*");
+    SF_ARG(sweep_kernel >= SF_SWEEP_AUTO && sweep_kernel <= SF_SWEEP_PERSISTENT, "sweep_kernel must be SF_SWEEP_*");
     const int vec = vec_of(storage);
     SF_ARG(slab_cols % vec == 0, "slab_cols %d is not a multiple of %d", slab_cols, vec);
     const int lpr = slab_cols / vec;
@@ -282,8 +282,12 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                             float *Y, double *mom, const sf_opts &o, cudaStream_t s, const float *coef_dev = nullptr,
                             const double *tol_dev = nullptr) {
     SweepShape sh;
-    sf_status st = make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode, G.val != nullptr, &sh,
-                              o.carveout_pct, o.sweep_kernel);
+    // batches: one persistent launch runs all orders of a slab (SF_SWEEP_PERSISTENT)
+    const bool persistent = G.gid != nullptr && mode != MODE_MOM && o.sweep_kernel == SF_SWEEP_PERSISTENT;
+    sf_status st = persistent ? make_batch_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode,
+                                                 G.val != nullptr, o.carveout_pct, &sh)
+                              : make_shape(o.storage, o.slab_cols, o.block_warps, o.blocks_per_sm, mode,
+                                           G.val != nullptr, &sh, o.carveout_pct, o.sweep_kernel);
     if (st) return st;
     int32_t *status = device_status();
     SF_ARG(status, "device status word unavailable");
@@ -388,6 +392,15 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 pair_sum_kernel<<<1, 256, 0, s>>>(part, pack_grid, 1, mom);
                 if ((st = check_launch("pair_sum_kernel"))) return st;
             }
+            if (persistent) {
+                double by = 0.0;
+                for (int j = 1; j <= p; ++j)
+                    by += step_bytes(n, G.nnz, unit, batched, w, o.storage, mode, j >= 2, n_cut, false, n_slabs);
+                if (p >= 1 && (st = launch_batch_persistent(sh, MODE_FWD, P, G.n_graphs, p, gid_t, buf, s, by)))
+                    return st;
+                goto slab_done;
+            }
+            {
             // orders 1..p: buffer of T_j is j % 3
             ProfSpan span(s, mode * 3 + o.storage);
             for (int j = 1; j <= p; ++j) {
@@ -404,6 +417,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 if ((st = launch_step(sh, mode, P, s, by))) return st;
                 span.add(by);
             }
+            }
         } else {
             // Clenshaw: Q = packed R, b_p = a_p R; b_j = a_j R + 2 Lt b_{j+1} - b_{j+2};
             // Y = a_0 R + Lt b_1 - b_2.
@@ -411,6 +425,15 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                                   0, 1, coef, p + 1, p, G.gid, buf[p % 3], nullptr, maxbits, perm, (int32_t)rows)))
                 return st;
             P.Q = qbuf;
+            if (persistent && p >= 1) {
+                P.outf = yacc;  // written by the final step (j = 0)
+                double by = 0.0;
+                for (int j = p - 1; j >= 0; --j)
+                    by += step_bytes(n, G.nnz, unit, batched, w, o.storage, MODE_CLEN, j + 2 <= p, 1, j == 0, n_slabs);
+                if ((st = launch_batch_persistent(sh, MODE_CLEN, P, G.n_graphs, p, gid_t, buf, s, by))) return st;
+                goto slab_done;
+            }
+            {
             ProfSpan span(s, MODE_CLEN * 3 + o.storage);
             for (int j = p - 1; j >= 0; --j) {
                 // b_j lives in buffer j % 3; b_{j+1}, b_{j+2} in the other two
@@ -431,6 +454,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                 if ((st = launch_step(sh, MODE_CLEN, P, s, by))) return st;
                 span.add(by);
             }
+            }
             if (p == 0) {
                 // Y = a_0 R: b_0 computed by the pack as a_p R with p = 0, widen to fp32
                 if ((st = launch_pack(o.storage, pack_grid, s, R, r_dtype, (int32_t)n, n_sig, c0, w, ld, qbuf, yacc,
@@ -439,6 +463,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                     return st;
             }
         }
+    slab_done:
         if (ncy) {
             unpack_kernel<<<pack_grid * 2, 256, 0, s>>>(yacc, (int32_t)n, ld, w, ncy, Y, n_sig, c0, maxbits, perm,
                                                         (int32_t)rows);
@@ -509,7 +534,9 @@ SF_API sf_status sf_device_check(void *stream) {
     if (h) {
         SF_CHECK_CUDA(cudaMemsetAsync(p, 0, sizeof(int32_t), s));
         SF_CHECK_CUDA(cudaStreamSynchronize(s));
-        set_error("a sweep kernel's bounded wait for its staged tile gave up (status %d)", h);
+        set_error("a sweep kernel's bounded wait gave up (status %d: bit 0 a staged tile, bit 1 a graph of a "
+                  "persistent batch sweep that never finished its previous order)",
+                  h);
         return SF_ERR_TIMEOUT;
     }
     return SF_OK;
@@ -591,12 +618,18 @@ SF_API sf_status sf_eigencount(const sf_graph *g, double lam_max, const void *R,
     return SF_OK;
 }
 
-SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
-                                        int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
-                                        const sf_opts *opts, void *stream) {
+}  // extern "C"
+
+namespace sf {
+// The batched filter with n_cut coefficient rows per graph (coeffs
+// [n_graphs][n_cut][p + 1], Y [n_cut][N][n_sig]).
+static sf_status batched_filter(const sf_batch *b, const double *lam_max, const double *coeffs, int32_t n_cut,
+                                int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                const sf_opts *opts, cudaStream_t stream) {
     SF_ARG(b, "batch is NULL");
     SF_ARG(lam_max && coeffs && R && Y, "null pointer");
     SF_ARG(p >= 0 && n_sig >= 1, "need p >= 0 and n_sig >= 1");
+    SF_ARG(n_cut >= 1 && n_cut <= 64, "n_cut must be in [1, 64] (got %d)", n_cut);
     SF_ARG(r_dtype == SF_F32 || r_dtype == SF_BF16, "R dtype must be SF_F32 or SF_BF16");
     SF_ARG(b->device == current_device(), "batch lives on another device");
     std::vector<double> tol((size_t)b->n_graphs);
@@ -604,23 +637,49 @@ SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max
         SF_ARG(lam_max[k] > 0.0 && isfinite(lam_max[k]), "lam_max[%d] must be finite and > 0", k);
         tol[k] = 2.0 / lam_max[k];
     }
-    for (int64_t k = 0; k < (int64_t)b->n_graphs * (p + 1); ++k)
-        SF_ARG(isfinite(coeffs[k]), "coefficient %lld is not finite", (long long)k);
+    const int64_t ncoef = (int64_t)b->n_graphs * n_cut * (p + 1);
+    for (int64_t k = 0; k < ncoef; ++k) SF_ARG(isfinite(coeffs[k]), "coefficient %lld is not finite", (long long)k);
     sf_opts o;
     sf_status st = resolve_opts(opts, b->n, n_sig, &o);
     if (st) return st;
-    int algo = o.algo == SF_ALGO_AUTO ? (o.storage == SF_F32 ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD) : o.algo;
+    int algo = o.algo;
+    if (algo == SF_ALGO_AUTO) algo = (n_cut == 1 && o.storage == SF_F32) ? SF_ALGO_CLENSHAW : SF_ALGO_FORWARD;
     SF_ARG(algo == SF_ALGO_FORWARD || algo == SF_ALGO_CLENSHAW, "unknown algo %d", algo);
     {
         std::lock_guard<std::mutex> lk(b->sell_mu);
-        if ((st = sell_build(&b->sell, b->n, b->rowptr, b->colidx, b->unit_weights ? nullptr : b->val,
-                             (cudaStream_t)stream)))
+        if ((st = sell_build(&b->sell, b->n, b->rowptr, b->colidx, b->unit_weights ? nullptr : b->val, stream)))
             return st;
     }
     GraphView G{b->n,          b->nnz,         b->rowptr,   b->colidx, b->unit_weights ? nullptr : b->val,
                 b->strength,   b->row_graph,   b->n_graphs, &b->sell};
-    return run_sweeps(G, tol.data(), 0.0, algo == SF_ALGO_FORWARD ? MODE_FWD : MODE_CLEN, coeffs, 1, p, R, r_dtype,
-                      n_sig, Y, nullptr, o, (cudaStream_t)stream);
+    if (algo == SF_ALGO_FORWARD)
+        return run_sweeps(G, tol.data(), 0.0, MODE_FWD, coeffs, n_cut, p, R, r_dtype, n_sig, Y, nullptr, o, stream);
+    // Clenshaw: one cutoff at a time, each with its own [n_graphs][p + 1] table
+    std::vector<double> one((size_t)b->n_graphs * (p + 1));
+    for (int c = 0; c < n_cut; ++c) {
+        for (int g = 0; g < b->n_graphs; ++g)
+            for (int j = 0; j <= p; ++j)
+                one[(size_t)g * (p + 1) + j] = coeffs[((int64_t)g * n_cut + c) * (p + 1) + j];
+        if ((st = run_sweeps(G, tol.data(), 0.0, MODE_CLEN, one.data(), 1, p, R, r_dtype, n_sig,
+                             Y + (int64_t)c * b->n * n_sig, nullptr, o, stream)))
+            return st;
+    }
+    return SF_OK;
+}
+}  // namespace sf
+
+extern "C" {
+
+SF_API sf_status sf_cheb_filter_batched(const sf_batch *b, const double *lam_max, const double *coeffs,
+                                        int32_t p, const void *R, int32_t r_dtype, int32_t n_sig, float *Y,
+                                        const sf_opts *opts, void *stream) {
+    return batched_filter(b, lam_max, coeffs, 1, p, R, r_dtype, n_sig, Y, opts, (cudaStream_t)stream);
+}
+
+SF_API sf_status sf_cheb_filter_batched_multi(const sf_batch *b, const double *lam_max, const double *coeffs,
+                                              int32_t n_cut, int32_t p, const void *R, int32_t r_dtype,
+                                              int32_t n_sig, float *Y, const sf_opts *opts, void *stream) {
+    return batched_filter(b, lam_max, coeffs, n_cut, p, R, r_dtype, n_sig, Y, opts, (cudaStream_t)stream);
 }
 
 SF_API sf_status sf_cheb_filter_batched_dev(const sf_batch *b, const double *two_over_lam, const float *coeffs,

@@ -613,9 +613,6 @@ __global__ void km_fix_centroid_kernel(int32_t n, int32_t d, int32_t k, const in
 }
 
 // ------------------------------------------------------------ tensor cores
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // 2-D tiled TMA load of box {32 FP32 columns, rows} at (x, y) into shared memory
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar) {

@@ -99,9 +99,49 @@ __global__ void selftest_wait_kernel(int32_t polls, int32_t *status) {
     if (!landed && threadIdx.x == 0) atomicOr(status, 1);
 }
 
+// One thread waits, as a persistent batch tile does, for a graph whose arrival
+// counter nothing increments (step 1 of a graph with one chunk), gives up after
+// `polls` polls and sets the status word and the abort flag as the batch
+// kernel does.
+__global__ void selftest_arrival_kernel(int32_t polls, int32_t *status, uint32_t *counters, int32_t *tables) {
+    BatchSched S = {};
+    S.n_tiles = 1;
+    S.n_chunks = 1;
+    S.p = 2;
+    S.chunk_glo = tables;       // chunk 0 covers graph 0 ...
+    S.chunk_ghi = tables;
+    S.graph_chunks = counters;  // ... which has one chunk
+    S.done = counters + 1;      // and has completed nothing
+    S.abort = tables + 1;
+    if (!wait_graph_deps(S, 1, 0, (uint32_t)polls)) {
+        atomicOr(status, 2);
+        atomicExch(S.abort, 1);
+    }
+}
+
 }  // namespace sf
 
 using namespace sf;
+
+extern "C" SF_API sf_status sf_selftest_arrival_wait(int32_t polls, void *stream) {
+    SF_ARG(polls >= 1 && polls <= (1 << 16), "polls must be in [1, 2^16]");
+    int32_t *status = device_status();
+    SF_ARG(status, "device status word unavailable");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    uint32_t *counters = nullptr;
+    int32_t *tables = nullptr;
+    sf_status st;
+    if ((st = sc.get(&counters, 2)) || (st = sc.get(&tables, 2))) return st;
+    const uint32_t c_h[2] = {1u, 0u};  // graph 0: one chunk, nothing completed
+    const int32_t t_h[2] = {0, 0};     // chunk 0 covers graph 0; abort flag clear
+    SF_CHECK_CUDA(cudaMemcpyAsync(counters, c_h, sizeof(c_h), cudaMemcpyHostToDevice, s));
+    SF_CHECK_CUDA(cudaMemcpyAsync(tables, t_h, sizeof(t_h), cudaMemcpyHostToDevice, s));
+    selftest_arrival_kernel<<<1, 1, 0, s>>>(polls, status, counters, tables);
+    st = check_launch("selftest_arrival_kernel");
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));  // the host copies and the scratch outlive the kernel
+    return st;
+}
 
 extern "C" SF_API sf_status sf_selftest_bounded_wait(int32_t polls, void *stream) {
     SF_ARG(polls >= 1 && polls <= (1 << 20), "polls must be in [1, 2^20]");

@@ -39,6 +39,18 @@ struct VT<float> {
     __device__ __forceinline__ static float cvt(float x) { return x; }
     using raw_t = float4;
     __device__ __forceinline__ static raw_t ld_raw(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    // coherent (L2) load, for blocks written earlier in the same launch
+    __device__ __forceinline__ static raw_t ld_raw_cg(const float *p) {
+        return __ldcg(reinterpret_cast<const float4 *>(p));
+    }
+    // the same, read once: evict-first in L2
+    __device__ __forceinline__ static raw_t ld_raw_cg_once(const float *p, uint64_t pol) {
+        float4 v;
+        asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(p), "l"(pol));
+        return v;
+    }
     __device__ __forceinline__ static raw_t zero_raw() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ static raw_t ld_raw_stream(const float *p) {
         return __ldcs(reinterpret_cast<const float4 *>(p));
@@ -97,6 +109,16 @@ struct VT<__nv_bfloat16> {
     using raw_t = uint4;
     __device__ __forceinline__ static raw_t ld_raw(const __nv_bfloat16 *p) {
         return __ldg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static raw_t ld_raw_cg(const __nv_bfloat16 *p) {
+        return __ldcg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static raw_t ld_raw_cg_once(const __nv_bfloat16 *p, uint64_t pol) {
+        uint4 v;
+        asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p), "l"(pol));
+        return v;
     }
     __device__ __forceinline__ static raw_t zero_raw() { return make_uint4(0u, 0u, 0u, 0u); }
     __device__ __forceinline__ static raw_t ld_raw_stream(const __nv_bfloat16 *p) {
@@ -165,6 +187,16 @@ struct VT<__half> {
     __device__ __forceinline__ static __half cvt(float x) { return __float2half_rn(x); }
     using raw_t = uint4;
     __device__ __forceinline__ static raw_t ld_raw(const __half *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+    __device__ __forceinline__ static raw_t ld_raw_cg(const __half *p) {
+        return __ldcg(reinterpret_cast<const uint4 *>(p));
+    }
+    __device__ __forceinline__ static raw_t ld_raw_cg_once(const __half *p, uint64_t pol) {
+        uint4 v;
+        asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "l"(p), "l"(pol));
+        return v;
+    }
     __device__ __forceinline__ static raw_t ld_raw_stream(const __half *p) {
         return __ldcs(reinterpret_cast<const uint4 *>(p));
     }
@@ -350,6 +382,11 @@ __device__ __forceinline__ void ld8_stream(const float *p, float (&x)[8]) {
                  : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
                  : "l"(p));
 }
+__device__ __forceinline__ void ld8_cg_once(const float *p, float (&x)[8], uint64_t pol) {
+    asm volatile("ld.global.cg.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p), "l"(pol));
+}
 __device__ __forceinline__ void st8_stream(float *p, const float (&x)[8]) {
     asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x[0]), "f"(x[1]),
                  "f"(x[2]), "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
@@ -421,8 +458,17 @@ __device__ __forceinline__ float4 ld_val4(const float *p) {
     else return __ldg(reinterpret_cast<const float4 *>(p));
 }
 
-// acc += sum over the row's ls entries of w_e * X[idx_e] (this lane's 16 bytes)
-template <typename TS, bool W, bool SMEM, bool MIX>
+// one gathered row chunk: the read-only path, or L2 (COH)
+template <typename TS, bool COH>
+__device__ __forceinline__ typename VT<TS>::raw_t ld_gathered(const TS *p) {
+    if constexpr (COH) return VT<TS>::ld_raw_cg(p);
+    else return VT<TS>::ld_raw(p);
+}
+
+// acc += sum over the row's ls entries of w_e * X[idx_e] (this lane's 16 bytes).
+// COH: the gathered block was written earlier in the same launch, so it is read
+// through L2 (the read-only path could hold lines from before the write).
+template <typename TS, bool W, bool SMEM, bool MIX, bool COH = false>
 __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rstride, const int32_t *ip,
                                            const float *wp, int32_t ls, float (&acc)[VT<TS>::V]) {
     using V = VT<TS>;
@@ -432,7 +478,7 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
         const int32_t k[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         typename V::raw_t x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = V::ld_raw(Xq + (uint32_t)k[u] * (uint32_t)rstride);
+        for (int u = 0; u < 8; ++u) x[u] = ld_gathered<TS, COH>(Xq + (uint32_t)k[u] * (uint32_t)rstride);
         if constexpr (W) {
             const float4 wa = ld_val4<SMEM>(wp + j), wb = ld_val4<SMEM>(wp + j + 4);
             const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
@@ -451,7 +497,7 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
         const int32_t k[4] = {a.x, a.y, a.z, a.w};
         typename V::raw_t x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = V::ld_raw(Xq + (uint32_t)k[u] * (uint32_t)rstride);
+        for (int u = 0; u < 4; ++u) x[u] = ld_gathered<TS, COH>(Xq + (uint32_t)k[u] * (uint32_t)rstride);
         if constexpr (W) {
             const float4 wa = ld_val4<SMEM>(wp + j);
             const float w[4] = {wa.x, wa.y, wa.z, wa.w};
@@ -467,24 +513,43 @@ __device__ __forceinline__ void gather_row(const TS *__restrict__ Xq, int32_t rs
     }
 }
 
+// The blocks and coefficient index one order works on: from the launch's
+// parameters (a launch per order) or from the work item (the persistent batch).
+struct OrderView {
+    const void *X;  // gathered block
+    const void *Z;  // subtracted block (nullptr: none)
+    void *out;      // output block
+    float *outf;    // Clenshaw final: fp32 output instead of `out`
+    float m;        // 2, or 1 for the first order / the final Clenshaw step
+    int32_t j;      // coefficient index
+};
+__device__ __forceinline__ OrderView order_of(const StepParams &P) {
+    return OrderView{P.X, P.Z, P.out, P.outf, P.m, P.j};
+}
+
 // One row of one order: acc = sum_e w_e X[idx_e] over the row's ls entries,
 // then v = m (d_t X_t - (2/lam) acc) - Z_t [+ a_j Q_t], stored; the forward
 // mode adds a_cj v to each accumulator, the moment mode sums v.v and v.X_t.
 // t is the row's slice-row position, which is also its row in every block.
-template <typename TS, int MODE, bool W, bool SMEM>
-__device__ __forceinline__ void sweep_row(const StepParams &P, int32_t t, int q, const int32_t *ip, const float *wp,
-                                          int32_t ls, double &mtt, double &mtx) {
+// COH: every block the launch itself writes is read through L2.
+template <typename TS, int MODE, bool W, bool SMEM, bool COH = false>
+__device__ __forceinline__ void sweep_row(const StepParams &P, const OrderView &O, int32_t t, int q, const int32_t *ip,
+                                          const float *wp, int32_t ls, double &mtt, double &mtx) {
     using V = VT<TS>;
     constexpr int VEC = V::V;
-    const TS *__restrict__ X = static_cast<const TS *>(P.X);
-    const TS *__restrict__ Z = static_cast<const TS *>(P.Z);
+    const TS *__restrict__ X = static_cast<const TS *>(O.X);
+    const TS *__restrict__ Z = static_cast<const TS *>(O.Z);
     const TS *__restrict__ Qb = static_cast<const TS *>(P.Q);
-    TS *__restrict__ out = static_cast<TS *>(P.out);
+    TS *__restrict__ out = static_cast<TS *>(O.out);
     const int32_t ld = P.ld;
     const int64_t ro = (int64_t)t * ld + q * VEC;
     // epilogue operands first (kept packed): their latency overlaps the gathers
-    const typename V::raw_t xi_r = V::ld_raw(X + ro);
-    const typename V::raw_t z_r = Z ? V::ld_raw_stream(Z + ro) : V::zero_raw();
+    const typename V::raw_t xi_r = ld_gathered<TS, COH>(X + ro);
+    typename V::raw_t z_r = V::zero_raw();
+    if (Z) {
+        if constexpr (COH) z_r = V::ld_raw_cg_once(Z + ro, l2_policy_evict_first());
+        else z_r = V::ld_raw_stream(Z + ro);
+    }
     typename V::raw_t q_r = V::zero_raw();
     if (MODE == MODE_CLEN) q_r = V::ld_raw_stream(Qb + ro);
     const float d = __ldcs(P.dtil + t);
@@ -494,8 +559,9 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t t, int q,
     float acc[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-    if (!W && VEC == 8 && (P.flags & STEP_MIXED_ADD)) gather_row<TS, W, SMEM, true>(X + q * VEC, ld, ip, wp, ls, acc);
-    else gather_row<TS, W, SMEM, false>(X + q * VEC, ld, ip, wp, ls, acc);
+    if (!W && VEC == 8 && (P.flags & STEP_MIXED_ADD))
+        gather_row<TS, W, SMEM, true, COH>(X + q * VEC, ld, ip, wp, ls, acc);
+    else gather_row<TS, W, SMEM, false, COH>(X + q * VEC, ld, ip, wp, ls, acc);
 
     float tv[VEC], xi[VEC];
     {
@@ -503,17 +569,17 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t t, int q,
         V::to_float(xi_r, xi);
         V::to_float(z_r, z);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) tv[v] = P.m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
+        for (int v = 0; v < VEC; ++v) tv[v] = O.m * fmaf(d, xi[v], -sc * acc[v]) - z[v];
     }
     if (MODE == MODE_CLEN) {
-        const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + P.j);
+        const float alpha = __ldg(P.coef + (int64_t)g * P.coef_ld + O.j);
         float qv[VEC];
         V::to_float(q_r, qv);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) tv[v] = fmaf(alpha, qv[v], tv[v]);
     }
-    if (MODE == MODE_CLEN && P.outf) {
-        float *o = P.outf + ro;
+    if (MODE == MODE_CLEN && O.outf) {
+        float *o = O.outf + ro;
         if constexpr (VEC == 8) {
             st8_stream(o, tv);
         } else {
@@ -526,16 +592,18 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, int32_t t, int q,
     }
     if (MODE == MODE_FWD) {
         for (int c = 0; c < P.n_cut; ++c) {
-            const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + P.j);
+            const float a = __ldg(P.coef + ((int64_t)g * P.n_cut + c) * P.coef_ld + O.j);
             float *y = P.Y + c * P.ystride + ro;
             if constexpr (VEC == 8) {
                 float yy[8];
-                ld8_stream(y, yy);
+                if constexpr (COH) ld8_cg_once(y, yy, l2_policy_evict_first());
+                else ld8_stream(y, yy);
 #pragma unroll
                 for (int v = 0; v < 8; ++v) yy[v] = fmaf(a, tv[v], yy[v]);
                 st8_stream(y, yy);
             } else {
-                float4 yy = __ldcs(reinterpret_cast<const float4 *>(y));
+                float4 yy = COH ? VT<float>::ld_raw_cg_once(y, l2_policy_evict_first())
+                                : __ldcs(reinterpret_cast<const float4 *>(y));
                 yy.x = fmaf(a, tv[0], yy.x);
                 yy.y = fmaf(a, tv[1], yy.y);
                 yy.z = fmaf(a, tv[2], yy.z);
@@ -701,9 +769,9 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
             const int sl = tr / kSliceRows, pos = tr % kSliceRows;
             const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
             const int32_t eo = so - e0 + pos * ls;  // offset of the row's first entry in the tile
-            if (fits) sweep_row<TS, MODE, W, true>(P, t, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
-            else sweep_row<TS, MODE, W, false>(P, t, q, P.sell_idx + e0 + eo, W ? P.sell_val + e0 + eo : nullptr,
-                                               ls, mtt, mtx);
+            if (fits) sweep_row<TS, MODE, W, true>(P, order_of(P), t, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
+            else sweep_row<TS, MODE, W, false>(P, order_of(P), t, q, P.sell_idx + e0 + eo,
+                                               W ? P.sell_val + e0 + eo : nullptr, ls, mtt, mtx);
         }
         __syncwarp();
         if (lane == 0) {
@@ -750,10 +818,262 @@ __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepPara
         const int32_t so = __ldg(P.sell_ptr + sl);
         const int32_t ls = (__ldg(P.sell_ptr + sl + 1) - so) / kSliceRows;
         const int64_t eo = (int64_t)so + (int64_t)pos * ls;
-        sweep_row<TS, MODE, W, false>(P, (int32_t)t, q, P.sell_idx + eo, W ? P.sell_val + eo : nullptr, ls, mtt,
-                                      mtx);
+        sweep_row<TS, MODE, W, false>(P, order_of(P), (int32_t)t, q, P.sell_idx + eo,
+                                      W ? P.sell_val + eo : nullptr, ls, mtt, mtx);
     }
     if (MODE == MODE_MOM) block_moments(P, mtt, mtx);
+}
+
+// ------------------------------------------------------------ persistent batch
+// One launch filters a batch of graphs through all p orders. Work item
+// i = s * n_chunks + c is order step s (forward: order s + 1; Clenshaw:
+// index j = p - 1 - s) of chunk c, kBatchChunk consecutive tiles. Blocks claim
+// items from a global counter in increasing order, and an item may start once
+// every graph its chunk covers has completed step s - 1 on all of that
+// graph's chunks (per-graph arrival counters). Every item an item waits for
+// has a smaller index, so it was claimed before by a block that is running:
+// the launch cannot deadlock, whatever the grid. A small graph therefore moves
+// to its next order as soon as its own chunks are done, without waiting for
+// the rest of the batch. Each wait is bounded; one that gives up sets the
+// status word and an abort flag that makes every other wait give up at once.
+constexpr int kBatchChunk = 8;  // tiles per work item
+
+struct BatchSched {
+    int32_t n_tiles;
+    int32_t n_chunks;             // ceil(n_tiles / kBatchChunk)
+    int32_t p;                    // orders: the launch runs p steps
+    const int32_t *chunk_glo;     // [n_chunks] lowest graph id among the chunk's rows
+    const int32_t *chunk_ghi;     // [n_chunks] highest graph id among the chunk's rows
+    const uint32_t *graph_chunks; // [n_graphs] chunks whose graph range covers the graph
+    uint32_t *done;               // [n_graphs] completed items covering the graph (zero at launch)
+    uint32_t *queue;              // next item to claim (zero at launch)
+    int32_t *abort;               // nonzero once any wait gave up (zero at launch)
+    void *buf[3];                 // the three rotating blocks (rows + 1 rows each)
+};
+
+// buf[k % 3] by selects (a dynamic index into the parameter array would go through local memory)
+__device__ __forceinline__ void *sched_buf(const BatchSched &S, int k) {
+    const int r = k % 3;
+    return r == 0 ? S.buf[0] : (r == 1 ? S.buf[1] : S.buf[2]);
+}
+
+template <int MODE>
+__device__ __forceinline__ OrderView order_at(const StepParams &P, const BatchSched &S, int s) {
+    OrderView O;
+    if (MODE == MODE_FWD) {
+        const int j = s + 1;
+        O.X = sched_buf(S, j - 1);
+        O.Z = (j >= 2) ? sched_buf(S, j - 2) : nullptr;
+        O.out = sched_buf(S, j);
+        O.outf = nullptr;
+        O.m = (j == 1) ? 1.0f : 2.0f;
+        O.j = j;
+    } else {
+        const int j = S.p - 1 - s;
+        O.X = sched_buf(S, j + 1);
+        O.Z = (j + 2 <= S.p) ? sched_buf(S, j + 2) : nullptr;
+        O.out = (j == 0) ? nullptr : sched_buf(S, j);
+        O.outf = (j == 0) ? P.outf : nullptr;
+        O.m = (j == 0) ? 1.0f : 2.0f;
+        O.j = j;
+    }
+    return O;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t *p) {
+    return *reinterpret_cast<const volatile int32_t *>(p);
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+constexpr uint32_t kDepPolls = 1u << 20;  // with a 128 ns sleep between polls: about a second
+
+// Waits (at most `polls` polls per graph) until every graph of chunk c has
+// completed step s - 1.
+__device__ __forceinline__ bool wait_graph_deps(const BatchSched &S, int s, int c, uint32_t polls = kDepPolls) {
+    if (s == 0) return true;
+    const int g0 = __ldg(S.chunk_glo + c), g1 = __ldg(S.chunk_ghi + c);
+    for (int g = g0; g <= g1; ++g) {
+        const uint32_t need = (uint32_t)s * __ldg(S.graph_chunks + g);
+        uint32_t it = 0;
+        while (ld_acquire_u32(S.done + g) < need) {
+            if (++it >= polls || ld_volatile_i32(S.abort)) return false;
+            __nanosleep(128);
+        }
+    }
+    return true;
+}
+
+// Stage wait that also gives up as soon as another wait of the launch did.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, const int32_t *abort) {
+    for (uint32_t it = 0; it < kWaitPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && ld_volatile_i32(abort)) return false;
+    }
+    return false;
+}
+
+// The block's tiles form a sequence (the tiles of its items in claim order);
+// the two stages hold consecutive positions of it. s_pos[b] = (item, tile of
+// the item) staged in stage b (item -1: the queue is exhausted); s_cur = the
+// next position to stage.
+template <typename TS, int LPR, int MODE, bool W>
+__global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, const BatchSched S) {
+    using C = TileCfg<LPR>;
+    constexpr int NST = C::stages;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem_raw);      // [NST] copy landed
+    int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 32);  // [NST][2]: entry base, fits
+    int32_t *s_cnt = s_meta + 2 * NST;                              // [NST] warps done with the stage's tile
+    int32_t *s_iss = s_cnt + NST;                                   // [NST] phases started on the stage
+    int32_t *s_pos = s_iss + NST;                                   // [NST][2]: item, tile of the item
+    int32_t *s_cur = s_pos + 2 * NST;                               // [2]: the next position to stage
+    unsigned char *s_buf0 = smem_raw + C::header;
+    constexpr int buf_bytes = C::buf_bytes(W);
+    static_assert(32 + 7 * NST * 4 + 8 <= C::header, "stage header");
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int q = tid % LPR, grp = tid / LPR;
+    const int ngrp = blockDim.x / LPR;
+    const int nwarps = blockDim.x >> 5;
+    const int total = S.p * S.n_chunks;
+    double mtt = 0.0, mtx = 0.0;  // unused (no moment mode for batches)
+
+    // tiles of chunk c
+    auto chunk_tiles = [&](int c) {
+        const int t0 = c * kBatchChunk;
+        return (S.n_tiles - t0) < kBatchChunk ? (S.n_tiles - t0) : kBatchChunk;
+    };
+    // one thread: claim a new item when the current one is used up, then stage
+    // the sequence's next tile into stage b (or mark the stage exhausted)
+    auto stage_next = [&](int b) {
+        int item = s_cur[0], k = s_cur[1];
+        if (item < 0 || k >= chunk_tiles(item % S.n_chunks)) {
+            const int it = (int)atomicAdd(S.queue, 1u);
+            item = (it < total) ? it : -1;
+            k = 0;
+        }
+        s_cur[0] = item;
+        s_cur[1] = k + 1;
+        s_pos[2 * b] = item;
+        s_pos[2 * b + 1] = k;
+        s_iss[b] += 1;
+        if (item < 0) {
+            mbar_arrive(&s_bar[b]);
+            return;
+        }
+        const int tile = (item % S.n_chunks) * kBatchChunk + k;
+        unsigned char *base = s_buf0 + b * buf_bytes;
+        int32_t *sp = reinterpret_cast<int32_t *>(base);
+        int32_t *ix = sp + 2 * C::sp_ints;
+        float *wv = reinterpret_cast<float *>(ix + C::entries);
+        const int32_t s0 = tile * C::slices;
+        const int32_t e0 = __ldg(P.sell_ptr + s0), e1 = __ldg(P.sell_ptr + s0 + C::slices);
+        const int32_t cnt = e1 - e0;
+        const bool fits = cnt <= C::entries;
+        const uint32_t bytes = C::sp_ints * 4 + (fits ? (uint32_t)cnt * 4u * (W ? 2u : 1u) : 0u);
+        s_meta[2 * b] = e0;
+        s_meta[2 * b + 1] = fits ? 1 : 0;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&s_bar[b], bytes);
+        bulk_g2s(sp, P.sell_ptr + s0, C::sp_ints * 4, &s_bar[b]);
+        if (fits && cnt > 0) {
+            if (P.flags & STEP_IDX_EVICT_FIRST) {
+                const uint64_t pol = l2_policy_evict_first();
+                bulk_g2s_hint(ix, P.sell_idx + e0, cnt * 4, &s_bar[b], pol);
+                if (W) bulk_g2s_hint(wv, P.sell_val + e0, cnt * 4, &s_bar[b], pol);
+            } else {
+                bulk_g2s(ix, P.sell_idx + e0, cnt * 4, &s_bar[b]);
+                if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
+            }
+        }
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < NST; ++b) {
+            mbar_init(&s_bar[b], 1);
+            s_cnt[b] = 0;
+            s_iss[b] = 0;
+        }
+        s_cur[0] = -1;
+        s_cur[1] = 0;
+        fence_mbar_init();
+        for (int b = 0; b < NST; ++b) stage_next(b);
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int b = k % NST;
+        const uint32_t par = (uint32_t)(k / NST) & 1u;
+        if (!mbar_wait_or_abort(&s_bar[b], par, S.abort)) {
+            if (lane == 0) {
+                atomicOr(P.status, 1);
+                atomicExch(S.abort, 1);
+            }
+            break;
+        }
+        const int item = s_pos[2 * b], kt = s_pos[2 * b + 1];
+        if (item < 0) break;  // the queue is exhausted
+        const int s = item / S.n_chunks, c = item % S.n_chunks;
+        const int tile = c * kBatchChunk + kt;
+        if (kt == 0) {  // the item's first tile: its graphs must have finished the previous step
+            bool ok = true;
+            if (lane == 0) {
+                ok = wait_graph_deps(S, s, c);
+                if (!ok) {
+                    atomicOr(P.status, 2);
+                    atomicExch(S.abort, 1);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            __syncwarp();  // lane 0's acquire of the counters is ordered before every lane's reads below
+            if (!ok) break;
+        }
+        const OrderView O = order_at<MODE>(P, S, s);
+        const int32_t *s_sp = reinterpret_cast<const int32_t *>(s_buf0 + b * buf_bytes);
+        const int32_t *s_ix = s_sp + 2 * C::sp_ints;
+        const float *s_wv = reinterpret_cast<const float *>(s_ix + C::entries);
+        const int32_t e0 = s_meta[2 * b];
+        const bool fits = s_meta[2 * b + 1] != 0;
+        for (int tr = grp; tr < C::rows; tr += ngrp) {
+            const int32_t t = tile * C::rows + tr;
+            if (t >= P.n) continue;
+            const int sl = tr / kSliceRows, pos = tr % kSliceRows;
+            const int32_t so = s_sp[sl], ls = (s_sp[sl + 1] - so) / kSliceRows;
+            const int32_t eo = so - e0 + pos * ls;
+            if (fits) sweep_row<TS, MODE, W, true, true>(P, O, t, q, s_ix + eo, s_wv + eo, ls, mtt, mtx);
+            else sweep_row<TS, MODE, W, false, true>(P, O, t, q, P.sell_idx + e0 + eo,
+                                                     W ? P.sell_val + e0 + eo : nullptr, ls, mtt, mtx);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();  // this warp's rows come before its release of the stage
+            if (atomicAdd(&s_cnt[b], 1) == nwarps - 1) {
+                __threadfence_block();
+                s_cnt[b] = 0;
+                if (kt == chunk_tiles(c) - 1) {
+                    // the item is complete: release every warp's rows to the GPU, then count the
+                    // item for every graph its chunk covers
+                    fence_acq_rel_gpu();
+                    const int g0 = __ldg(S.chunk_glo + c), g1 = __ldg(S.chunk_ghi + c);
+                    for (int g = g0; g <= g1; ++g) atomicAdd(S.done + g, 1u);
+                }
+                stage_next(b);
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // copies may still be in flight after a wait gave up: wait (bounded) for the last one of each stage
+        for (int b = 0; b < NST; ++b)
+            if (s_iss[b] > 0) mbar_wait_bounded(&s_bar[b], (uint32_t)(s_iss[b] - 1) & 1u);
+    }
 }
 
 // ------------------------------------------------------------ pack / unpack
@@ -903,5 +1223,13 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
 int32_t step_flags(const sf_opts &o);
 // Finiteness and growth checks of a moment sweep's dot products (SF_ERR_NUMERIC).
 sf_status check_moment_dots(const double *dots, double e_last, int p, double lam_max);
+
+// The persistent batch sweep (sf_batch.cu): all p orders of one column slab
+// of a batch in one launch. gid_t holds the graph id of each slice row; P is
+// set up as for the per-order launches (P.outf: the Clenshaw output block).
+sf_status make_batch_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
+                           int carveout_pct, SweepShape *sh);
+sf_status launch_batch_persistent(const SweepShape &sh, int mode, StepParams P, int32_t n_graphs, int32_t p,
+                                  const int32_t *gid_t, void *const buf[3], cudaStream_t s, double bytes);
 
 }  // namespace sf

@@ -630,3 +630,101 @@ def test_bounded_wait_gives_up_without_fault(sf, oracle_mod):
     Y = sf.cheb_filter(g, lh, sf.cheb_coeffs(lh, 0.3 * lh, 10, True), R)
     sf.device_check()
     assert torch.isfinite(Y).all()
+
+
+# ------------------------------------------------------------------ persistent batch sweep
+def _small_batch(sf, oracle_mod, n_graphs, seed):
+    from paper_1509_08863_gb300 import synth
+
+    graphs, _ = synth.batched_sbm(n_graphs, seed=seed, n_lo=300, n_hi=2500, k_lo=2, k_hi=6)
+    gs, gos, lams = [], [], []
+    for gr in graphs:
+        g, go = build_both(sf, oracle_mod, gr.n, gr.src, gr.dst, gr.w)
+        gs.append(g)
+        gos.append(go)
+        lams.append(oracle_lambda_hat(oracle_mod, go, 40, seed=1))
+    return graphs, gs, gos, lams, sf.batch_build(gs)
+
+
+def test_batched_persistent_equals_per_order_launches(sf, oracle_mod):
+    """One persistent launch for all orders computes every row with the same
+    operations as one launch per order: bit-identical outputs for every
+    storage and algorithm, on a batch whose 32768-row sorting window spans
+    all 23 graphs (tiles straddle graph boundaries), and within 1e-5 of the
+    oracle with several cutoffs per graph (FP32)."""
+    graphs, gs, gos, lams, b = _small_batch(sf, oracle_mod, 23, seed=123)
+    n_tot, _, ng, offs = b.info()
+    p, n_sig = 25, 24
+    cuts = np.array([0.03, 0.1, 0.3])
+    coeffs3 = np.stack([oracle_mod.cheb_coeffs(lams[i], cuts * lams[i], p, True) for i in range(ng)])
+    R = np.random.default_rng(4).standard_normal((n_tot, n_sig)) / math.sqrt(n_sig)
+    Rt = torch.as_tensor(R, dtype=torch.float32, device="cuda")
+    for st, algo, slab in ((sf.F32, sf.ALGO_CLENSHAW, 16), (sf.F32, sf.ALGO_FORWARD, 8), (sf.BF16, sf.ALGO_FORWARD, 32),
+                           (sf.BF16, sf.ALGO_CLENSHAW, 16), (sf.F16, sf.ALGO_FORWARD, 32)):
+        outs = []
+        for kind in (sf.SWEEP_TILED, sf.SWEEP_PERSISTENT):
+            o = sf.Opts(storage=st, algo=algo, slab_cols=slab, sweep_kernel=kind)
+            outs.append(sf.cheb_filter_batched(b, lams, coeffs3[:, 1, :], Rt, o))
+        sf.device_check()
+        assert torch.equal(outs[0], outs[1]), (st, algo, slab)
+    for kind in (sf.SWEEP_TILED, sf.SWEEP_PERSISTENT):
+        Y = sf.cheb_filter_batched_multi(b, lams, coeffs3, Rt, sf.Opts(algo=sf.ALGO_FORWARD, sweep_kernel=kind))
+        if kind == sf.SWEEP_TILED:
+            Yt = Y
+        else:
+            assert torch.equal(Y, Yt)
+    Yc = sf.cheb_filter_batched_multi(b, lams, coeffs3, Rt, sf.Opts(algo=sf.ALGO_CLENSHAW,
+                                                                     sweep_kernel=sf.SWEEP_PERSISTENT))
+    for i in range(ng):
+        sl = slice(int(offs[i]), int(offs[i + 1]))
+        Yo = oracle_mod.cheb_filter(gos[i], lams[i], coeffs3[i], R[sl])
+        for c in range(3):
+            assert rel(Yt[c][sl].cpu().numpy(), Yo[c]) <= 1e-5, (i, c)
+            assert rel(Yc[c][sl].cpu().numpy(), Yo[c]) <= 1e-5, (i, c)
+
+
+def test_batched_persistent_under_cuda_graph(sf, oracle_mod):
+    graphs, gs, gos, lams, b = _small_batch(sf, oracle_mod, 6, seed=321)
+    n_tot = b.info()[0]
+    p = 17
+    coeffs = np.stack([oracle_mod.cheb_coeffs(lams[i], 0.1 * lams[i], p, True)[0] for i in range(len(gs))])
+    R = torch.randn(n_tot, 32, device="cuda")
+    opts = sf.Opts(storage=sf.BF16, slab_cols=32, sweep_kernel=sf.SWEEP_PERSISTENT)
+    Yref = sf.cheb_filter_batched(b, lams, coeffs, R, sf.Opts(storage=sf.BF16, slab_cols=32))
+    tol_d = torch.as_tensor(2.0 / np.array(lams), dtype=torch.float64, device="cuda")
+    coef_d = torch.as_tensor(coeffs, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(Yref)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Y, opts)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Yref)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        sf.cheb_filter_batched_dev(b, tol_d, coef_d, R, Y, opts)
+    for _ in range(2):
+        Y.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(Y, Yref)
+    sf.device_check()
+
+
+def test_arrival_wait_gives_up_without_fault(sf, oracle_mod):
+    """The persistent batch sweep's wait for a graph's previous order gives up
+    after its poll budget (a counter nothing increments), the host reads
+    SF_ERR_TIMEOUT, the word clears, and the next batched call works."""
+    sf.selftest_arrival_wait(500)
+    with pytest.raises(sf.SpecFiltError) as e:
+        sf.device_check()
+    assert e.value.status == 4
+    sf.device_check()
+    graphs, gs, gos, lams, b = _small_batch(sf, oracle_mod, 3, seed=7)
+    n_tot = b.info()[0]
+    coeffs = np.stack([oracle_mod.cheb_coeffs(lams[i], 0.2 * lams[i], 9, True)[0] for i in range(3)])
+    Y = sf.cheb_filter_batched(b, lams, coeffs, torch.ones((n_tot, 8), device="cuda"),
+                               sf.Opts(sweep_kernel=sf.SWEEP_PERSISTENT))
+    sf.device_check()
+    assert torch.isfinite(Y).all()
