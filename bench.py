@@ -910,7 +910,9 @@ def adjusted_rand_index(a, b):
 
 
 def stability_leg(sf, g, lh, p, n, eta, k, seed, J=4, half_width=2, starts=4):
-    """gamma(k) of §4.3 / Eq. (12) around the generating k, J realisations."""
+    """gamma(k) of §4.3 / Eq. (12) around the generating k, J realisations: at the
+    order that separates the filters of adjacent k (p_filter = 0) and, beside it,
+    with the filters at the count's order p."""
     import torch
 
     from paper_1509_08863_gb300 import synth
@@ -919,16 +921,20 @@ def stability_leg(sf, g, lh, p, n, eta, k, seed, J=4, half_width=2, starts=4):
     R = torch.as_tensor(np.stack([synth.gaussian_block(n, eta, seed + 200 + j) for j in range(J)]),
                         dtype=torch.float32, device="cuda")
     kmin, kmax = max(2, k - half_width), k + half_width
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    gamma, lam_k = sf.stability(g, lh, p, Rc, R, kmin, kmax, 50, starts, seed)
-    e1.record()
-    torch.cuda.synchronize()
     ks = list(range(kmin, kmax + 1))
-    return {"k": ks, "gamma": [float(x) for x in gamma], "lam_k": [float(x) for x in lam_k],
-            "k_star": ks[int(np.argmax(gamma))], "generating_k": k, "realisations": J, "starts": starts,
-            "ms": e0.elapsed_time(e1)}
+    out = {"k": ks, "generating_k": k, "realisations": J, "starts": starts, "count_order": p}
+    for name, pf in (("resolving_order", 0), ("count_order", None)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gamma, lam_k, used = sf.stability(g, lh, p, Rc, R, kmin, kmax, 50, starts, seed, p_filter=pf,
+                                          return_order=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"filter_order": used, "gamma": [float(x) for x in gamma], "lam_k": [float(x) for x in lam_k],
+                     "k_star": ks[int(np.argmax(gamma))], "ms": e0.elapsed_time(e1)}
+    out.update(out["resolving_order"])
+    return out
 
 
 def cluster_recovery(sf, g, lh, R, k, p, truth, seed, restarts=10):

@@ -560,24 +560,37 @@ SF_API sf_status sf_adjusted_rand(const int32_t *a, const int32_t *b, int32_t n,
 /*
  * gamma(k) of §4.3, Eq. (12), for k = kmin..kmax: the mean adjusted Rand
  * index between the clusterings of J realisations of the eta random signals.
+ *   p           order of the count's moment sweep
+ *   p_filter    order of the filters: > 0 as given (<= 20000); 0 picks the
+ *               order at which the filters of adjacent k differ: in
+ *               theta = arccos(2 lambda / lam_max - 1) a Jackson-damped series
+ *               of order q has a transition of standard deviation about
+ *               pi / (q + 2), and the order makes +-2 of them fit in the
+ *               smallest theta gap between the cutoffs of k - 1 .. kmax + 1
+ *               (q + 2 >= 4 pi / gap, at least p, at most 20000). The cutoffs
+ *               always come from the count at order p.
  *   Rc          device float[N][eta]: the count's probe block; lam_k is the
  *               dichotomy of the moments for the count k - 1/2 (one moment
  *               sweep serves every k)
- *   R           device float[J][N][eta]: the J realisations; each is filtered
- *               at every lam_k in one forward sweep (order p, Jackson damping),
- *               its rows are normalised and clustered by sf_kmeans into k
- *               clusters from `starts` seeded starts (lowest inertia kept)
+ *   R           device float[J][N][eta]: the J realisations, filtered side by
+ *               side as one block of J * eta columns at every lam_k in one
+ *               forward sweep (Jackson damping); each realisation's rows are
+ *               normalised and clustered by sf_kmeans into k clusters from
+ *               `starts` seeded starts (lowest inertia kept)
  *   max_iter    k-means assignments per start
  *   seed        start rows: SplitMix64 (Steele, Lea, Flood 2014) of
  *               (j << 40) | (k << 20) | (t << 10) | c, modulo N, for start t
  *               of realisation j, centroid c
  *   opts        block storage and tiles of the sweeps (the algorithm is forward)
  *   gamma       host out double[kmax - kmin + 1]; lam_k host out, same length
- * Needs J >= 2, 1 <= kmin <= kmax <= 1023, starts <= 1023. Synchronises `stream`.
+ *   p_used      host out: the filter order used (NULL: not reported)
+ * Needs J >= 2, J * eta <= 2^20, 1 <= kmin <= kmax <= 1023, starts <= 1023.
+ * Synchronises `stream`.
  */
-SF_API sf_status sf_stability(const sf_graph *g, double lam_max, int32_t p, const float *Rc, const float *R,
-                              int32_t J, int32_t eta, int32_t kmin, int32_t kmax, int32_t max_iter, int32_t starts,
-                              uint64_t seed, const sf_opts *opts, void *stream, double *gamma, double *lam_k);
+SF_API sf_status sf_stability(const sf_graph *g, double lam_max, int32_t p, int32_t p_filter, const float *Rc,
+                              const float *R, int32_t J, int32_t eta, int32_t kmin, int32_t kmax, int32_t max_iter,
+                              int32_t starts, uint64_t seed, const sf_opts *opts, void *stream, double *gamma,
+                              double *lam_k, int32_t *p_used);
 
 /*
  * Self-test of the failure path (no counterpart in the paper): one block

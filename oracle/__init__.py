@@ -110,7 +110,8 @@ def _load(parallel: bool = False):
         lib.oracle_adjusted_rand.restype = C.c_double
         lib.oracle_adjusted_rand.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.c_int32]
         lib.oracle_stability.restype = None
-        lib.oracle_stability.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int64, _f64p,
+        lib.oracle_stability.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_double, C.c_int32, C.c_int32, C.c_int64,
+                                         _f64p,
                                          C.c_int32, _f64p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                          _f64p, _f64p]
         lib.oracle_stability_init_row.restype = C.c_int32
@@ -354,17 +355,19 @@ def adjusted_rand(a, b) -> float:
 
 
 def stability(g: CSR, lam_max: float, p: int, Rc, R_blocks, kmin: int, kmax: int, max_iter: int, seed: int,
-              starts: int = 1):
+              starts: int = 1, p_filter: int | None = None):
     """gamma(k) of §4.3 / Eq. (12) for k = kmin..kmax (and the lam_k used):
     J = len(R_blocks) realisations of the filtered signals, count probes Rc,
-    k-means from `starts` seeded starts per clustering (lowest inertia kept)."""
+    k-means from `starts` seeded starts per clustering (lowest inertia kept).
+    The count uses order p, the filters order p_filter (None: p)."""
     Rc = _c(Rc, np.float64)
     R = _c(np.stack(R_blocks), np.float64)
     J, n, eta = R.shape
     K = kmax - kmin + 1
     gamma = np.zeros(K)
     lam_k = np.zeros(K)
-    _load().oracle_stability(g.n, g.rowptr, g.colidx, g.val, lam_max, p, eta, Rc, J, R, kmin, kmax, max_iter,
+    pf = int(p) if p_filter is None else int(p_filter)
+    _load().oracle_stability(g.n, g.rowptr, g.colidx, g.val, lam_max, p, pf, eta, Rc, J, R, kmin, kmax, max_iter,
                              int(starts), int(seed), gamma, lam_k)
     return gamma, lam_k
 

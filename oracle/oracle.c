@@ -686,9 +686,10 @@ int32_t oracle_stability_init_row(uint64_t seed, int32_t j, int32_t k, int32_t t
 }
 
 /* The stability measure of §4.3, Eq. (12), step by step: for every k in
- * [kmin, kmax], lam_k by the dichotomy of §3.2 on the count probes Rc (target
- * k - 1/2); for every realisation j of the eta signals (R_j, block j of R),
- * the filtered block at lam_k (Jackson-damped coefficients, order p), its
+ * [kmin, kmax], lam_k by the dichotomy of §3.2 (order p) on the count probes
+ * Rc (target k - 1/2); for every realisation j of the eta signals (R_j, block
+ * j of R), the filtered block at lam_k (Jackson-damped coefficients, order
+ * p_filter: the filters may use a higher order than the count), its
  * normalised rows rounded to FP32, and k-means (oracle_kmeans, max_iter) from
  * `starts` sets of rows that oracle_stability_init_row picks, keeping the
  * lowest inertia (the first on ties); gamma(k) = the mean adjusted Rand
@@ -697,16 +698,16 @@ int32_t oracle_stability_init_row(uint64_t seed, int32_t j, int32_t k, int32_t t
  * entries. Parity: its parts are pinned; the composition is checked on graphs
  * with a clear cluster structure (gamma = 1 at the true k). */
 void oracle_stability(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
-                      double lam_max, int32_t p, int64_t eta, const double *Rc, int32_t J, const double *R,
-                      int32_t kmin, int32_t kmax, int32_t max_iter, int32_t starts, uint64_t seed, double *gamma,
-                      double *lam_k) {
+                      double lam_max, int32_t p, int32_t p_filter, int64_t eta, const double *Rc, int32_t J,
+                      const double *R, int32_t kmin, int32_t kmax, int32_t max_iter, int32_t starts, uint64_t seed,
+                      double *gamma, double *lam_k) {
     const int32_t K = kmax - kmin + 1;
     const int64_t sz = (int64_t)n * eta;
-    double *a = (double *)malloc(sizeof(double) * (size_t)K * (size_t)(p + 1));
+    double *a = (double *)malloc(sizeof(double) * (size_t)K * (size_t)(p_filter + 1));
     for (int32_t q = 0; q < K; ++q) {
         lam_k[q] = oracle_dichotomy(n, rowptr, colidx, val, lam_max, p, 1, eta, Rc, (double)(kmin + q) - 0.5, 40,
                                     1e-9);
-        oracle_cheb_coeffs(lam_max, lam_k[q], p, 1, a + (int64_t)q * (p + 1));
+        oracle_cheb_coeffs(lam_max, lam_k[q], p_filter, 1, a + (int64_t)q * (p_filter + 1));
     }
     double *Y = (double *)malloc(sizeof(double) * (size_t)(K * sz > 0 ? K * sz : 1));
     double *Fd = (double *)malloc(sizeof(double) * (size_t)(sz > 0 ? sz : 1));
@@ -715,7 +716,7 @@ void oracle_stability(int32_t n, const int32_t *rowptr, const int32_t *colidx, c
     int32_t *labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)J * K * (size_t)(n > 0 ? n : 1));
     int32_t *trial = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int32_t j = 0; j < J; ++j) {
-        oracle_cheb_filter(n, rowptr, colidx, val, lam_max, K, p, a, eta, R + (int64_t)j * sz, Y);
+        oracle_cheb_filter(n, rowptr, colidx, val, lam_max, K, p_filter, a, eta, R + (int64_t)j * sz, Y);
         for (int32_t q = 0; q < K; ++q) {
             const int32_t k = kmin + q;
             oracle_features(n, eta, Y + (int64_t)q * sz, 1, Fd);

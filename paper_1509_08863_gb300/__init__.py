@@ -163,8 +163,8 @@ def lib():
         "sf_kmeans": (_i32, [_vp, _i32, _i32, _i32, _vp, _i32, _i32, _vp, C.POINTER(_i32), _dp, _vp]),
         "sf_graph_normalize": (_i32, [_vp, _vp, C.POINTER(_vp)]),
         "sf_adjusted_rand": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _dp]),
-        "sf_stability": (_i32, [_vp, _f64, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _i32, C.c_uint64, _vp, _vp,
-                                _dp, _dp]),
+        "sf_stability": (_i32, [_vp, _f64, _i32, _i32, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _i32, C.c_uint64, _vp,
+                                _vp, _dp, _dp, C.POINTER(_i32)]),
         "sf_cheb_order": (_i32, [_f64, _f64, _f64, _i32, _i32, C.POINTER(_i32)]),
         "sf_selftest_bounded_wait": (_i32, [_i32, _vp]),
         "sf_selftest_arrival_wait": (_i32, [_i32, _vp]),
@@ -588,20 +588,25 @@ def adjusted_rand(a, b, ka: int | None = None, kb: int | None = None) -> float:
 
 
 def stability(g: Graph, lam_max: float, p: int, Rc, R, kmin: int, kmax: int, max_iter: int = 50,
-              starts: int = 4, seed: int = 0, opts: Opts | None = None):
+              starts: int = 4, seed: int = 0, opts: Opts | None = None, p_filter: int | None = None,
+              return_order: bool = False):
     """gamma(k) of §4.3 / Eq. (12) for k = kmin..kmax and the lam_k used:
-    count probes Rc [N, eta], realisations R [J, N, eta] (FP32, on the device)."""
+    count probes Rc [N, eta], realisations R [J, N, eta] (FP32, on the device).
+    p: the count's order; p_filter: the filters' order (None: p; 0: the order
+    at which the filters of adjacent k differ). return_order adds the order used."""
     torch = _torch()
     J, n, eta = R.shape
     K = kmax - kmin + 1
     gamma = np.zeros(K)
     lam_k = np.zeros(K)
+    used = _i32()
     o, op = _opts_ptr(opts)
-    _check(lib().sf_stability(g.handle, float(lam_max), int(p), _dev_ptr(Rc, torch.float32, "Rc"),
+    pf = int(p) if p_filter is None else int(p_filter)
+    _check(lib().sf_stability(g.handle, float(lam_max), int(p), pf, _dev_ptr(Rc, torch.float32, "Rc"),
                               _dev_ptr(R, torch.float32, "R"), int(J), int(eta), int(kmin), int(kmax), int(max_iter),
                               int(starts), int(seed), op, _stream(), gamma.ctypes.data_as(_dp),
-                              lam_k.ctypes.data_as(_dp)), "sf_stability")
-    return gamma, lam_k
+                              lam_k.ctypes.data_as(_dp), C.byref(used)), "sf_stability")
+    return (gamma, lam_k, used.value) if return_order else (gamma, lam_k)
 
 
 def cheb_order(x: float, delta: float, w: float, jackson: bool = True, p_max: int = 1000) -> int:

@@ -70,3 +70,26 @@ def test_stability_matches_oracle(sf, oracle_mod):
     np.testing.assert_allclose(lk, lk_o, rtol=1e-3)
     np.testing.assert_allclose(gam, gam_o, atol=1e-9)
     assert int(np.argmax(gam)) == k - 2 and gam[k - 2] == pytest.approx(1.0)
+
+
+def test_stability_automatic_order_matches_oracle_at_that_order(sf, oracle_mod):
+    """p_filter = 0: the filters take the order that separates adjacent k
+    (their cutoffs' theta gap holds +-2 Jackson widths) while the count keeps
+    order p; gamma and lam_k equal the oracle's with the same two orders."""
+    k, m, eta, p, J = 4, 40, 12, 30, 3
+    n = k * m
+    src, dst, rng = _communities(k, m, 23)
+    go = oracle_mod.csr_build(n, src, dst)
+    g = sf.csr_build(n, torch.as_tensor(src, device="cuda"), torch.as_tensor(dst, device="cuda"), None)
+    lh = oracle_mod.lambda_hat(oracle_mod.lanczos_max(go, 60, rng.standard_normal(n)), oracle_mod.strength(go))
+    Rc = rng.standard_normal((n, eta)) / np.sqrt(eta)
+    Rs = [rng.standard_normal((n, eta)) / np.sqrt(eta) for _ in range(J)]
+    gam, lk, used = sf.stability(g, lh, p, torch.as_tensor(Rc, dtype=torch.float32, device="cuda"),
+                                 torch.as_tensor(np.stack(Rs), dtype=torch.float32, device="cuda"), 2, 6, 50, 8, 7,
+                                 p_filter=0, return_order=True)
+    assert used >= p
+    th = np.arccos(np.clip(2.0 * np.sort(lk) / lh - 1.0, -1.0, 1.0))
+    assert np.all(np.abs(np.diff(th)) * (used + 2) >= 4 * np.pi * (1 - 1e-9))  # the gaps inside [2, 6] resolved
+    gam_o, lk_o = oracle_mod.stability(go, lh, p, Rc, Rs, 2, 6, 50, 7, starts=8, p_filter=used)
+    np.testing.assert_allclose(lk, lk_o, rtol=1e-3)
+    np.testing.assert_allclose(gam, gam_o, atol=1e-9)

@@ -109,15 +109,19 @@ def test_stability_and_rand_argument_checks_without_gpu(sflib):
     lk = np.zeros(8)
     dp = C.POINTER(C.c_double)
 
-    def stab(J, kmin, kmax, max_iter, starts):
-        return L.sf_stability(fake, 10.0, 20, fake, fake, J, 8, kmin, kmax, max_iter, starts, 1, None, None,
-                              gam.ctypes.data_as(dp), lk.ctypes.data_as(dp))
+    used = C.c_int32(-7)
+
+    def stab(J, kmin, kmax, max_iter, starts, p_filter=20):
+        return L.sf_stability(fake, 10.0, 20, p_filter, fake, fake, J, 8, kmin, kmax, max_iter, starts, 1, None, None,
+                              gam.ctypes.data_as(dp), lk.ctypes.data_as(dp), C.byref(used))
 
     assert stab(1, 2, 4, 10, 2) == 1 and b"J >= 2" in L.sf_last_error()
     assert stab(3, 5, 4, 10, 2) == 1 and b"kmin" in L.sf_last_error()
     assert stab(3, 2, 4, 0, 2) == 1 and b"max_iter" in L.sf_last_error()
     assert stab(3, 2, 4, 10, 0) == 1 and b"starts" in L.sf_last_error()
-    assert np.all(gam == 0) and np.all(lk == 0)  # outputs untouched
+    assert stab(3, 2, 4, 10, 2, p_filter=-1) == 1 and b"p_filter" in L.sf_last_error()
+    assert stab(3, 2, 4, 10, 2, p_filter=20001) == 1 and b"p_filter" in L.sf_last_error()
+    assert np.all(gam == 0) and np.all(lk == 0) and used.value == -7  # outputs untouched
 
 
 def test_filter_and_moment_argument_checks_without_gpu(sflib):

@@ -670,6 +670,11 @@ def test_stability_peaks_at_the_true_number_of_clusters(oracle_mod):
     assert gamma[k - 2] == pytest.approx(1.0)
     assert np.argmax(gamma) == k - 2
     assert np.all(np.diff(lam_k) >= 0)  # more clusters, higher cutoff
+    # sharper filters (order 3p) at the same count cutoffs: the same cutoffs; the clusterings stay
+    # identical up to the true k and become unstable beyond it
+    gamma3, lam_k3 = oracle_mod.stability(g, lh, 60, Rc, Rs, 2, 6, 50, 7, starts=8, p_filter=180)
+    np.testing.assert_array_equal(lam_k3, lam_k)
+    assert gamma3[k - 2] == pytest.approx(1.0) and np.all(gamma3[k - 1:] < 1.0 - 1e-3)
     # the init rule is SplitMix64 (Steele, Lea and Flood 2014) of the packed counter, mod n
     z = (7 + (((1 << 40) | (3 << 20) | (5 << 10) | 2) + 1) * 0x9E3779B97F4A7C15) & (2**64 - 1)
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2**64 - 1)
