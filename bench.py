@@ -1174,6 +1174,7 @@ def other_configs(args, sf):
     for name, fn in (("sbm1k", lambda: config_sbm1k(sf, sub)), ("sbm100k", lambda: config_sbm100k(sf, sub)),
                      ("knn200k", lambda: run_knn_grad(sub, WORKLOADS["knn200k"])),
                      ("batch256", lambda: run_batch(sub, WORKLOADS["batch256"]))):
+        sub.workload = name  # each leg reads its own workload's profile figures
         t0 = time.perf_counter()
         try:
             out[name] = fn()
