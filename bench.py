@@ -296,11 +296,6 @@ def run_reference(args, wl):
     gr, R = make_inputs(wl)
     g = oracle.csr_build(wl["n"], gr.src, gr.dst, gr.w)
     lam = 2.0 * float(oracle.strength(g).max())
-    p_ref = 4 if wl["n"] >= 500_000 else max(1, min(wl["p"], 20))
-    a = oracle.cheb_coeffs(lam, 0.1 * lam, p_ref, True)
-    cols = min(8, wl["R"])
-    blk = np.ascontiguousarray(R[:, :cols])
-    units = (g.nnz + wl["n"]) * cols * p_ref
     try:  # the OpenMP build on every host core (identical results to the plain build)
         oracle.build_parallel()
         par = True
@@ -308,6 +303,12 @@ def run_reference(args, wl):
     except Exception:
         par = False
         threads = 1
+    # a bounded sample per step: every order on a few columns (all cores), or a few orders on one thread
+    p_ref = wl["p"] if par else (4 if wl["n"] >= 500_000 else max(1, min(wl["p"], 20)))
+    a = oracle.cheb_coeffs(lam, 0.1 * lam, p_ref, True)
+    cols = min(4 if wl["n"] >= 500_000 else 8, wl["R"])
+    blk = np.ascontiguousarray(R[:, :cols])
+    units = (g.nnz + wl["n"]) * cols * p_ref
     for _ in range(args.warmup):
         oracle.cheb_filter(g, lam, a, blk, parallel=par)
     ts = []
