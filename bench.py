@@ -77,7 +77,7 @@ def parse():
                     help="skip the other workloads' legs (sbm1k, sbm100k, knn200k, batch256) of the default run")
     ap.add_argument("--kernel-case", default=None,
                     help="profiling aid: MODE:STORAGE:SLAB:WARPS:CARVEOUT[:KERNEL] (MODE moments|clenshaw|forward|adjoint|"
-                         "kmeans|batched, STORAGE f32|bf16, KERNEL tiled|direct) runs two sweeps of --case-orders orders over one column slab of "
+                         "kmeans|batched, STORAGE f32|bf16, KERNEL tiled|direct|persistent) runs two sweeps of --case-orders orders over one column slab of "
                          "the workload and exits")
     ap.add_argument("--case-orders", type=int, default=6)
     ap.add_argument("--case-graphs", type=int, default=0,
@@ -100,7 +100,8 @@ def run_kernel_case(args, wl):
     sfbuild.build()
     fields = args.kernel_case.split(":")
     mode, stor, slab, warps, carve = fields[:5]
-    kind = {"tiled": sf.SWEEP_TILED, "direct": sf.SWEEP_DIRECT}[fields[5] if len(fields) > 5 else "tiled"]
+    kind = {"tiled": sf.SWEEP_TILED, "direct": sf.SWEEP_DIRECT,
+            "persistent": sf.SWEEP_PERSISTENT}[fields[5] if len(fields) > 5 else "tiled"]
     slab, warps, carve = int(slab), int(warps), int(carve)
     st = sf.BF16 if stor == "bf16" else sf.F32
     dev = torch.device("cuda")

@@ -106,6 +106,7 @@ __global__ void selftest_wait_kernel(int32_t polls, int32_t *status) {
 __global__ void selftest_arrival_kernel(int32_t polls, int32_t *status, uint32_t *counters, int32_t *tables) {
     BatchSched S = {};
     S.n_tiles = 1;
+    S.chunk = 1;
     S.n_chunks = 1;
     S.p = 2;
     S.chunk_glo = tables;       // chunk 0 covers graph 0 ...

@@ -547,7 +547,8 @@ __device__ __forceinline__ void sweep_row(const StepParams &P, const OrderView &
     const typename V::raw_t xi_r = ld_gathered<TS, COH>(X + ro);
     typename V::raw_t z_r = V::zero_raw();
     if (Z) {
-        if constexpr (COH) z_r = V::ld_raw_cg_once(Z + ro, l2_policy_evict_first());
+        // COH: T_{j-2} may still be gathered by tiles of the previous order, so no evict-first hint
+        if constexpr (COH) z_r = V::ld_raw_cg(Z + ro);
         else z_r = V::ld_raw_stream(Z + ro);
     }
     typename V::raw_t q_r = V::zero_raw();
@@ -827,7 +828,7 @@ __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepPara
 // ------------------------------------------------------------ persistent batch
 // One launch filters a batch of graphs through all p orders. Work item
 // i = s * n_chunks + c is order step s (forward: order s + 1; Clenshaw:
-// index j = p - 1 - s) of chunk c, kBatchChunk consecutive tiles. Blocks claim
+// index j = p - 1 - s) of chunk c, `chunk` consecutive tiles. Blocks claim
 // items from a global counter in increasing order, and an item may start once
 // every graph its chunk covers has completed step s - 1 on all of that
 // graph's chunks (per-graph arrival counters). Every item an item waits for
@@ -836,11 +837,15 @@ __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepPara
 // to its next order as soon as its own chunks are done, without waiting for
 // the rest of the batch. Each wait is bounded; one that gives up sets the
 // status word and an abort flag that makes every other wait give up at once.
-constexpr int kBatchChunk = 8;  // tiles per work item
+// The thread that claims an item polls its counters once; when they are
+// already complete the item's first tile arrives marked ready and the warps
+// skip their own wait.
+constexpr int kBatchChunk = 8;  // most tiles per work item
 
 struct BatchSched {
     int32_t n_tiles;
-    int32_t n_chunks;             // ceil(n_tiles / kBatchChunk)
+    int32_t chunk;                // tiles per work item, 1..kBatchChunk
+    int32_t n_chunks;             // ceil(n_tiles / chunk)
     int32_t p;                    // orders: the launch runs p steps
     const int32_t *chunk_glo;     // [n_chunks] lowest graph id among the chunk's rows
     const int32_t *chunk_ghi;     // [n_chunks] highest graph id among the chunk's rows
@@ -895,6 +900,15 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 
 constexpr uint32_t kDepPolls = 1u << 20;  // with a 128 ns sleep between polls: about a second
 
+// One poll: has every graph of chunk c completed step s - 1?
+__device__ __forceinline__ bool graph_deps_done(const BatchSched &S, int s, int c) {
+    if (s == 0) return true;
+    const int g0 = __ldg(S.chunk_glo + c), g1 = __ldg(S.chunk_ghi + c);
+    for (int g = g0; g <= g1; ++g)
+        if (ld_acquire_u32(S.done + g) < (uint32_t)s * __ldg(S.graph_chunks + g)) return false;
+    return true;
+}
+
 // Waits (at most `polls` polls per graph) until every graph of chunk c has
 // completed step s - 1.
 __device__ __forceinline__ bool wait_graph_deps(const BatchSched &S, int s, int c, uint32_t polls = kDepPolls) {
@@ -922,8 +936,13 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
 
 // The block's tiles form a sequence (the tiles of its items in claim order);
 // the two stages hold consecutive positions of it. s_pos[b] = (item, tile of
-// the item) staged in stage b (item -1: the queue is exhausted); s_cur = the
-// next position to stage.
+// the item, ready) staged in stage b (item -1: the queue is exhausted); s_cur
+// = the next position to stage. The next item is claimed, and its counters
+// polled once, right after the copy of the current item's last tile is
+// issued (s_next = item, ready), so neither round trip delays a stage.
+// ready: the item's dependencies were complete when polled; the polling
+// thread's acquire reaches the warps through the stage counters' CTA fences
+// and the stage mbarrier's release/acquire.
 template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, const BatchSched S) {
     using C = TileCfg<LPR>;
@@ -933,11 +952,12 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
     int32_t *s_meta = reinterpret_cast<int32_t *>(smem_raw + 32);  // [NST][2]: entry base, fits
     int32_t *s_cnt = s_meta + 2 * NST;                              // [NST] warps done with the stage's tile
     int32_t *s_iss = s_cnt + NST;                                   // [NST] phases started on the stage
-    int32_t *s_pos = s_iss + NST;                                   // [NST][2]: item, tile of the item
-    int32_t *s_cur = s_pos + 2 * NST;                               // [2]: the next position to stage
+    int32_t *s_pos = s_iss + NST;                                   // [NST][3]: item, tile of the item, ready
+    int32_t *s_cur = s_pos + 3 * NST;                               // [2]: the next position to stage
+    int32_t *s_next = s_cur + 2;                                    // [2]: the claimed next item, ready
     unsigned char *s_buf0 = smem_raw + C::header;
     constexpr int buf_bytes = C::buf_bytes(W);
-    static_assert(32 + 7 * NST * 4 + 8 <= C::header, "stage header");
+    static_assert(32 + 8 * NST * 4 + 16 <= C::header, "stage header");
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int q = tid % LPR, grp = tid / LPR;
@@ -948,28 +968,38 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
 
     // tiles of chunk c
     auto chunk_tiles = [&](int c) {
-        const int t0 = c * kBatchChunk;
-        return (S.n_tiles - t0) < kBatchChunk ? (S.n_tiles - t0) : kBatchChunk;
+        const int t0 = c * S.chunk;
+        return (S.n_tiles - t0) < S.chunk ? (S.n_tiles - t0) : S.chunk;
     };
-    // one thread: claim a new item when the current one is used up, then stage
-    // the sequence's next tile into stage b (or mark the stage exhausted)
+    // one thread: claim the next item and poll its dependencies once
+    auto claim_next = [&]() {
+        const int it = (int)atomicAdd(S.queue, 1u);
+        const int item = (it < total) ? it : -1;
+        s_next[0] = item;
+        s_next[1] = (item >= 0 && graph_deps_done(S, item / S.n_chunks, item % S.n_chunks)) ? 1 : 0;
+    };
+    // one thread: stage the sequence's next tile into stage b (or mark the
+    // stage exhausted), moving to the claimed item when the current one is
+    // used up; after the copy of an item's last tile, claim the next item
     auto stage_next = [&](int b) {
         int item = s_cur[0], k = s_cur[1];
+        int ready = 1;
         if (item < 0 || k >= chunk_tiles(item % S.n_chunks)) {
-            const int it = (int)atomicAdd(S.queue, 1u);
-            item = (it < total) ? it : -1;
+            item = s_next[0];
+            ready = s_next[1];
             k = 0;
         }
         s_cur[0] = item;
         s_cur[1] = k + 1;
-        s_pos[2 * b] = item;
-        s_pos[2 * b + 1] = k;
+        s_pos[3 * b] = item;
+        s_pos[3 * b + 1] = k;
+        s_pos[3 * b + 2] = ready;
         s_iss[b] += 1;
         if (item < 0) {
             mbar_arrive(&s_bar[b]);
             return;
         }
-        const int tile = (item % S.n_chunks) * kBatchChunk + k;
+        const int tile = (item % S.n_chunks) * S.chunk + k;
         unsigned char *base = s_buf0 + b * buf_bytes;
         int32_t *sp = reinterpret_cast<int32_t *>(base);
         int32_t *ix = sp + 2 * C::sp_ints;
@@ -994,6 +1024,7 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
                 if (W) bulk_g2s(wv, P.sell_val + e0, cnt * 4, &s_bar[b]);
             }
         }
+        if (k + 1 >= chunk_tiles(item % S.n_chunks)) claim_next();
     };
 
     if (tid == 0) {
@@ -1005,6 +1036,7 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
         s_cur[0] = -1;
         s_cur[1] = 0;
         fence_mbar_init();
+        claim_next();
         for (int b = 0; b < NST; ++b) stage_next(b);
     }
     __syncthreads();
@@ -1018,11 +1050,11 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
             }
             break;
         }
-        const int item = s_pos[2 * b], kt = s_pos[2 * b + 1];
+        const int item = s_pos[3 * b], kt = s_pos[3 * b + 1];
         if (item < 0) break;  // the queue is exhausted
         const int s = item / S.n_chunks, c = item % S.n_chunks;
-        const int tile = c * kBatchChunk + kt;
-        if (kt == 0) {  // the item's first tile: its graphs must have finished the previous step
+        const int tile = c * S.chunk + kt;
+        if (kt == 0 && !s_pos[3 * b + 2]) {  // the item's first tile: its graphs must have finished the previous step
             bool ok = true;
             if (lane == 0) {
                 ok = wait_graph_deps(S, s, c);
