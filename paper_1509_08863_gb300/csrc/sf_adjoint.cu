@@ -322,7 +322,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
         if ((st = check_launch("dtil_kernel"))) return st;
     }
     const float *val = g->unit_weights ? nullptr : g->val;
-    const int pack_grid = 2 * sm_count();
+    const int pack_grid = kPackBlocksPerSm * sm_count();
     const double two_over_lam = 2.0 / lam_max;
     const int n_slabs = (n_sig + ld - 1) / ld;
 

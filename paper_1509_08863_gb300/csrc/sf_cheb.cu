@@ -3,6 +3,7 @@
 // sweep behind the eigenvalue count, batched graphs, and the tile autotuner.
 #include <math.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -327,7 +328,9 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
     }
     uint32_t *done = nullptr;
     if (mode == MODE_MOM) {
-        if ((st = sc.get(&part, (size_t)2 * sh.grid + 2)) || (st = sc.get(&done, 1))) return st;
+        // the sweep's block partials (2 per block) and the pack kernel's (1 per block)
+        const size_t n_part = std::max((size_t)2 * sh.grid + 2, (size_t)kPackBlocksPerSm * sm_count());
+        if ((st = sc.get(&part, n_part)) || (st = sc.get(&done, 1))) return st;
         SF_CHECK_CUDA(cudaMemsetAsync(done, 0, sizeof(uint32_t), s));
     }
     // FP16 blocks: each slab is scaled by a power of two so that its largest
@@ -353,7 +356,7 @@ static sf_status run_sweeps(const GraphView &G, const double *two_over_lam_g, do
                                                                    tol, dtil, wscale, perm, gid_t);
         if ((st = check_launch("dtil_kernel"))) return st;
     }
-    const int pack_grid = 2 * sm_count();
+    const int pack_grid = kPackBlocksPerSm * sm_count();
     const int n_slabs = (n_sig + ld - 1) / ld;
     for (int c0 = 0; c0 < n_sig; c0 += ld) {
         const int w = (n_sig - c0) < ld ? (n_sig - c0) : ld;

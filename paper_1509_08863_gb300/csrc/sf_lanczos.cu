@@ -134,9 +134,11 @@ __global__ void sumsq_kernel(int32_t n, const double *v, double *part) {
 }
 
 // ------------------------------------------------------------ features
-// One warp per row: per-lane FP32 partial sums of squares combined in FP64,
-// then scale by the FP32-rounded 1/norm; rows of zero norm are written as
-// zeros.
+// One warp per row, in FP32: the row is first scaled by the power of two that
+// brings its largest magnitude into [1/2, 1) (exact), so that the sum of
+// squares neither underflows nor overflows; F = y * (scale / sqrt(sum)).
+// Rows of zero norm are written as zeros (rows with an infinite or NaN entry
+// as y * 0).
 __global__ void __launch_bounds__(256) features_kernel(const float *Y, int32_t n, int32_t n_sig, int32_t normalize,
                                                        float *F) {
     const int lane = threadIdx.x & 31;
@@ -149,13 +151,24 @@ __global__ void __launch_bounds__(256) features_kernel(const float *Y, int32_t n
             for (int c = lane; c < n_sig; c += 32) f[c] = y[c];
             continue;
         }
-        float part = 0.f;
-        for (int c = lane; c < n_sig; c += 32) part = fmaf(y[c], y[c], part);
-        double ss = (double)part;
+        float m = 0.f;
+        for (int c = lane; c < n_sig; c += 32) m = fmaxf(m, fabsf(y[c]));
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-        const double nrm = sqrt(ss);
-        const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        float inv = 0.f;
+        if (m > 0.f && m <= 3.4028235e38f) {
+            int e;
+            frexpf(m, &e);                                        // m = fr * 2^e, fr in [1/2, 1)
+            const float sc = ldexpf(1.0f, e < -125 ? 125 : -e);  // exact power of two
+            float ss = 0.f;
+            for (int c = lane; c < n_sig; c += 32) {
+                const float v = y[c] * sc;
+                ss = fmaf(v, v, ss);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+            if (ss > 0.f && ss <= 3.4028235e38f) inv = sc / sqrtf(ss);
+        }
         for (int c = lane; c < n_sig; c += 32) f[c] = y[c] * inv;
     }
 }

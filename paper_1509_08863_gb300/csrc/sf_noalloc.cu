@@ -89,7 +89,7 @@ extern "C" SF_API sf_status sf_cheb_moments_noalloc(const sf_graph *g, double la
     const int64_t rows = g->sell.rows;
     const int32_t *perm = g->sell.perm;
     const bool weighted = !g->unit_weights;
-    const int pack_grid = 2 * sm_count();
+    const int pack_grid = kPackBlocksPerSm * sm_count();
     // The slab sf_cheb_moments picks by default, halved (down to 8 columns) until
     // the working memory fits the array: the size limit is monotone in N.
     int ld = auto_slab_cols(n, n_sig, SF_F32, 32ll << 20);

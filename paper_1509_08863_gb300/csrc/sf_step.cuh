@@ -1115,69 +1115,118 @@ __global__ void __launch_bounds__(256, 4) cheb_batch_kernel(const StepParams P, 
 // to ld columns). Optionally: Y_c = a_c0 * T0 (forward, rows [0, rows)),
 // b_p = a_p * T0 (Clenshaw start, written to `bstart`), and per-block
 // partial sum of T0.T0 (moments). gid is indexed by graph row.
+//
+// Elements are taken in block order, kPackUnroll per lane per pass (their
+// loads issued together, so that a pass keeps that many reads in flight); a
+// warp's 32 x kPackUnroll elements are summed in FP32, then in FP64 across
+// passes and warps in a fixed order. ld is a power of two.
+constexpr int kPackUnroll = 8;
+constexpr int kPackBlocksPerSm = 8;  // pack/unpack grids: kPackBlocksPerSm x SMs blocks of 256 threads
+
 template <typename TS>
-__global__ void pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0, int32_t w,
-                            int32_t ld, TS *T0, float *Y, int64_t ystride, int32_t n_cut, const float *coef,
-                            int32_t coef_ld, int32_t jcoef, const int32_t *gid, TS *bstart, double *part,
-                            const uint32_t *maxbits, const int32_t *perm, int32_t rows) {
-    __shared__ double red[256];
+__global__ void __launch_bounds__(256) pack_kernel(const void *R, int r_dtype, int32_t n, int32_t n_sig, int32_t c0,
+                                                   int32_t w, int32_t ld, TS *T0, float *Y, int64_t ystride,
+                                                   int32_t n_cut, const float *coef, int32_t coef_ld, int32_t jcoef,
+                                                   const int32_t *gid, TS *bstart, double *part,
+                                                   const uint32_t *maxbits, const int32_t *perm, int32_t rows) {
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31;
+    const int lg = __ffs(ld) - 1;
     const int64_t total = (int64_t)(rows + 1) * ld;
     const float scale = block_scale(maxbits);
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int64_t kSpan = 32 * kPackUnroll;
     double acc = 0.0;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = idx / ld;
-        const int32_t c = (int32_t)(idx - t * ld);
-        const int32_t i = (t < rows) ? perm[t] : -1;
-        float x = 0.f;
-        if (i >= 0 && c < w) {
-            const int64_t src = (int64_t)i * n_sig + c0 + c;
-            x = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
-                                     : static_cast<const float *>(R)[src];
-            x *= scale;
-        }
-        T0[idx] = VT<TS>::cvt(x);
-        const float xr = VT<TS>::rt(x);
-        acc += (double)xr * (double)xr;
-        if (t == rows) continue;  // the zero row of the gathered block
-        const int g = (gid && i >= 0) ? gid[i] : 0;
-        if (Y) {
-            for (int k = 0; k < n_cut; ++k) {
-                const float a = coef[((int64_t)g * n_cut + k) * coef_ld + jcoef];
-                Y[k * ystride + idx] = a * xr;
+    for (int64_t base = warp0 * kSpan; base < total; base += nwarps * kSpan) {
+        float x[kPackUnroll];
+        int32_t iv[kPackUnroll];
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t idx = base + u * 32 + lane;
+            const int64_t t = idx >> lg;
+            const int32_t c = (int32_t)(idx & (ld - 1));
+            const int32_t i = (idx < total && t < rows) ? __ldg(perm + t) : -1;
+            iv[u] = i;
+            x[u] = 0.f;
+            if (i >= 0 && c < w) {
+                const int64_t src = (int64_t)i * n_sig + c0 + c;
+                x[u] = (r_dtype == SF_BF16) ? __bfloat162float(static_cast<const __nv_bfloat16 *>(R)[src])
+                                            : __ldg(static_cast<const float *>(R) + src);
             }
         }
-        if (bstart) {
-            const float a = coef[(int64_t)g * coef_ld + jcoef];
-            bstart[idx] = VT<TS>::cvt(a * xr);
+        float ss = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t idx = base + u * 32 + lane;
+            if (idx >= total) continue;
+            const float xs = x[u] * scale;
+            T0[idx] = VT<TS>::cvt(xs);
+            const float xr = VT<TS>::rt(xs);
+            ss = fmaf(xr, xr, ss);
+            if ((idx >> lg) == rows) continue;  // the zero row of the gathered block
+            const int32_t i = iv[u];
+            const int g = (gid && i >= 0) ? __ldg(gid + i) : 0;
+            if (Y) {
+                for (int k = 0; k < n_cut; ++k) {
+                    const float a = __ldg(coef + ((int64_t)g * n_cut + k) * coef_ld + jcoef);
+                    Y[k * ystride + idx] = a * xr;
+                }
+            }
+            if (bstart) {
+                const float a = __ldg(coef + (int64_t)g * coef_ld + jcoef);
+                bstart[idx] = VT<TS>::cvt(a * xr);
+            }
+        }
+        if (part) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+            acc += (double)ss;  // the same in every lane
         }
     }
     if (part) {
-        red[threadIdx.x] = acc;
+        if (lane == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sum += red[k];
+            part[blockIdx.x] = sum;
         }
-        if (threadIdx.x == 0) part[blockIdx.x] = red[0];
     }
 }
 
-// Y_out[c][perm[t]][c0 + col] = Yslab[c][t][col] for col < w and graph rows t.
-static __global__ void unpack_kernel(const float *Yslab, int32_t n, int32_t ld, int32_t w, int32_t n_cut,
-                                     float *Y, int32_t n_sig, int32_t c0, const uint32_t *maxbits,
-                                     const int32_t *perm, int32_t rows) {
-    const int64_t total = (int64_t)n_cut * rows * w;
+// Y_out[c][perm[t]][c0 + col] = Yslab[c][t][col] for col < w and graph rows t
+// (kPackUnroll elements per lane per pass, in block order; ld a power of two).
+static __global__ void __launch_bounds__(256) unpack_kernel(const float *Yslab, int32_t n, int32_t ld, int32_t w,
+                                                            int32_t n_cut, float *Y, int32_t n_sig, int32_t c0,
+                                                            const uint32_t *maxbits, const int32_t *perm,
+                                                            int32_t rows) {
+    const int lane = threadIdx.x & 31;
+    const int lg = __ffs(ld) - 1;
+    const int64_t per_cut = (int64_t)rows * ld;
     const float inv = 1.0f / block_scale(maxbits);  // exact: a power of two
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t cc = idx / ((int64_t)rows * w);
-        const int64_t rem = idx - cc * rows * w;
-        const int64_t t = rem / w;
-        const int32_t col = (int32_t)(rem - t * w);
-        const int32_t i = perm[t];
-        if (i < 0) continue;
-        Y[(cc * n + i) * n_sig + c0 + col] = __ldcs(Yslab + (cc * rows + t) * ld + col) * inv;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int64_t kSpan = 32 * kPackUnroll;
+    for (int32_t cc = 0; cc < n_cut; ++cc) {
+        const float *src = Yslab + cc * per_cut;
+        float *dst = Y + (int64_t)cc * n * n_sig + c0;
+        for (int64_t base = warp0 * kSpan; base < per_cut; base += nwarps * kSpan) {
+            float v[kPackUnroll];
+            int32_t iv[kPackUnroll];
+#pragma unroll
+            for (int u = 0; u < kPackUnroll; ++u) {
+                const int64_t idx = base + u * 32 + lane;
+                const int32_t c = (int32_t)(idx & (ld - 1));
+                iv[u] = (idx < per_cut && c < w) ? __ldg(perm + (idx >> lg)) : -1;
+                v[u] = iv[u] >= 0 ? __ldcs(src + idx) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kPackUnroll; ++u) {
+                const int64_t idx = base + u * 32 + lane;
+                if (iv[u] >= 0) dst[(int64_t)iv[u] * n_sig + (idx & (ld - 1))] = v[u] * inv;
+            }
+        }
     }
 }
 

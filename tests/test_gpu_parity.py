@@ -683,6 +683,34 @@ def test_batched_persistent_equals_per_order_launches(sf, oracle_mod):
             assert rel(Yc[c][sl].cpu().numpy(), Yo[c]) <= 1e-5, (i, c)
 
 
+@pytest.mark.parametrize("n_graphs,n_lo,n_hi", [(40, 3000, 8000), (60, 4000, 8000), (60, 8000, 16000)])
+def test_batched_persistent_multi_tile_items(sf, n_graphs, n_lo, n_hi):
+    """Batches of about 220k, 380k and 760k rows, large enough that the
+    persistent sweep's work items hold several tiles (its claim of the next
+    item and the counter poll then happen mid-item): bit-identical to one
+    launch per order, forward with two cutoffs in BF16 and Clenshaw in FP32."""
+    from paper_1509_08863_gb300 import synth
+
+    graphs, _ = synth.batched_sbm(n_graphs, 777 + n_graphs, n_lo=n_lo, n_hi=n_hi, d_lo=8.0, d_hi=16.0)
+    dev = torch.device("cuda")
+    gs = [sf.csr_build(gr.n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+          for gr in graphs]
+    # 2 max_i s_i bounds lambda_N (unit weights: s_i <= the edge list's count of i as either endpoint)
+    lams = [2.0 * float((np.bincount(gr.src, minlength=gr.n) + np.bincount(gr.dst, minlength=gr.n)).max())
+            for gr in graphs]
+    b = sf.batch_build(gs)
+    n_tot = b.info()[0]
+    p = 12
+    coeffs2 = np.stack([np.stack([sf.cheb_coeffs(lams[i], c * lams[i], p, True)[0] for c in (0.05, 0.2)])
+                        for i in range(len(gs))])
+    R = torch.randn(n_tot, 32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(n_graphs))
+    for st, algo in ((sf.BF16, sf.ALGO_FORWARD), (sf.F32, sf.ALGO_CLENSHAW)):
+        outs = [sf.cheb_filter_batched_multi(b, lams, coeffs2, R, sf.Opts(storage=st, algo=algo, sweep_kernel=kind))
+                for kind in (sf.SWEEP_TILED, sf.SWEEP_PERSISTENT)]
+        sf.device_check()
+        assert torch.equal(outs[0], outs[1]), (st, algo)
+
+
 def test_batched_persistent_under_cuda_graph(sf, oracle_mod):
     graphs, gs, gos, lams, b = _small_batch(sf, oracle_mod, 6, seed=321)
     n_tot = b.info()[0]
