@@ -417,20 +417,25 @@ SF_API sf_status sf_cheb_filter_batched_multi(const sf_batch *b, const double *l
 /*
  * sf_cheb_moments without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
- * device memory when they need the moments -- code running while a stream
- * is captured into a CUDA graph, frameworks whose own caching allocator owns
- * all device memory, latency-bound loops that cannot afford an allocator
- * call. Its working memory is one fixed 64 MiB array in the library's device
- * image, held by every GPU that loads the library until the process exits.
+ * device memory when they need the moments -- frameworks whose own caching
+ * allocator owns all device memory and forbids foreign allocations, and
+ * latency-bound loops that cannot afford an allocator call (cudaFree
+ * synchronises the device). Its working memory is one fixed 64 MiB array in
+ * the library's device image, held by every GPU that loads the library until
+ * the process exits.
  *   R        device float[N][n_sig] (FP32 signals; blocks are FP32)
- *   moments  host double[2p + 1], same values as sf_cheb_moments with default
- *            options
+ *   moments  host double[2p + 1]: the moments of sf_cheb_moments, equal to
+ *            that entry point's within the FP64 reduction-order tolerance
+ *            (the two may cut the block into different column slabs)
  * Requirements and behaviour:
  *   - the graph must already have its sweep layout, which the first
  *     sf_cheb_moments / sf_cheb_filter / sf_autotune call on it builds
  *     (SF_ERR_ARG otherwise);
- *   - SF_ERR_ARG when the working memory, about 3 (N + 1) * 16 * 4 bytes plus
- *     small tables, exceeds 64 MiB (roughly N > 340,000 for n_sig >= 16);
+ *   - the column slab halves (down to 8 columns) until three FP32 blocks of
+ *     the graph and the small tables fit the array; SF_ERR_ARG beyond that,
+ *     about 670,000 rows for moderate p (the limit does not depend on n_sig);
+ *   - the same finiteness and growth checks as sf_cheb_moments
+ *     (SF_ERR_NUMERIC for non-finite signals or lam_max below the spectrum);
  *   - the first call on a device looks up the array's address; make that
  *     call before any stream capture;
  *   - calls share the array: calls whose GPU work can overlap (unordered
