@@ -651,7 +651,18 @@ def main():
         gather = {"rows_per_s": rps, "row_bytes": rb, "table_rows": n, "deg": deg,
                   "launch_ms_at_ceiling": at_ceiling,
                   "frac_of_ceiling": {name: at_ceiling / v["avg_launch_ms"] for name, v in by_variant.items()},
-                  "note": "sf_gather_ceiling: the sweep's random-row gathers alone (nnz_off rows per launch)"}
+                  "note": "sf_gather_ceiling: the sweep's random-row gathers with each row's sums written back "
+                          "(nnz_off rows per launch)"}
+        # the gathers with nothing else in flight (one float written per row): the bound any kernel that
+        # gathers these rows meets, and the HBM fraction of the algorithmic bytes it allows
+        rps0 = sf.gather_rate(n, rb, deg, 10, write_rows=False)
+        at0 = nnz / rps0 * 1e3
+        gather["gathers_alone"] = {
+            "rows_per_s": rps0, "launch_ms": at0,
+            "frac_of_rate": {name: at0 / v["avg_launch_ms"] for name, v in by_variant.items()},
+            "roofline_frac_bound": {name: v["bytes_per_launch"] / (at0 * 1e-3) / 1e9 / v["peak"]
+                                    for name, v in by_variant.items() if v.get("bytes_per_launch")},
+            "note": "sf_gather_rate(write_rows=0)"}
 
     result = {
         "metric": "filtered nnz*R*p updates/s",

@@ -638,6 +638,17 @@ SF_API sf_status sf_selftest_arrival_wait(int32_t polls, void *stream);
 SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps, void *stream,
                                    double *rows_per_s);
 
+/*
+ * sf_gather_ceiling with the write-back made optional (a diagnostic with no
+ * counterpart in the paper). write_rows != 0 is sf_gather_ceiling itself;
+ * write_rows == 0 writes one float per output row instead of the row's sums,
+ * so the timing is that of the random-row gathers (and their index reads)
+ * alone: the rate the memory system sustains for the pattern with nothing
+ * else in flight. Arguments, buffers and errors as for sf_gather_ceiling.
+ */
+SF_API sf_status sf_gather_rate(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps, int32_t write_rows,
+                                void *stream, double *rows_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -169,6 +169,7 @@ def lib():
         "sf_selftest_bounded_wait": (_i32, [_i32, _vp]),
         "sf_selftest_arrival_wait": (_i32, [_i32, _vp]),
         "sf_gather_ceiling": (_i32, [_i64, _i32, _i32, _i32, _vp, _dp]),
+        "sf_gather_rate": (_i32, [_i64, _i32, _i32, _i32, _i32, _vp, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -618,11 +619,20 @@ def cheb_order(x: float, delta: float, w: float, jackson: bool = True, p_max: in
 
 
 def gather_ceiling(n_rows: int, row_bytes: int, deg: int, reps: int = 10) -> float:
-    """Rows per second of the sweep's random-row gather pattern alone (synthetic
-    BF16 table of n_rows + 1 rows of row_bytes bytes, deg entries per row)."""
+    """Rows per second of the sweep's random-row gather pattern with each output
+    row's sums written back (synthetic BF16 table of n_rows + 1 rows of
+    row_bytes bytes, deg entries per row)."""
     r = _f64()
     _check(lib().sf_gather_ceiling(int(n_rows), int(row_bytes), int(deg), int(reps), _stream(), C.byref(r)),
            "sf_gather_ceiling")
+    return r.value
+
+
+def gather_rate(n_rows: int, row_bytes: int, deg: int, reps: int = 10, write_rows: bool = False) -> float:
+    """Rows per second of the same pattern; without write_rows, the gathers alone."""
+    r = _f64()
+    _check(lib().sf_gather_rate(int(n_rows), int(row_bytes), int(deg), int(reps), int(bool(write_rows)), _stream(),
+                                C.byref(r)), "sf_gather_rate")
     return r.value
 
 

@@ -39,7 +39,9 @@ __device__ __forceinline__ void probe_add(float (&acc)[8], const uint4 v) {
     }
 }
 
-template <int LPR>
+// WROW: each output row's FP32 sums written back (as a sweep writes T_j);
+// else one float per row (the gathers alone).
+template <int LPR, bool WROW>
 __global__ void __launch_bounds__(256, 4) probe_gather_kernel(const uint16_t *T, const int32_t *idx, int64_t n_out,
                                                               int32_t deg, float *out) {
     constexpr int COLS = LPR * 8;  // BF16 columns per row
@@ -72,16 +74,24 @@ __global__ void __launch_bounds__(256, 4) probe_gather_kernel(const uint16_t *T,
 #pragma unroll
             for (int u = 0; u < 4; ++u) probe_add(acc, x[u]);
         }
-        float4 *o = reinterpret_cast<float4 *>(out + row * COLS + q * 8);
-        __stcs(o, make_float4(acc[0], acc[1], acc[2], acc[3]));
-        __stcs(o + 1, make_float4(acc[4], acc[5], acc[6], acc[7]));
+        if (WROW) {
+            float4 *o = reinterpret_cast<float4 *>(out + row * COLS + q * 8);
+            __stcs(o, make_float4(acc[0], acc[1], acc[2], acc[3]));
+            __stcs(o + 1, make_float4(acc[4], acc[5], acc[6], acc[7]));
+        } else {
+            float t = 0.f;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) t += acc[v];
+            if (q == 0) out[row] = t;
+        }
     }
 }
 
 template <int LPR>
 static void probe_launch(int grid, cudaStream_t s, const uint16_t *T, const int32_t *idx, int64_t n, int32_t deg,
-                         float *out) {
-    probe_gather_kernel<LPR><<<grid, 256, 0, s>>>(T, idx, n, deg, out);
+                         float *out, bool write_rows) {
+    if (write_rows) probe_gather_kernel<LPR, true><<<grid, 256, 0, s>>>(T, idx, n, deg, out);
+    else probe_gather_kernel<LPR, false><<<grid, 256, 0, s>>>(T, idx, n, deg, out);
 }
 
 // One block waits on an mbarrier that nothing ever completes, with the same
@@ -152,8 +162,8 @@ extern "C" SF_API sf_status sf_selftest_bounded_wait(int32_t polls, void *stream
     return check_launch("selftest_wait_kernel");
 }
 
-extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps,
-                                              void *stream, double *rows_per_s) {
+static sf_status gather_rate(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps, bool write_rows,
+                             void *stream, double *rows_per_s) {
     SF_ARG(rows_per_s, "rows_per_s is NULL");
     SF_ARG(n_rows >= 1 && n_rows <= (1ll << 31) - 2, "n_rows must be in [1, 2^31 - 2]");
     SF_ARG(row_bytes == 32 || row_bytes == 64 || row_bytes == 128 || row_bytes == 256,
@@ -178,10 +188,10 @@ extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes,
     const int grid = 4 * sm_count();
     auto launch = [&]() {
         switch (row_bytes) {
-            case 32: probe_launch<2>(grid, s, T, idx, n_rows, deg, out); break;
-            case 64: probe_launch<4>(grid, s, T, idx, n_rows, deg, out); break;
-            case 128: probe_launch<8>(grid, s, T, idx, n_rows, deg, out); break;
-            default: probe_launch<16>(grid, s, T, idx, n_rows, deg, out); break;
+            case 32: probe_launch<2>(grid, s, T, idx, n_rows, deg, out, write_rows); break;
+            case 64: probe_launch<4>(grid, s, T, idx, n_rows, deg, out, write_rows); break;
+            case 128: probe_launch<8>(grid, s, T, idx, n_rows, deg, out, write_rows); break;
+            default: probe_launch<16>(grid, s, T, idx, n_rows, deg, out, write_rows); break;
         }
         return check_launch("probe_gather_kernel");
     };
@@ -205,4 +215,14 @@ extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes,
     if (e != cudaSuccess) return cuda_fail(e, "timing the gather ceiling");
     *rows_per_s = (double)n_rows * deg * reps / ((double)ms * 1e-3);
     return SF_OK;
+}
+
+extern "C" SF_API sf_status sf_gather_ceiling(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps,
+                                              void *stream, double *rows_per_s) {
+    return gather_rate(n_rows, row_bytes, deg, reps, true, stream, rows_per_s);
+}
+
+extern "C" SF_API sf_status sf_gather_rate(int64_t n_rows, int32_t row_bytes, int32_t deg, int32_t reps,
+                                           int32_t write_rows, void *stream, double *rows_per_s) {
+    return gather_rate(n_rows, row_bytes, deg, reps, write_rows != 0, stream, rows_per_s);
 }

@@ -575,9 +575,13 @@ def test_autotune_and_profile(sf, oracle_mod):
 def test_gather_ceiling_diagnostic(sf):
     r = sf.gather_ceiling(100_000, 64, 32, 2)
     assert np.isfinite(r) and r > 1e9  # rows per second
+    r0 = sf.gather_rate(100_000, 64, 32, 2, write_rows=False)
+    assert np.isfinite(r0) and r0 > 1e9
     for bad in ((0, 64, 32), (1000, 48, 32), (1000, 64, 30), (1000, 64, 0)):
         with pytest.raises(sf.SpecFiltError):
             sf.gather_ceiling(*bad, 1)
+        with pytest.raises(sf.SpecFiltError):
+            sf.gather_rate(*bad, 1, write_rows=False)
 
 
 def test_normalized_laplacian_matches_oracle(sf, oracle_mod):
