@@ -643,15 +643,41 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32(int nmma) {
 // x = hi + lo + r with hi = x rounded to TF32 (nearest, ties away from
 // zero), lo = (x - hi) rounded to TF32 (x - hi is exact in FP32), so
 // |r| <= 2^-11 |x - hi| <= 2^-22 |x|.
+__device__ __forceinline__ void km_split1(float v, float &h, float &l) {
+    uint32_t a, b;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(a) : "f"(v));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(__fsub_rn(v, __uint_as_float(a))));
+    h = __uint_as_float(a);
+    l = __uint_as_float(b);
+}
+
+// 16-byte loads and stores (four independent ones per thread in flight) when
+// the three arrays are 16-byte aligned; the remainder one element at a time.
 __global__ void km_split_tf32_kernel(const float *x, int64_t count, float *hi, float *lo) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = x[i];
-        uint32_t h, l;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fsub_rn(v, __uint_as_float(h))));
-        hi[i] = __uint_as_float(h);
-        lo[i] = __uint_as_float(l);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const bool vec = (((uintptr_t)x | (uintptr_t)hi | (uintptr_t)lo) & 15u) == 0;
+    const int64_t nv = vec ? count / 4 : 0;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float4 *h4 = reinterpret_cast<float4 *>(hi), *l4 = reinterpret_cast<float4 *>(lo);
+    constexpr int U = 4;
+    for (int64_t i0 = tid; i0 < nv; i0 += nth * U) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * nth < nv) v[u] = __ldcs(x4 + i0 + u * nth);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * nth >= nv) continue;
+            float4 h, l;
+            km_split1(v[u].x, h.x, l.x);
+            km_split1(v[u].y, h.y, l.y);
+            km_split1(v[u].z, h.z, l.z);
+            km_split1(v[u].w, h.w, l.w);
+            h4[i0 + u * nth] = h;
+            l4[i0 + u * nth] = l;
+        }
     }
+    for (int64_t i = 4 * nv + tid; i < count; i += nth) km_split1(x[i], hi[i], lo[i]);
 }
 
 // D (TMEM, FP32) (+)= A B^T for one K = 8 step of TF32 operands (A: 128 rows, B: N rows, both K-major)
@@ -977,6 +1003,32 @@ static sf_status encode_rows(CUtensorMap *map, const float *ptr, int64_t rows, i
     return SF_OK;
 }
 
+// Pinned host words that the iterations' flags are copied into without
+// blocking: one buffer per host thread (calls from one thread run one after
+// another), grown when a call needs more. It is never freed (a few hundred
+// bytes per thread; freeing it while the CUDA runtime shuts down at exit is
+// not safe).
+static sf_status host_flags(int32_t **out, size_t count) {
+    struct Buf {
+        int32_t *p = nullptr;
+        size_t n = 0;
+    };
+    static thread_local Buf buf;
+    if (buf.n < count) {
+        if (buf.p) cudaFreeHost(buf.p);
+        buf.p = nullptr;
+        buf.n = 0;
+        void *q = nullptr;
+        const size_t want = count < 64 ? 64 : count;
+        const cudaError_t e = cudaHostAlloc(&q, want * sizeof(int32_t), cudaHostAllocPortable);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc (k-means flags)");
+        buf.p = static_cast<int32_t *>(q);
+        buf.n = want;
+    }
+    *out = buf.p;
+    return SF_OK;
+}
+
 static bool tc_shape_ok(int32_t d, int32_t k) { return d % 32 == 0 && d >= 32 && d <= 128 && k >= 1 && k <= 128; }
 
 static int tc_smem_bytes(int32_t d, int32_t nmma) {
@@ -1012,11 +1064,12 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     const int ig = 2 * sm_count();
     sf_status st;
     if ((st = sc.get(&fn, (size_t)n)) || (st = sc.get(&cn2, (size_t)k)) || (st = sc.get(&cmax, 1)) ||
-        (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
+        (st = sc.get(&changed, (size_t)max_iter)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
         (st = sc.get(&count, 2)) || (st = sc.get(&fmax_bits, 1)) || (st = sc.get(&S, (size_t)k * (d + 1))) ||
         (st = sc.get(&ipart, (size_t)ig)) || (st = sc.get(&isum, 1)))
         return st;
     SF_CHECK_CUDA(cudaMemsetAsync(labels, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1: no label yet
+    SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t) * (size_t)max_iter, s));  // one flag per assignment
     SF_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
     SF_CHECK_CUDA(cudaMemsetAsync(fmax_bits, 0, sizeof(int32_t), s));
     km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad, fmax_bits);
@@ -1035,7 +1088,7 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
             if ((st = sc.get(&Fhi, (size_t)n * d)) || (st = sc.get(&Flo, (size_t)n * d)) ||
                 (st = sc.get(&Chi, (size_t)k * d)) || (st = sc.get(&Clo, (size_t)k * d)))
                 return st;
-            km_split_tf32_kernel<<<4 * sm_count(), 256, 0, s>>>(F, (int64_t)n * d, Fhi, Flo);
+            km_split_tf32_kernel<<<8 * sm_count(), 256, 0, s>>>(F, (int64_t)n * d, Fhi, Flo);
             if ((st = check_launch("km_split_tf32_kernel"))) return st;
             if ((st = encode_rows(&mapF, Fhi, n, d, kTcRows)) || (st = encode_rows(&mapFlo, Flo, n, d, kTcRows)) ||
                 (st = encode_rows(&mapC, Chi, k, d, nmma)) || (st = encode_rows(&mapClo, Clo, k, d, nmma)))
@@ -1091,13 +1144,13 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
                                            (int)c_smem));
     }
     const int assign_grid = blocked ? (ex_occ > 0 ? ex_occ : 1) * sm_count() : (smem_c ? sm_count() : 4 * sm_count());
-    auto exact = [&](const int32_t *lst, const int32_t *cnt) -> sf_status {
+    auto exact = [&](const int32_t *lst, const int32_t *cnt, int32_t *chg) -> sf_status {
         if (blocked && ex_v4)
-            km_assign_blocked_kernel<true><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
+            km_assign_blocked_kernel<true><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, chg);
         else if (blocked)
-            km_assign_blocked_kernel<false><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, changed);
+            km_assign_blocked_kernel<false><<<assign_grid, 128, ex_smem, s>>>(F, n, d, C, k, lst, cnt, labels, chg);
         else
-            km_assign_kernel<<<assign_grid, 256, smem_c ? c_smem : 0, s>>>(F, n, d, C, k, lst, cnt, labels, changed,
+            km_assign_kernel<<<assign_grid, 256, smem_c ? c_smem : 0, s>>>(F, n, d, C, k, lst, cnt, labels, chg,
                                                                            smem_c);
         return check_launch("km_assign_kernel");
     };
@@ -1153,23 +1206,45 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
         SF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, km_inertia_kernel, kInWarps * 32, in_smem));
         in_grid = std::min(ig, std::max(occ, 1) * sm_count());
     }
-    int it = 0;
-    while (it < max_iter) {
-        SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+    // Lloyd iterations with one assignment of look-ahead: assignment t and its flags' copy to the host are
+    // queued, then the host waits for assignment t - 1's flags (the GPU meanwhile runs update t - 1 and
+    // assignment t), so the GPU does not idle on the host round trip. An update queued after an assignment
+    // that turns out to have changed no label recomputes the same centroids bit for bit (the same labels,
+    // the same exact sums), and the assignment after it the same labels: the look-ahead leaves labels,
+    // centroids, inertia and the iteration count as a loop that waits after every assignment.
+    int32_t *hflags = nullptr;  // [2 * max_iter]: changed and bad per assignment (pinned)
+    if ((st = host_flags(&hflags, 2 * (size_t)max_iter))) return st;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    SF_CHECK_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    }
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            cudaEventDestroy(e[0]);
+            cudaEventDestroy(e[1]);
+        }
+    } ev_guard{ev};
+    auto assign = [&](int t) -> sf_status {
+        sf_status r;
         km_centroid_norm_kernel<<<1, 1024, 0, s>>>(C, k, d, cn2, cmax, bad);
-        if ((st = check_launch("km_centroid_norm_kernel"))) return st;
+        if ((r = check_launch("km_centroid_norm_kernel"))) return r;
         if (tc) {
             SF_CHECK_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
             cudaEvent_t ea = nullptr, eb = nullptr;
             const bool prof = profiling_on() && profile_events(&ea, &eb);
             if (split) {
                 km_split_tf32_kernel<<<sm_count(), 256, 0, s>>>(C, (int64_t)k * d, Chi, Clo);
-                if ((st = check_launch("km_split_tf32_kernel"))) return st;
+                if ((r = check_launch("km_split_tf32_kernel"))) return r;
             }
+            TcParams Tt = T;
+            Tt.changed = changed + t;
             if (prof) cudaEventRecord(ea, s);
-            if (split) kmeans_tc_kernel<true><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, T);
-            else kmeans_tc_kernel<false><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, T);
-            if ((st = check_launch("kmeans_tc_kernel"))) return st;
+            if (split) kmeans_tc_kernel<true><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, Tt);
+            else kmeans_tc_kernel<false><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, Tt);
+            if ((r = check_launch("kmeans_tc_kernel"))) return r;
             if (prof) {
                 cudaEventRecord(eb, s);
                 // compulsory bytes: the rows once, the centroids per CTA (each in two parts when split),
@@ -1179,41 +1254,71 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
                                kProfTagKmeansTc);
             }
             km_assign_cands_kernel<<<4 * sm_count(), 256, (size_t)k * (d + 1) * sizeof(float), s>>>(
-                F, d, C, k, list, count, cmask, labels, changed);
-            if ((st = check_launch("km_assign_cands_kernel"))) return st;
-        } else {
-            if ((st = exact(nullptr, nullptr))) return st;
+                F, d, C, k, list, count, cmask, labels, changed + t);
+            if ((r = check_launch("km_assign_cands_kernel"))) return r;
+        } else if ((r = exact(nullptr, nullptr, changed + t))) {
+            return r;
         }
-        int32_t h_changed = 0, h_bad = 0;
-        SF_CHECK_CUDA(cudaMemcpyAsync(&h_changed, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SF_CHECK_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SF_CHECK_CUDA(cudaStreamSynchronize(s));
-        if ((st = sf_device_check(stream))) return st;
-        if (h_bad) {
-            set_error("non-finite feature row or centroid");
-            return SF_ERR_NUMERIC;
-        }
-        ++it;
-        const bool last = (it > 1 && !h_changed) || it == max_iter;
-        if (last && inertia) {
-            km_inertia_kernel<<<in_grid, kInWarps * 32, in_smem, s>>>(F, n, d, C, k, labels, in_t_smem, in_c_smem,
-                                                                    ipart);
-            if ((st = check_launch("km_inertia_kernel"))) return st;
-            if ((st = reduce_sum_f64(ipart, in_grid, isum, s))) return st;
-            SF_CHECK_CUDA(cudaMemcpyAsync(inertia, isum, sizeof(double), cudaMemcpyDeviceToHost, s));
-            SF_CHECK_CUDA(cudaStreamSynchronize(s));
-        }
-        if (it > 1 && !h_changed) break;
-        // update: exact fixed-point sums per cluster, then the FP64 means
+        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * t, changed + t, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * t + 1, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaEventRecord(ev[t & 1], s));
+        return SF_OK;
+    };
+    auto update = [&]() -> sf_status {
+        // exact fixed-point sums per cluster, then the FP64 means
+        sf_status r;
         SF_CHECK_CUDA(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * (size_t)k * (d + 1), s));
         if (fix_fn == (const void *)km_fixsum_kernel<true>)
             km_fixsum_kernel<true><<<fix_grid, kFixWarps * 32, fix_smem, s>>>(FP);
         else
             km_fixsum_kernel<false><<<fix_grid, kFixWarps * 32, fix_smem, s>>>(FP);
-        if ((st = check_launch("km_fixsum_kernel"))) return st;
+        if ((r = check_launch("km_fixsum_kernel"))) return r;
         km_fix_centroid_kernel<<<(k * d + 255) / 256, 256, 0, s>>>(n, d, k, fmax_bits, S, S + (size_t)k * d, C);
-        if ((st = check_launch("km_fix_centroid_kernel"))) return st;
+        return check_launch("km_fix_centroid_kernel");
+    };
+    // assignment t's flags on the host (its event has completed): SF_ERR_NUMERIC for a non-finite row or
+    // centroid; *conv: no label changed (from the second assignment on)
+    auto landed = [&](int t, bool *conv) -> sf_status {
+        SF_CHECK_CUDA(cudaEventSynchronize(ev[t & 1]));
+        if (hflags[2 * t + 1]) {
+            set_error("non-finite feature row or centroid");
+            return SF_ERR_NUMERIC;
+        }
+        *conv = t >= 1 && hflags[2 * t] == 0;
+        return SF_OK;
+    };
+    int final_t = -1;
+    bool conv_final = false;
+    for (int t = 0; t < max_iter; ++t) {
+        if ((st = assign(t))) return st;
+        if (t >= 1) {
+            bool conv = false;
+            if ((st = landed(t - 1, &conv))) return st;
+            if (conv) {  // assignment t - 1 changed nothing: update t - 1 and assignment t were no-ops
+                final_t = t - 1;
+                conv_final = true;
+                break;
+            }
+        }
+        if (t == max_iter - 1) {
+            bool conv = false;
+            if ((st = landed(t, &conv))) return st;
+            final_t = t;
+            conv_final = conv;
+            break;
+        }
+        if ((st = update())) return st;
     }
-    *iters = it;
+    SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    if ((st = sf_device_check(stream))) return st;
+    if (inertia) {  // of the final labels and the centroids they were assigned to
+        km_inertia_kernel<<<in_grid, kInWarps * 32, in_smem, s>>>(F, n, d, C, k, labels, in_t_smem, in_c_smem, ipart);
+        if ((st = check_launch("km_inertia_kernel"))) return st;
+        if ((st = reduce_sum_f64(ipart, in_grid, isum, s))) return st;
+        SF_CHECK_CUDA(cudaMemcpyAsync(inertia, isum, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!conv_final && (st = update())) return st;  // the last assignment changed labels: its update
+    *iters = final_t + 1;
     return SF_OK;
 }
