@@ -540,8 +540,10 @@ enum {
  * SF_KMEANS_TENSOR_SINGLE. Every row whose two best candidates lie within
  * the products' error bound is decided again with the exact FP32 sum on
  * CUDA cores, so all modes return the same labels. Deterministic.
- * SF_ERR_NUMERIC when a row or a centroid is not finite. Synchronises
- * `stream` once per assignment (to read whether labels changed).
+ * SF_ERR_NUMERIC when a row or a centroid is not finite (labels and C are
+ * then unspecified). The host reads whether an assignment changed labels
+ * one assignment later, while the GPU runs on (an update after the final
+ * assignment leaves C as it was); synchronises `stream` before returning.
  */
 SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int32_t k, float *C, int32_t max_iter,
                            int32_t mode, int32_t *labels, int32_t *iters, double *inertia, void *stream);
