@@ -72,6 +72,19 @@ def test_kmeans_tensor_cores_match_oracle(sf, oracle_mod, d, k):
         check_same(sf, oracle_mod, F, C0, 12, mode)
 
 
+def test_kmeans_iteration_limit_boundaries(sf, oracle_mod):
+    """The host learns whether an assignment changed labels one assignment
+    late; with max_iter just below, at and above the count at which labels
+    stop changing, labels, centroids, inertia and the count still equal the
+    oracle's (which stops after every assignment)."""
+    F, C0 = mixture(2500, 64, 12, seed=21)
+    _, _, it_free, _ = oracle_mod.kmeans(F, C0, 100)
+    assert it_free >= 3
+    for mode in (sf.KMEANS_TENSOR, sf.KMEANS_CUDA_CORES):
+        for mi in (1, 2, it_free - 1, it_free, it_free + 1):
+            check_same(sf, oracle_mod, F, C0, mi, mode)
+
+
 def test_kmeans_other_shapes_use_cuda_cores(sf, oracle_mod):
     F, C0 = mixture(1500, 48, 200, seed=5)  # d not a multiple of 32, k > 128
     check_same(sf, oracle_mod, F, C0, 6, sf.KMEANS_AUTO)
