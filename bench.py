@@ -307,7 +307,7 @@ def run_reference(args, wl):
     # a bounded sample per step: every order on a few columns (all cores), or a few orders on one thread
     p_ref = wl["p"] if par else (4 if wl["n"] >= 500_000 else max(1, min(wl["p"], 20)))
     a = oracle.cheb_coeffs(lam, 0.1 * lam, p_ref, True)
-    cols = min(4 if wl["n"] >= 500_000 else 8, wl["R"])
+    cols = min(8, wl["R"])  # as the cpu_baseline leg of our own arm
     blk = np.ascontiguousarray(R[:, :cols])
     units = (g.nnz + wl["n"]) * cols * p_ref
     for _ in range(args.warmup):
