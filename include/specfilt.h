@@ -98,9 +98,11 @@ enum {
  *                   (exact, undone on output), which keeps the blocks inside
  *                   the FP16 range. The moment sweep rejects SF_F16.
  *   algo            SF_ALGO_*.
- *   slab_cols       signal columns processed per sweep (0 = automatic). The
- *                   signals are independent, so the block is filtered in
- *                   column slabs whose gathered operand fits in L2.
+ *   slab_cols       signal columns processed per sweep (0 = automatic: the
+ *                   widest power-of-two slab whose gathered block fits in
+ *                   64 MB, about half of L2, and at least 16 FP32 or 32
+ *                   16-bit columns). The signals are independent, so the
+ *                   block is filtered in column slabs.
  *   block_warps     warps per thread block of the sweep kernel (0 = automatic).
  *   blocks_per_sm   resident blocks per SM of the persistent sweep grid (0 = max).
  *   ckpt_every      adjoint only: 0 = automatic (store every T_j when it fits

@@ -255,7 +255,7 @@ extern "C" SF_API sf_status sf_cheb_filter_backward(const sf_graph *g, double la
     sf_opts o = {};
     if (opts) o = *opts;
     SF_ARG(o.storage == SF_F32, "the adjoint keeps FP32 blocks (storage must be SF_F32)");
-    if (o.slab_cols <= 0) o.slab_cols = auto_slab_cols(g->n, n_sig, SF_F32, 32ll << 20);
+    if (o.slab_cols <= 0) o.slab_cols = auto_slab_cols(g->n, n_sig, SF_F32, kAutoSlabBudget);
     SweepShape sh;
     sf_status st = make_shape(SF_F32, o.slab_cols, o.block_warps, o.blocks_per_sm, MODE_FWD,
                               !g->unit_weights, &sh, o.carveout_pct, o.sweep_kernel);

@@ -1292,6 +1292,7 @@ struct SweepShape {
 
 // Picks the slab width (columns) for n rows and n_sig signals.
 int auto_slab_cols(int64_t n, int n_sig, int storage, int64_t l2_budget_bytes);
+constexpr int64_t kAutoSlabBudget = 64ll << 20;  // gathered block per slab: about half of L2
 sf_status make_shape(int storage, int slab_cols, int block_warps, int blocks_per_sm, int mode, bool weighted,
                      SweepShape *sh, int carveout_pct = 0, int sweep_kernel = 0);
 using StepFn = void (*)(const StepParams);
