@@ -308,6 +308,37 @@ def test_direct_kernel_matches_tiled_and_oracle(sf, oracle_mod, weighted):
     assert torch.equal(grads[0][2], grads[1][2])
 
 
+def test_default_slab_on_a_mid_size_graph(sf):
+    """A 150k-node graph with 64 FP32 signals: the automatic slab is the whole
+    64-column block (38 MB, under the 64 MB budget), where a 16-column slab was
+    the default before. Each column's arithmetic does not depend on the slab,
+    so the filter (both algorithms, two cutoffs) is bit-identical to 16-column
+    slabs, the moments agree to FP64 reduction order and the adjoint to its
+    tolerance."""
+    from paper_1509_08863_gb300 import synth
+
+    n, n_sig, p = 150_000, 64, 20
+    gr = synth.sbm_edges(n, synth.community_sizes_equal(n, 10), 10.0, 0.1, seed=41)
+    dev = torch.device("cuda")
+    g = sf.csr_build(n, torch.as_tensor(gr.src, device=dev), torch.as_tensor(gr.dst, device=dev), None)
+    lh = 2.0 * float((np.bincount(gr.src, minlength=n) + np.bincount(gr.dst, minlength=n)).max())
+    a = sf.cheb_coeffs(lh, [0.05 * lh, 0.2 * lh], p, True)
+    R = torch.randn(n, n_sig, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3)) / 8.0
+    for algo in (sf.ALGO_FORWARD, sf.ALGO_CLENSHAW):
+        y_auto = sf.cheb_filter(g, lh, a, R, sf.Opts(algo=algo))
+        y_16 = sf.cheb_filter(g, lh, a, R, sf.Opts(algo=algo, slab_cols=16))
+        assert torch.equal(y_auto, y_16), algo
+    mu_auto = sf.cheb_moments(g, lh, R, p)
+    mu_16 = sf.cheb_moments(g, lh, R, p, sf.Opts(slab_cols=16))
+    assert np.all(np.abs(mu_auto - mu_16) <= 2e-6 * (np.arange(2 * p + 1) + 1) * mu_auto[0])
+    G = torch.randn(n, n_sig, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4))
+    gw_a, ga_a, _ = sf.cheb_filter_backward(g, lh, a[0], R, G, False)
+    gw_16, ga_16, _ = sf.cheb_filter_backward(g, lh, a[0], R, G, False, sf.Opts(slab_cols=16))
+    assert rel(gw_a.cpu().numpy(), gw_16.cpu().numpy()) <= 2e-5
+    assert np.all(np.abs(ga_a - ga_16) <= 2e-5 * np.abs(ga_16).max())
+    sf.device_check()
+
+
 # ------------------------------------------------------------------ moments / count
 def test_moments_and_counts_match_oracle(sf, oracle_mod):
     from paper_1509_08863_gb300 import synth
