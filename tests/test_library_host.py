@@ -174,3 +174,17 @@ def test_host_cheb_order_matches_oracle(sflib, oracle_mod):
             assert sflib.cheb_order(x, delta, w, True, 800) == oracle_mod.cheb_order(x, delta, w, True, 800)
     with pytest.raises(sflib.SpecFiltError):
         sflib.cheb_order(1.5, 0.1, 0.01)
+
+
+def test_diagnostic_argument_checks_without_gpu(sflib):
+    """The gather diagnostics reject bad sizes before allocating or launching anything, and leave the
+    result untouched."""
+    L = sflib.lib()
+    r = C.c_double(-1.0)
+    for args in ((0, 64, 32, 1), (1000, 48, 32, 1), (1000, 64, 30, 1), (1000, 64, 0, 1), (1000, 64, 32, 0),
+                 (1 << 31, 64, 32, 1)):
+        assert L.sf_gather_ceiling(*args, None, C.byref(r)) == 1
+        assert L.sf_gather_rate(*args, 0, None, C.byref(r)) == 1
+        assert L.sf_gather_rate(*args, 1, None, C.byref(r)) == 1
+    assert r.value == -1.0
+    assert L.sf_gather_rate(1000, 64, 32, 1, 0, None, None) == 1 and b"rows_per_s" in L.sf_last_error()
