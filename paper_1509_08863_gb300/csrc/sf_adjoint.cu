@@ -136,23 +136,39 @@ __global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
             }
             const int32_t *ip = fits ? s_ix + eo : P.sell_idx + e0 + eo;
             float *mp = P.Msell + (int64_t)e0 + eo;  // 16-byte aligned: rows start on multiples of 4
-            for (int32_t j = 0; j < ls; j += 4) {
+            // eight entries per pass (four in the last one when ls is not a multiple of 8): their gathers and
+            // the accumulators they add into are all requested before the first product is reduced
+            for (int32_t j = 0; j < ls; j += 8) {
+                const bool two = j + 4 < ls;
                 const int4 a = fits ? lds_int4(ip + j) : __ldg(reinterpret_cast<const int4 *>(ip + j));
-                const int32_t kk[4] = {a.x, a.y, a.z, a.w};
-                float4 x[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
-                float d[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] = group_sum<LPR>(gmask, dot4(gb, x[u]));
+                const int4 b = two ? (fits ? lds_int4(ip + j + 4) : __ldg(reinterpret_cast<const int4 *>(ip + j + 4)))
+                                   : a;
+                float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
                 if (q == 0) {
-                    float4 m = *reinterpret_cast<float4 *>(mp + j);
-                    m.x = fmaf(P.csd, d[0], m.x);
-                    m.y = fmaf(P.csd, d[1], m.y);
-                    m.z = fmaf(P.csd, d[2], m.z);
-                    m.w = fmaf(P.csd, d[3], m.w);
-                    *reinterpret_cast<float4 *>(mp + j) = m;
+                    m0 = __ldcg(reinterpret_cast<const float4 *>(mp + j));
+                    if (two) m1 = __ldcg(reinterpret_cast<const float4 *>(mp + j + 4));
+                }
+                const int32_t kk[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
+                float d[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[u] = group_sum<LPR>(gmask, dot4(gb, x[u]));
+                if (q == 0) {
+                    m0.x = fmaf(P.csd, d[0], m0.x);
+                    m0.y = fmaf(P.csd, d[1], m0.y);
+                    m0.z = fmaf(P.csd, d[2], m0.z);
+                    m0.w = fmaf(P.csd, d[3], m0.w);
+                    *reinterpret_cast<float4 *>(mp + j) = m0;
+                    if (two) {
+                        m1.x = fmaf(P.csd, d[4], m1.x);
+                        m1.y = fmaf(P.csd, d[5], m1.y);
+                        m1.z = fmaf(P.csd, d[6], m1.z);
+                        m1.w = fmaf(P.csd, d[7], m1.w);
+                        *reinterpret_cast<float4 *>(mp + j + 4) = m1;
+                    }
                 }
             }
         }
