@@ -143,31 +143,63 @@ __global__ void __launch_bounds__(256, 4) sddmm_kernel(const SddmmParams P) {
                 const int4 a = fits ? lds_int4(ip + j) : __ldg(reinterpret_cast<const int4 *>(ip + j));
                 const int4 b = two ? (fits ? lds_int4(ip + j + 4) : __ldg(reinterpret_cast<const int4 *>(ip + j + 4)))
                                    : a;
-                float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
-                if (q == 0) {
-                    m0 = __ldcg(reinterpret_cast<const float4 *>(mp + j));
-                    if (two) m1 = __ldcg(reinterpret_cast<const float4 *>(mp + j + 4));
-                }
                 const int32_t kk[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                float4 x[8];
+                if constexpr (LPR >= 8) {
+                    // the group's 8 partial sums are reduced transposed: three exchange steps leave lane q
+                    // with the sum over LPR / 8 ... of entry q / (LPR / 8), the remaining steps finish it
+                    constexpr int kSub = LPR / 8;
+                    const int e = q / kSub;
+                    const bool writer = q % kSub == 0 && (two || e < 4);
+                    const float m = writer ? __ldcg(mp + j + e) : 0.f;
+                    float4 x[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
-                float d[8];
+                    for (int u = 0; u < 8; ++u)
+                        x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
+                    float d[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) d[u] = group_sum<LPR>(gmask, dot4(gb, x[u]));
-                if (q == 0) {
-                    m0.x = fmaf(P.csd, d[0], m0.x);
-                    m0.y = fmaf(P.csd, d[1], m0.y);
-                    m0.z = fmaf(P.csd, d[2], m0.z);
-                    m0.w = fmaf(P.csd, d[3], m0.w);
-                    *reinterpret_cast<float4 *>(mp + j) = m0;
-                    if (two) {
-                        m1.x = fmaf(P.csd, d[4], m1.x);
-                        m1.y = fmaf(P.csd, d[5], m1.y);
-                        m1.z = fmaf(P.csd, d[6], m1.z);
-                        m1.w = fmaf(P.csd, d[7], m1.w);
-                        *reinterpret_cast<float4 *>(mp + j + 4) = m1;
+                    for (int u = 0; u < 8; ++u) d[u] = dot4(gb, x[u]);
+#pragma unroll
+                    for (int st = 0; st < 3; ++st) {
+                        const int o = LPR >> (st + 1);
+                        const int half = 4 >> st;
+                        const bool up = (q & o) != 0;
+#pragma unroll
+                        for (int i = 0; i < half; ++i) {
+                            const float send = up ? d[i] : d[i + half];
+                            const float keep = up ? d[i + half] : d[i];
+                            d[i] = keep + __shfl_xor_sync(gmask, send, o);
+                        }
+                    }
+                    float v = d[0];
+#pragma unroll
+                    for (int o = kSub / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
+                    if (writer) mp[j + e] = fmaf(P.csd, v, m);
+                } else {
+                    float4 m0 = make_float4(0.f, 0.f, 0.f, 0.f), m1 = m0;
+                    if (q == 0) {
+                        m0 = __ldcg(reinterpret_cast<const float4 *>(mp + j));
+                        if (two) m1 = __ldcg(reinterpret_cast<const float4 *>(mp + j + 4));
+                    }
+                    float4 x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        x[u] = __ldg(reinterpret_cast<const float4 *>(Tm1q + (uint32_t)kk[u] * (uint32_t)ld));
+                    float d[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) d[u] = group_sum<LPR>(gmask, dot4(gb, x[u]));
+                    if (q == 0) {
+                        m0.x = fmaf(P.csd, d[0], m0.x);
+                        m0.y = fmaf(P.csd, d[1], m0.y);
+                        m0.z = fmaf(P.csd, d[2], m0.z);
+                        m0.w = fmaf(P.csd, d[3], m0.w);
+                        *reinterpret_cast<float4 *>(mp + j) = m0;
+                        if (two) {
+                            m1.x = fmaf(P.csd, d[4], m1.x);
+                            m1.y = fmaf(P.csd, d[5], m1.y);
+                            m1.z = fmaf(P.csd, d[6], m1.z);
+                            m1.w = fmaf(P.csd, d[7], m1.w);
+                            *reinterpret_cast<float4 *>(mp + j + 4) = m1;
+                        }
                     }
                 }
             }
