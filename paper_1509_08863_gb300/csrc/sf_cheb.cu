@@ -137,16 +137,21 @@ sf_status launch_step(const SweepShape &sh, int mode, const StepParams &P, cudaS
     cfg.blockDim = dim3(sh.block);
     cfg.dynamicSmemBytes = sh.smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
+    // programmatic dependent launch: the sweep's blocks start (and stage their first CSR tiles) while the
+    // previous launch in the stream finishes; they wait for it before touching its outputs (pdl_wait)
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     if (sh.l2_window_bytes > 0) {
-        at[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        at[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(P.X);
-        at[0].val.accessPolicyWindow.num_bytes = sh.l2_window_bytes;
-        at[0].val.accessPolicyWindow.hitRatio = sh.l2_hit_ratio;
-        at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-        at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
+        at[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[1].val.accessPolicyWindow.base_ptr = const_cast<void *>(P.X);
+        at[1].val.accessPolicyWindow.num_bytes = sh.l2_window_bytes;
+        at[1].val.accessPolicyWindow.hitRatio = sh.l2_hit_ratio;
+        at[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.numAttrs = 2;
     }
     cudaLaunchKernelEx(&cfg, fn, P);
     sf_status st = check_launch(sh.direct ? "cheb_step_direct_kernel" : "cheb_step_kernel");

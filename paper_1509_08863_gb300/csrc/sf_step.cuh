@@ -366,6 +366,17 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: a sweep launched with programmatic stream
+// serialization may have its blocks resident while the previous launch in
+// the stream is still finishing. Each block signals at its start that the
+// next launch may begin (pdl_allow_next) and, before it touches any block,
+// accumulator or counter that an earlier launch writes, waits until that
+// launch has completed with its memory visible (pdl_wait; it returns at once
+// when the launch was not programmatic). Only the CSR (read-only during a
+// sweep) is read before the wait.
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Polls are bounded: a copy that never lands makes the kernel record an
 // error in *status and return instead of waiting forever.
 constexpr uint32_t kWaitPolls = 1u << 22;
@@ -736,6 +747,7 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
         }
     };
 
+    pdl_allow_next();
     if (tid == 0) {
         for (int b = 0; b < NST; ++b) {
             mbar_init(&s_bar[b], 1);
@@ -749,6 +761,7 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
         }
     }
     __syncthreads();
+    pdl_wait();  // the first tiles' CSR copies overlap the previous launch's end
     for (int k = 0;; ++k) {
         const int tile = blockIdx.x + k * gridDim.x;
         if (tile >= n_tiles) break;
@@ -806,6 +819,8 @@ __global__ void __launch_bounds__(256, 4) cheb_step_kernel(const StepParams P) {
 // group). With no shared memory the whole L1 holds gathers in flight.
 template <typename TS, int LPR, int MODE, bool W>
 __global__ void __launch_bounds__(256, 4) cheb_step_direct_kernel(const StepParams P) {
+    pdl_allow_next();
+    pdl_wait();
     constexpr int RPW = 32 / LPR;
     const int lane = threadIdx.x & 31, q = lane % LPR, g = lane / LPR;
     const int64_t n_chunks = ((int64_t)P.n + RPW - 1) / RPW;
