@@ -1064,12 +1064,11 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     const int ig = 2 * sm_count();
     sf_status st;
     if ((st = sc.get(&fn, (size_t)n)) || (st = sc.get(&cn2, (size_t)k)) || (st = sc.get(&cmax, 1)) ||
-        (st = sc.get(&changed, (size_t)max_iter)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
+        (st = sc.get(&changed, 2)) || (st = sc.get(&bad, 1)) || (st = sc.get(&list, (size_t)n)) ||
         (st = sc.get(&count, 2)) || (st = sc.get(&fmax_bits, 1)) || (st = sc.get(&S, (size_t)k * (d + 1))) ||
         (st = sc.get(&ipart, (size_t)ig)) || (st = sc.get(&isum, 1)))
         return st;
     SF_CHECK_CUDA(cudaMemsetAsync(labels, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1: no label yet
-    SF_CHECK_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t) * (size_t)max_iter, s));  // one flag per assignment
     SF_CHECK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
     SF_CHECK_CUDA(cudaMemsetAsync(fmax_bits, 0, sizeof(int32_t), s));
     km_row_norm_kernel<<<4 * sm_count(), 256, 0, s>>>(F, n, d, fn, bad, fmax_bits);
@@ -1212,8 +1211,10 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     // that turns out to have changed no label recomputes the same centroids bit for bit (the same labels,
     // the same exact sums), and the assignment after it the same labels: the look-ahead leaves labels,
     // centroids, inertia and the iteration count as a loop that waits after every assignment.
-    int32_t *hflags = nullptr;  // [2 * max_iter]: changed and bad per assignment (pinned)
-    if ((st = host_flags(&hflags, 2 * (size_t)max_iter))) return st;
+    // flags of assignment t in slot t & 1 (device: changed; pinned host: changed, bad): at most two assignments
+    // are in flight, and a slot is cleared for assignment t only after the host has read assignment t - 2
+    int32_t *hflags = nullptr;
+    if ((st = host_flags(&hflags, 4))) return st;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     SF_CHECK_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -1229,6 +1230,7 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     } ev_guard{ev};
     auto assign = [&](int t) -> sf_status {
         sf_status r;
+        SF_CHECK_CUDA(cudaMemsetAsync(changed + (t & 1), 0, sizeof(int32_t), s));
         km_centroid_norm_kernel<<<1, 1024, 0, s>>>(C, k, d, cn2, cmax, bad);
         if ((r = check_launch("km_centroid_norm_kernel"))) return r;
         if (tc) {
@@ -1240,7 +1242,7 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
                 if ((r = check_launch("km_split_tf32_kernel"))) return r;
             }
             TcParams Tt = T;
-            Tt.changed = changed + t;
+            Tt.changed = changed + (t & 1);
             if (prof) cudaEventRecord(ea, s);
             if (split) kmeans_tc_kernel<true><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, Tt);
             else kmeans_tc_kernel<false><<<tc_grid, 192, tc_smem, s>>>(mapF, mapC, mapFlo, mapClo, Tt);
@@ -1254,13 +1256,13 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
                                kProfTagKmeansTc);
             }
             km_assign_cands_kernel<<<4 * sm_count(), 256, (size_t)k * (d + 1) * sizeof(float), s>>>(
-                F, d, C, k, list, count, cmask, labels, changed + t);
+                F, d, C, k, list, count, cmask, labels, changed + (t & 1));
             if ((r = check_launch("km_assign_cands_kernel"))) return r;
-        } else if ((r = exact(nullptr, nullptr, changed + t))) {
+        } else if ((r = exact(nullptr, nullptr, changed + (t & 1)))) {
             return r;
         }
-        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * t, changed + t, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * t + 1, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * (t & 1), changed + (t & 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SF_CHECK_CUDA(cudaMemcpyAsync(hflags + 2 * (t & 1) + 1, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SF_CHECK_CUDA(cudaEventRecord(ev[t & 1], s));
         return SF_OK;
     };
@@ -1280,11 +1282,11 @@ extern "C" SF_API sf_status sf_kmeans(const float *F, int32_t n, int32_t d, int3
     // centroid; *conv: no label changed (from the second assignment on)
     auto landed = [&](int t, bool *conv) -> sf_status {
         SF_CHECK_CUDA(cudaEventSynchronize(ev[t & 1]));
-        if (hflags[2 * t + 1]) {
+        if (hflags[2 * (t & 1) + 1]) {
             set_error("non-finite feature row or centroid");
             return SF_ERR_NUMERIC;
         }
-        *conv = t >= 1 && hflags[2 * t] == 0;
+        *conv = t >= 1 && hflags[2 * (t & 1)] == 0;
         return SF_OK;
     };
     int final_t = -1;
