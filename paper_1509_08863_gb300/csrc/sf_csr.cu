@@ -129,36 +129,56 @@ __global__ void run_heads_kernel(const uint64_t *keys, int64_t valid, int32_t *h
 
 // For each run head: colidx/val at the run's output slot (largest weight of
 // the run) and one count for its row.
+// The keys are sorted, so a warp's heads mostly share one or two rows: the
+// row counts are added once per row and warp (the lanes of a row matched).
 __global__ void compact_runs_kernel(const uint64_t *keys, const float *vals, const int32_t *head,
                                     const int32_t *pos, int64_t valid, int cb, int32_t *colidx, float *val,
                                     int32_t *rowcnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= valid || !head[i]) return;
-    uint64_t k = keys[i];
-    float x = vals[i];
-    for (int64_t t = i + 1; t < valid && keys[t] == k; ++t) x = fmaxf(x, vals[t]);
-    int32_t o = pos[i];
-    colidx[o] = (int32_t)(k & ((1ull << cb) - 1ull));
-    val[o] = x;
-    atomicAdd(&rowcnt[(int32_t)(k >> cb)], 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool h = i < valid && head[i];
+    int32_t row = -1 - lane;  // distinct for lanes without a head: they match no other lane
+    if (h) {
+        const uint64_t k = keys[i];
+        float x = vals[i];
+        for (int64_t t = i + 1; t < valid && keys[t] == k; ++t) x = fmaxf(x, vals[t]);
+        const int32_t o = pos[i];
+        colidx[o] = (int32_t)(k & ((1ull << cb) - 1ull));
+        val[o] = x;
+        row = (int32_t)(k >> cb);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, row);
+    if (h && lane == __ffs(peers) - 1) atomicAdd(&rowcnt[row], __popc(peers));
 }
 
-// s_i = sum of row i in column order (FP64); flags[0] set if a weight != 1.
+// s_i = sum of row i in column order (FP64); flags[0] set if a weight != 1;
+// the largest s_i. The flag and the maximum are combined over the warp first
+// (one atomic per warp instead of one per row on a single address).
 __global__ void strength_kernel(int32_t n, const int32_t *rowptr, const float *val, double *s,
                                 int32_t *nonunit, unsigned long long *smax_bits) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
     int nu = 0;
-    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-        float x = val[e];
-        acc += (double)x;
-        nu |= (x != 1.0f);
+    if (i < n) {
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            float x = val[e];
+            acc += (double)x;
+            nu |= (x != 1.0f);
+        }
+        s[i] = acc;
     }
-    s[i] = acc;
-    if (nu) atomicOr(nonunit, 1);
     // non-negative doubles order like their bit patterns
-    atomicMax(smax_bits, (unsigned long long)__double_as_longlong(acc));
+    unsigned long long m = (unsigned long long)__double_as_longlong(acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+    }
+    const bool any_nu = __any_sync(0xffffffffu, nu);
+    if ((threadIdx.x & 31) == 0) {
+        if (any_nu) atomicOr(nonunit, 1);
+        atomicMax(smax_bits, m);
+    }
 }
 
 sf_status compute_strength(sf_graph *g, cudaStream_t s) {
