@@ -68,15 +68,24 @@ __global__ void radix_hist_kernel(const uint64_t *keys, int64_t count, int shift
 // them in 8 rounds of 32 consecutive items; equal digits in a round are
 // ranked by lane order through __match_any_sync, and running per-warp digit
 // counts carry the order across rounds. Per-digit warp bases then follow
-// warp order, so the scatter preserves input order among equal digits.
+// warp order, so the scatter preserves input order among equal digits. The
+// tile's items are first placed in shared memory in (digit, input) order,
+// then written out by consecutive threads: each digit's items of a tile land
+// in consecutive words (coalesced runs) instead of one scattered word per
+// item.
 __global__ void radix_scatter_kernel(const uint64_t *keys_in, const float *vals_in, uint64_t *keys_out,
                                      float *vals_out, int64_t count, int shift, const int32_t *offs,
                                      int32_t tiles) {
     __shared__ int32_t wcnt[kSortWarps][256];
+    __shared__ int32_t tdig[256];  // first tile-local position of each digit
+    __shared__ int32_t wsum[kSortWarps];
+    __shared__ uint64_t s_key[kSortTile];
+    __shared__ float s_val[kSortTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
     __syncwarp();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * 256;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)w * 256;
     uint64_t key[kSortItems];
     float val[kSortItems];
     int32_t rank[kSortItems];
@@ -98,9 +107,9 @@ __global__ void radix_scatter_kernel(const uint64_t *keys_in, const float *vals_
         rank[r] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
-    // exclusive prefix over warps, one digit per thread
+    // exclusive prefix over warps, one digit per thread, then over digits
     {
-        int d = threadIdx.x;
+        const int d = threadIdx.x;
         int32_t run = 0;
 #pragma unroll
         for (int q = 0; q < kSortWarps; ++q) {
@@ -108,15 +117,35 @@ __global__ void radix_scatter_kernel(const uint64_t *keys_in, const float *vals_
             wcnt[q][d] = run;
             run += c;
         }
+        int32_t v = run;  // inclusive scan of the digit totals within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        int32_t wb = 0;
+        for (int q = 0; q < w; ++q) wb += wsum[q];
+        tdig[d] = wb + v - run;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (dig[r] < 0) continue;
-        int d = dig[r];
-        int64_t pos = (int64_t)offs[(int64_t)d * tiles + blockIdx.x] + wcnt[w][d] + rank[r];
-        keys_out[pos] = key[r];
-        if (vals_out) vals_out[pos] = val[r];
+        const int d = dig[r];
+        const int32_t lp = tdig[d] + wcnt[w][d] + rank[r];
+        s_key[lp] = key[r];
+        if (vals_out) s_val[lp] = val[r];
+    }
+    __syncthreads();
+    const int items = (int)min((int64_t)kSortTile, count - tile0);
+    for (int t = threadIdx.x; t < items; t += kSortThreads) {
+        const uint64_t kk = s_key[t];
+        const int d = (int)((kk >> shift) & 0xFF);
+        const int64_t pos = (int64_t)offs[(int64_t)d * tiles + blockIdx.x] + (t - tdig[d]);
+        keys_out[pos] = kk;
+        if (vals_out) vals_out[pos] = s_val[t];
     }
 }
 
